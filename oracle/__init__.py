@@ -1,0 +1,230 @@
+"""ORACLE -- test infrastructure only.
+
+ctypes binding of ``oracle.c``: the plain single-threaded CPU statement of what
+the map / map-reduce path computes (Sec. 3.2.4 and Sec. 3.2.5 of Klockner et al.,
+"GPU Scripting and Code Generation with PyCUDA"), in binary64.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The library (``paper_1304_5553_gb300``) never
+does, and this package imports nothing from the library.
+
+Every function here is pinned by ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_DIR = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_DIR, "_build")
+_SRC = os.path.join(_DIR, "oracle.c")
+LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+
+def build_cmd():
+    return [os.environ.get("CC", "gcc"), "-O2", "-std=gnu11", "-ffp-contract=off",
+            "-fno-fast-math", "-fPIC", "-shared", "-o", LIB_PATH, _SRC, "-lm"]
+
+
+def build(force=False):
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(LIB_PATH) or \
+            os.path.getmtime(LIB_PATH) < os.path.getmtime(_SRC):
+        p = subprocess.run(build_cmd(), capture_output=True, text=True)
+        if p.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + p.stderr)
+    return LIB_PATH
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(LIB_PATH)
+        i64, f64, vp = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+        sig = {
+            "orc_round_bf16": (f64, [f64]),
+            "orc_round_f32": (ctypes.c_float, [f64]),
+            "orc_map_scale": (None, [i64, f64, vp, vp, vp]),
+            "orc_map_add": (None, [i64, vp, vp, vp, vp]),
+            "orc_map_lin_comb": (None, [i64, f64, vp, f64, vp, ctypes.c_int, vp, vp, vp]),
+            "orc_map_gauss_sin": (None, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "orc_map_gauss_sin_at": (None, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "orc_sum_f32": (f64, [i64, vp, vp]),
+            "orc_dot_f32": (f64, [i64, vp, vp, vp]),
+            "orc_dot_segments_f32": (None, [i64, vp, vp, vp, vp, vp]),
+            "orc_sum_i32_i64": (i64, [i64, vp]),
+            "orc_dot_i32_i64": (i64, [i64, vp, vp]),
+            "orc_max_f32": (ctypes.c_float, [i64, vp]),
+            "orc_min_f32": (ctypes.c_float, [i64, vp]),
+            "orc_argmin_f32": (None, [i64, vp, vp, vp]),
+            "orc_argmax_f32": (None, [i64, vp, vp, vp]),
+            "orc_exact_sum_f64": (f64, [i64, vp]),
+            "orc_exact_dot_f32": (f64, [i64, vp, vp]),
+            "orc_exact_sum_f32": (f64, [i64, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# ------------------------------------------------------------------ rounding
+
+def round_bf16(d: float) -> float:
+    """binary64 -> nearest bfloat16, ties to even (one rounding)."""
+    return float(_load().orc_round_bf16(float(d)))
+
+
+def round_f32(d: float) -> float:
+    return float(_load().orc_round_f32(float(d)))
+
+
+# ------------------------------------------------------------------ maps
+
+def map_scale(s, x):
+    """Listing 1/2: z = s*x.  Returns (z binary32, z binary64)."""
+    x = _f32(x)
+    z, z64 = np.empty_like(x), np.empty(x.size, np.float64)
+    _load().orc_map_scale(x.size, float(s), _ptr(x), _ptr(z), _ptr(z64))
+    return z, z64
+
+
+def map_add(x, y):
+    """Listing 4: z = x + y.  Returns (z binary32, z binary64)."""
+    x, y = _f32(x), _f32(y)
+    assert x.size == y.size
+    z, z64 = np.empty_like(x), np.empty(x.size, np.float64)
+    _load().orc_map_add(x.size, _ptr(x), _ptr(y), _ptr(z), _ptr(z64))
+    return z, z64
+
+
+def map_lin_comb(a, x, b, y, out_bf16=False):
+    """Listing 3a: z = a*x + b*y.  Returns (z, z64, |a x| + |b y|); z holds the
+    binary32 or bfloat16 (as binary32 values) storage result."""
+    x, y = _f32(x), _f32(y)
+    assert x.size == y.size
+    z = np.empty_like(x)
+    z64, tab = np.empty(x.size, np.float64), np.empty(x.size, np.float64)
+    _load().orc_map_lin_comb(x.size, float(a), _ptr(x), float(b), _ptr(y), int(out_bf16),
+                             _ptr(z), _ptr(z64), _ptr(tab))
+    return z, z64, tab
+
+
+def map_gauss_sin(x, y, u, w):
+    """z = x*exp(-y*y) + sin(u)*w.  Returns (z, z64, t1, t2) with the binary64
+    addends t1 = x exp(-y^2), t2 = sin(u) w."""
+    x, y, u, w = _f32(x), _f32(y), _f32(u), _f32(w)
+    n = x.size
+    assert y.size == n and u.size == n and w.size == n
+    z = np.empty_like(x)
+    z64, t1, t2 = (np.empty(n, np.float64) for _ in range(3))
+    _load().orc_map_gauss_sin(n, _ptr(x), _ptr(y), _ptr(u), _ptr(w), _ptr(z), _ptr(z64),
+                              _ptr(t1), _ptr(t2))
+    return z, z64, t1, t2
+
+
+def map_gauss_sin_at(idx, x, y, u, w):
+    """The four-input map at the given indices only: (z64, t1, t2)."""
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    k = idx.size
+    z64, t1, t2 = (np.empty(k, np.float64) for _ in range(3))
+    _load().orc_map_gauss_sin_at(k, _ptr(idx), _ptr(_f32(x)), _ptr(_f32(y)), _ptr(_f32(u)),
+                                 _ptr(_f32(w)), _ptr(z64), _ptr(t1), _ptr(t2))
+    return z64, t1, t2
+
+
+# ------------------------------------------------------------------ reductions
+
+def sum_f32(x):
+    """(sum x in binary64 (compensated), sum |x|)."""
+    x = _f32(x)
+    a = ctypes.c_double()
+    s = _load().orc_sum_f32(x.size, _ptr(x), ctypes.addressof(a))
+    return s, a.value
+
+
+def dot_f32(x, y):
+    """Listing 3b: (sum x*y in binary64 (compensated), sum |x*y|)."""
+    x, y = _f32(x), _f32(y)
+    assert x.size == y.size
+    a = ctypes.c_double()
+    s = _load().orc_dot_f32(x.size, _ptr(x), _ptr(y), ctypes.addressof(a))
+    return s, a.value
+
+
+def dot_segments_f32(offsets, x, y):
+    """Per-segment dot products; returns (values, sum |terms| per segment)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nseg = off.size - 1
+    x, y = _f32(x), _f32(y)
+    assert off[-1] <= x.size and off[-1] <= y.size
+    out, ab = np.empty(nseg, np.float64), np.empty(nseg, np.float64)
+    _load().orc_dot_segments_f32(nseg, _ptr(off), _ptr(x), _ptr(y), _ptr(out), _ptr(ab))
+    return out, ab
+
+
+def sum_i32_i64(x):
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    return int(_load().orc_sum_i32_i64(x.size, _ptr(x)))
+
+
+def dot_i32_i64(x, y):
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    return int(_load().orc_dot_i32_i64(x.size, _ptr(x), _ptr(y)))
+
+
+def max_f32(x):
+    x = _f32(x)
+    return float(_load().orc_max_f32(x.size, _ptr(x)))
+
+
+def min_f32(x):
+    x = _f32(x)
+    return float(_load().orc_min_f32(x.size, _ptr(x)))
+
+
+def argmin_f32(x):
+    x = _f32(x)
+    v, i = ctypes.c_float(), ctypes.c_int64()
+    _load().orc_argmin_f32(x.size, _ptr(x), ctypes.addressof(v), ctypes.addressof(i))
+    return float(v.value), int(i.value)
+
+
+def argmax_f32(x):
+    x = _f32(x)
+    v, i = ctypes.c_float(), ctypes.c_int64()
+    _load().orc_argmax_f32(x.size, _ptr(x), ctypes.addressof(v), ctypes.addressof(i))
+    return float(v.value), int(i.value)
+
+
+def exact_sum_f64(t):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    return float(_load().orc_exact_sum_f64(t.size, _ptr(t)))
+
+
+def exact_sum_f32(x):
+    x = _f32(x)
+    return float(_load().orc_exact_sum_f32(x.size, _ptr(x)))
+
+
+def exact_dot_f32(x, y):
+    x, y = _f32(x), _f32(y)
+    return float(_load().orc_exact_dot_f32(x.size, _ptr(x), _ptr(y)))

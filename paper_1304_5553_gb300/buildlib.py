@@ -1,0 +1,111 @@
+"""Build steps for the native parts of the package.
+
+* ``libpyc.so``    -- the C-ABI library (C++ host code: spec parser, code
+  generator, NVRTC driver + kernel cache, launches, batched reducer,
+  autotuner, server).  Device code is generated per spec and compiled by
+  NVRTC for sm_103a at run time; :func:`check_templates` compiles the stock
+  templates ahead of time so that a template error fails the build.
+* ``libpycgen.so`` -- the seeded input generator (plain C).
+
+Everything is built in-tree under ``paper_1304_5553_gb300/_build`` with plain
+compiler invocations (no cmake), so the same step works on x86_64 and aarch64.
+"""
+from __future__ import annotations
+
+import glob
+import os
+import shutil
+import subprocess
+import sys
+
+PKG_DIR = os.path.dirname(os.path.abspath(__file__))
+BUILD_DIR = os.path.join(PKG_DIR, "_build")
+CSRC = os.path.join(PKG_DIR, "csrc")
+REPO_DIR = os.path.dirname(PKG_DIR)
+INCLUDE_DIR = os.path.join(REPO_DIR, "include")
+ARCH = "sm_103a"
+
+
+def cuda_home() -> str:
+    for cand in (os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"), "/usr/local/cuda"):
+        if cand and os.path.isdir(os.path.join(cand, "include")):
+            return cand
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        return os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    raise RuntimeError("CUDA toolkit not found (set CUDA_HOME)")
+
+
+def pyc_lib_path() -> str:
+    return os.path.join(BUILD_DIR, "libpyc.so")
+
+
+def gen_lib_path() -> str:
+    return os.path.join(BUILD_DIR, "libpycgen.so")
+
+
+def _run(cmd):
+    p = subprocess.run(cmd, capture_output=True, text=True)
+    if p.returncode != 0:
+        raise RuntimeError("build step failed: %s\n%s\n%s" % (" ".join(cmd), p.stdout, p.stderr))
+    return p
+
+
+def _newer(target, sources) -> bool:
+    if not os.path.exists(target):
+        return False
+    t = os.path.getmtime(target)
+    return all(os.path.getmtime(s) <= t for s in sources)
+
+
+def gen_cmd():
+    src = os.path.join(PKG_DIR, "inputs", "gen.c")
+    return [os.environ.get("CC", "gcc"), "-O2", "-std=c11", "-fPIC", "-shared", "-o",
+            gen_lib_path(), src, "-lm", "-lpthread"], [src]
+
+
+def pyc_cmd():
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
+    hdrs = sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
+        sorted(glob.glob(os.path.join(INCLUDE_DIR, "*.h")))
+    cmd = [os.environ.get("CXX", "g++"), "-O2", "-std=c++17", "-fPIC", "-shared",
+           "-Wall", "-Wno-unused-function", "-fvisibility=hidden",
+           "-I", INCLUDE_DIR, "-I", os.path.join(cuda_home(), "include"),
+           "-o", pyc_lib_path()] + srcs + ["-ldl", "-lpthread"]
+    return cmd, srcs + hdrs
+
+
+def build_gen(force=False):
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    cmd, deps = gen_cmd()
+    if force or not _newer(gen_lib_path(), deps):
+        _run(cmd)
+    return gen_lib_path()
+
+
+def build_pyc(force=False):
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    cmd, deps = pyc_cmd()
+    if force or not _newer(pyc_lib_path(), deps):
+        _run(cmd)
+    return pyc_lib_path()
+
+
+def build_all(force=False, jobs=None):
+    """Compile both libraries in parallel (independent translation units)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    steps = [(gen_lib_path(),) + gen_cmd(), (pyc_lib_path(),) + pyc_cmd()]
+    procs = []
+    for target, cmd, deps in steps:
+        if force or not _newer(target, deps):
+            procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
+                                                stderr=subprocess.PIPE, text=True)))
+    for cmd, p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("build step failed: %s\n%s\n%s" % (" ".join(cmd), out, err))
+
+
+if __name__ == "__main__":
+    build_all(force="--force" in sys.argv)
+    print("built", pyc_lib_path(), gen_lib_path())
