@@ -1,0 +1,239 @@
+/*
+ * pyc.h -- C ABI of the run-time specialised map and map-reduce library for
+ * GB300 (sm_103a).
+ *
+ * The operations follow Klockner et al., "GPU Scripting and Code Generation
+ * with PyCUDA":
+ *   - map (ElementwiseKernel, Sec. 3.2.4, Listing 3a): a C argument list plus a
+ *     statement (or ';'-separated statements) executed for every value of the
+ *     formal index i over arrays that all have the same length, in one pass
+ *     with no temporaries;
+ *   - map-reduce (ReductionKernel, Sec. 3.2.5, Listing 3b): a result type, a C
+ *     argument list, a map expression in i, a reduce expression in the two
+ *     formal values a and b, and an expression giving the neutral element;
+ *     the result stays in device memory;
+ *   - source is generated per specification, compiled at run time and cached
+ *     by a hash of the source (Sec. 2, Fig. 1; Sec. 3.3 on run-time code
+ *     generation and automated tuning);
+ *   - launches are asynchronous on an optional stream (Sec. 3.1) and take a
+ *     prepared argument layout (Sec. 3.1, prepared invocation).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a pyc_status and never aborts.  On failure
+ *     pyc_last_error() returns a message for the calling thread (for
+ *     compile errors it contains the compiler log).
+ *   - Device pointers are plain CUDA device addresses in the context that is
+ *     current on the calling thread (the primary context of the device if no
+ *     context is current).  The caller owns every buffer and stream passed in.
+ *   - A stream argument is a CUstream / cudaStream_t; NULL is the legacy
+ *     default stream.  Launches are enqueued and return immediately; device
+ *     faults surface at the caller's next synchronisation.
+ *   - Handles are safe to launch from several threads.  Creating a handle
+ *     needs no GPU (parse, generate, compile); the first launch on a device
+ *     loads the module there.
+ */
+#ifndef PYC_H
+#define PYC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PYC_VERSION_MAJOR 0
+#define PYC_VERSION_MINOR 1
+
+typedef struct CUstream_st* pyc_stream_t; /* same object as CUstream / cudaStream_t */
+typedef struct pyc_map* pyc_map_t;
+typedef struct pyc_reduce* pyc_reduce_t;
+
+typedef enum {
+  PYC_OK = 0,
+  PYC_E_PARSE = 1,    /* malformed argument spec, statement or expression */
+  PYC_E_COMPILE = 2,  /* run-time compilation failed; pyc_last_error() holds the log */
+  PYC_E_ARG = 3,      /* invalid argument (null or misaligned pointer, bad size, ...) */
+  PYC_E_CUDA = 4,     /* CUDA driver error, or no driver / device available */
+  PYC_E_NOMEM = 5,    /* device or host allocation failed, or over a memory budget */
+  PYC_E_BUSY = 6,     /* resource in use (e.g. a queue is full) */
+  PYC_E_TIMEOUT = 7,  /* a bounded wait ran out */
+  PYC_E_INTERNAL = 8, /* invariant violated inside the library */
+  PYC_E_NOTFOUND = 9  /* unknown id */
+} pyc_status;
+
+/* Element / result types.  ARGMIN_F32 and ARGMAX_F32 are (value, index) pairs
+ * laid out as pyc_argf32. */
+typedef enum {
+  PYC_F32 = 0,
+  PYC_F64 = 1,
+  PYC_BF16 = 2,
+  PYC_F16 = 3,
+  PYC_I32 = 4,
+  PYC_I64 = 5,
+  PYC_ARGMIN_F32 = 6,
+  PYC_ARGMAX_F32 = 7,
+  PYC_U8 = 8,
+  PYC_I8 = 9,
+  PYC_U32 = 10,
+  PYC_U64 = 11,
+  PYC_I16 = 12,
+  PYC_U16 = 13
+} pyc_dtype;
+
+/* Result of an ARGMIN_F32 / ARGMAX_F32 reduction (16 bytes). */
+typedef struct {
+  float v;
+  int32_t pad;
+  int64_t i;
+} pyc_argf32;
+
+/* Creation options.  Zero in a tuning field means "use the tuned value for
+ * the launch's size bucket, or the built-in default".  A NULL pyc_opts* means
+ * all zero. */
+typedef struct {
+  int block;            /* threads per CTA: 0 or a multiple of 32 in [32, 1024] */
+  int vec_bytes;        /* bytes per vector access: 0, 16 or 32 */
+  int items_per_thread; /* vector accesses per thread per tile (unroll): 0, 1, 2, 4 or 8 */
+  int compensated;      /* map-reduce only: 1 = compensated FP32 sum (two-sum per element,
+                           pairwise (sum, error) combine, binary64 final combine).  Needs
+                           result type F32 and reduce expression a+b. */
+  int fmad;             /* 1 = let the compiler contract a*b+c into FMA.  0 (default) =
+                           each +,-,* rounds as written, so results are reproducible
+                           bit-for-bit against IEEE binary32 evaluation of the source. */
+  const char* preamble; /* optional device code (helper functions, constants) placed
+                           before the kernel; NULL = none */
+} pyc_opts;
+
+/* Static description of one declared argument (for prepared invocation). */
+typedef struct {
+  const char* name;  /* owned by the handle */
+  int is_pointer;    /* 1 = array (device pointer), 0 = scalar passed by value */
+  int dtype;         /* pyc_dtype of the scalar or of the array element */
+  int elem_bytes;    /* size of the scalar / array element */
+  int scalar_offset; /* byte offset of a scalar inside the packed scalar block; -1 for arrays */
+  int pointer_slot;  /* index into the ptrs[] array for arrays; -1 for scalars */
+  int read;          /* array is read by the statement / map expression */
+  int written;       /* array is written by the statement */
+  int lifted;        /* array is only accessed as name[i], so it is moved through
+                        registers with vector loads / stores */
+} pyc_param_info;
+
+/* ------------------------------------------------------------------ errors */
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next pyc_* call on the same thread. */
+const char* pyc_last_error(void);
+
+/* Library version string, e.g. "pyc 0.1 (sm_103a)". */
+const char* pyc_version(void);
+
+/* ------------------------------------------------------------------ map */
+
+/* Create a map (ElementwiseKernel, Sec. 3.2.4, Listing 3a).
+ *   argspec  C parameter list, e.g. "float a, float *x, float b, float *y, float *z".
+ *            Types: float, double, int, unsigned, long long, unsigned long long,
+ *            short, unsigned short, signed char, unsigned char, (u)int{8,16,32,64}_t,
+ *            __nv_bfloat16 (bf16), __half (half).  bf16 / half storage is
+ *            read and computed in binary32 and rounded to nearest even on store.
+ *   stmt     statement(s) executed for each i in [0, n), e.g. "z[i] = a*x[i] + b*y[i]".
+ *            i (long long) and n (long long) are in scope; names starting with
+ *            "pyc_" are reserved.
+ *   name     kernel name used in diagnostics (may be NULL).
+ * On success *out owns the compiled module.  Errors: PYC_E_PARSE (spec or
+ * statement), PYC_E_COMPILE (log in pyc_last_error()), PYC_E_ARG. */
+pyc_status pyc_map_create(const char* argspec, const char* stmt, const char* name,
+                          const pyc_opts* opts, pyc_map_t* out);
+
+/* Launch a map over i in [0, n).
+ *   ptrs     one device pointer per array parameter, in declaration order; every
+ *            array must hold at least n elements.  Arrays may alias exactly (the
+ *            same pointer, as in Listing 1's in-place a[i] *= 2); partial overlap
+ *            is undefined.
+ *   scalars  the scalar parameters packed in declaration order, each at its
+ *            natural alignment (a C struct of the scalars; see pyc_param_info
+ *            scalar_offset); may be NULL if there are none.
+ *   stream   stream to enqueue on.
+ * n == 0 is a no-op.  Errors: PYC_E_ARG (n < 0, null or misaligned array),
+ * PYC_E_CUDA. */
+pyc_status pyc_map_launch(pyc_map_t h, int64_t n, void* const* ptrs, const void* scalars,
+                          pyc_stream_t stream);
+
+/* Number of declared parameters and their descriptions. */
+int pyc_map_num_params(pyc_map_t h);
+pyc_status pyc_map_param(pyc_map_t h, int idx, pyc_param_info* info);
+/* Size of the packed scalar block in bytes. */
+int pyc_map_scalar_bytes(pyc_map_t h);
+/* Generated CUDA source (owned by the handle). */
+const char* pyc_map_source(pyc_map_t h);
+
+/* Time the tuning candidates for n's size bucket on scratch buffers the library
+ * allocates and frees, remember the fastest for the handle and persist it in the
+ * tuning cache.  Synchronises the stream.  (Automated tuning, Sec. 3.3.1.) */
+pyc_status pyc_map_autotune(pyc_map_t h, int64_t n, pyc_stream_t stream);
+
+void pyc_map_destroy(pyc_map_t h);
+
+/* ------------------------------------------------------------------ map-reduce */
+
+/* Create a map-reduce (ReductionKernel, Sec. 3.2.5, Listing 3b).
+ *   out_dtype    result type; the reduction accumulates in this type, except
+ *                BF16/F16 results, which accumulate in binary32.
+ *   neutral      C expression of the neutral element, e.g. "0" (Sec. 3.2.5);
+ *                NULL for ARGMIN/ARGMAX selects (+-inf, INT64_MAX).
+ *   reduce_expr  C expression in a and b (both of the accumulation type), e.g.
+ *                "a+b"; must be associative and commutative.  NULL for
+ *                ARGMIN/ARGMAX selects "smaller (larger) value, then smaller index".
+ *   map_expr     C expression in i, e.g. "x[i]*y[i]"; NULL means "in[i]" for a
+ *                single-array spec.  For ARGMIN/ARGMAX it gives the value; the
+ *                index is i.
+ *   argspec      C parameter list as for pyc_map_create.
+ * Errors as for pyc_map_create. */
+pyc_status pyc_reduce_create(pyc_dtype out_dtype, const char* neutral, const char* reduce_expr,
+                             const char* map_expr, const char* argspec, const pyc_opts* opts,
+                             pyc_reduce_t* out);
+
+/* Reduce over i in [0, n) in one launch: every CTA folds its chunks, writes a
+ * partial, and the last CTA to finish combines the partials and writes the
+ * single result to d_out (one element of the result type).  No host round
+ * trip.  n == 0 writes the neutral element.  Launches of one handle on one
+ * stream are serialised by the stream; launches of one handle on different
+ * streams use separate workspaces.  The result is a fixed function of
+ * (n, tuning), independent of timing.  Errors as for pyc_map_launch. */
+pyc_status pyc_reduce_launch(pyc_reduce_t h, int64_t n, void* const* ptrs, const void* scalars,
+                             void* d_out, pyc_stream_t stream);
+
+/* Segmented map-reduce: nseg independent reductions in one persistent launch.
+ *   seg_offsets  HOST array of nseg+1 non-decreasing element offsets; segment s
+ *                covers [seg_offsets[s], seg_offsets[s+1]) of every array.
+ *   ptrs         base pointers of the concatenated arrays.
+ *   d_out        nseg results (device).
+ * The segment table is turned into a work list once (large segments split into
+ * chunks, small ones packed one per warp); the list and the launch are cached
+ * per (handle, table, pointers, scalars, output, stream) and replayed as a CUDA
+ * graph on later calls with the same arguments.  Empty segments get the neutral
+ * element.  Errors as for pyc_reduce_launch. */
+pyc_status pyc_reduce_batched(pyc_reduce_t h, int64_t nseg, const int64_t* seg_offsets,
+                              void* const* ptrs, const void* scalars, void* d_out,
+                              pyc_stream_t stream);
+
+int pyc_reduce_num_params(pyc_reduce_t h);
+pyc_status pyc_reduce_param(pyc_reduce_t h, int idx, pyc_param_info* info);
+int pyc_reduce_scalar_bytes(pyc_reduce_t h);
+/* Size in bytes of one result element (4, 8 or 16). */
+int pyc_reduce_out_bytes(pyc_reduce_t h);
+const char* pyc_reduce_source(pyc_reduce_t h);
+pyc_status pyc_reduce_autotune(pyc_reduce_t h, int64_t n, pyc_stream_t stream);
+void pyc_reduce_destroy(pyc_reduce_t h);
+
+/* ------------------------------------------------------------------ cache */
+
+/* Kernel cache statistics since process start: compiled = NVRTC compilations,
+ * disk_hits = modules read from the on-disk cache, mem_hits = in-memory hits.
+ * The on-disk cache lives in $PYC_CACHE_DIR (default $HOME/.cache/pyc). */
+void pyc_cache_stats(int64_t* compiled, int64_t* disk_hits, int64_t* mem_hits);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PYC_H */

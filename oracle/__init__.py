@@ -54,6 +54,8 @@ def _load():
             "orc_map_scale": (None, [i64, f64, vp, vp, vp]),
             "orc_map_add": (None, [i64, vp, vp, vp, vp]),
             "orc_map_lin_comb": (None, [i64, f64, vp, f64, vp, ctypes.c_int, vp, vp, vp]),
+            "orc_map_lin_comb_f32ops": (None, [i64, ctypes.c_float, vp, ctypes.c_float, vp,
+                                               ctypes.c_int, vp]),
             "orc_map_gauss_sin": (None, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
             "orc_map_gauss_sin_at": (None, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
             "orc_sum_f32": (f64, [i64, vp, vp]),
@@ -125,6 +127,17 @@ def map_lin_comb(a, x, b, y, out_bf16=False):
     _load().orc_map_lin_comb(x.size, float(a), _ptr(x), float(b), _ptr(y), int(out_bf16),
                              _ptr(z), _ptr(z64), _ptr(tab))
     return z, z64, tab
+
+
+def map_lin_comb_f32ops(a, x, b, y, out_bf16=False):
+    """Listing 3a evaluated as binary32 C source (each operation rounded, no
+    contraction); bfloat16 output rounds the binary32 value on the store."""
+    x, y = _f32(x), _f32(y)
+    assert x.size == y.size
+    z = np.empty_like(x)
+    _load().orc_map_lin_comb_f32ops(x.size, float(a), _ptr(x), float(b), _ptr(y), int(out_bf16),
+                                    _ptr(z))
+    return z
 
 
 def map_gauss_sin(x, y, u, w):

@@ -92,6 +92,20 @@ void orc_map_lin_comb(int64_t n, double a, const float* x, double b, const float
   }
 }
 
+/* Listing 3a as C source on binary32 operands: with the declared types every
+ * operation rounds to binary32 in source order (no contraction):
+ * z = RN32(RN32(a*x) + RN32(b*y)); out_bf16 = 1 rounds that binary32 value to
+ * bfloat16 on the store.  Inputs given as binary32 values. */
+void orc_map_lin_comb_f32ops(int64_t n, float a, const float* x, float b, const float* y,
+                             int out_bf16, float* z) {
+  for (int64_t i = 0; i < n; ++i) {
+    float p = a * x[i];
+    float q = b * y[i];
+    float v = p + q;
+    z[i] = out_bf16 ? (float)orc_round_bf16((double)v) : v;
+  }
+}
+
 /* The four-input map z[i] = x[i]*exp(-y[i]*y[i]) + sin(u[i])*w[i].
  * t1 and t2 receive the two top-level addends in binary64. */
 void orc_map_gauss_sin(int64_t n, const float* x, const float* y, const float* u,
@@ -200,23 +214,25 @@ float orc_min_f32(int64_t n, const float* x) {
   return m;
 }
 
-/* argmin / argmax with the first index winning ties: scanning upward and
- * replacing only on strict improvement keeps the first occurrence.  Neutral
- * (+inf / -inf, index -1) is returned for n == 0. */
+/* argmin / argmax (Sec. 3.2.5): the fold r = R(r, (x[i], i)) from the neutral
+ * element, where R keeps the smaller (larger) value and, on equal values, the
+ * smaller index.  The neutral element that makes R an identity is
+ * (+inf / -inf, INT64_MAX); it is the result for n == 0.  Scanning upward,
+ * the first occurrence of the extremum wins. */
 void orc_argmin_f32(int64_t n, const float* x, float* v, int64_t* idx) {
   float bv = INFINITY;
-  int64_t bi = -1;
+  int64_t bi = INT64_MAX;
   for (int64_t i = 0; i < n; ++i)
-    if (x[i] < bv || (bi < 0 && x[i] == bv)) { bv = x[i]; bi = i; }
+    if (x[i] < bv || (x[i] == bv && i < bi)) { bv = x[i]; bi = i; }
   *v = bv;
   *idx = bi;
 }
 
 void orc_argmax_f32(int64_t n, const float* x, float* v, int64_t* idx) {
   float bv = -INFINITY;
-  int64_t bi = -1;
+  int64_t bi = INT64_MAX;
   for (int64_t i = 0; i < n; ++i)
-    if (x[i] > bv || (bi < 0 && x[i] == bv)) { bv = x[i]; bi = i; }
+    if (x[i] > bv || (x[i] == bv && i < bi)) { bv = x[i]; bi = i; }
   *v = bv;
   *idx = bi;
 }

@@ -64,15 +64,32 @@ def gen_cmd():
             gen_lib_path(), src, "-lm", "-lpthread"], [src]
 
 
-def pyc_cmd():
+def _pyc_sources():
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
     hdrs = sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
+        sorted(glob.glob(os.path.join(CSRC, "*.inc"))) + \
         sorted(glob.glob(os.path.join(INCLUDE_DIR, "*.h")))
-    cmd = [os.environ.get("CXX", "g++"), "-O2", "-std=c++17", "-fPIC", "-shared",
-           "-Wall", "-Wno-unused-function", "-fvisibility=hidden",
-           "-I", INCLUDE_DIR, "-I", os.path.join(cuda_home(), "include"),
-           "-o", pyc_lib_path()] + srcs + ["-ldl", "-lpthread"]
-    return cmd, srcs + hdrs
+    return srcs, hdrs
+
+
+def _obj_path(src):
+    return os.path.join(BUILD_DIR, "obj", os.path.basename(src) + ".o")
+
+
+def pyc_compile_cmds():
+    """One compile command per translation unit (run in parallel)."""
+    srcs, hdrs = _pyc_sources()
+    base = [os.environ.get("CXX", "g++"), "-O2", "-std=c++17", "-fPIC",
+            "-Wall", "-Wno-unused-function", "-fvisibility=hidden",
+            "-I", INCLUDE_DIR, "-I", os.path.join(cuda_home(), "include")]
+    return [(_obj_path(s), base + ["-c", s, "-o", _obj_path(s)], [s] + hdrs) for s in srcs]
+
+
+def pyc_link_cmd():
+    srcs, _ = _pyc_sources()
+    objs = [_obj_path(s) for s in srcs]
+    return [os.environ.get("CXX", "g++"), "-shared", "-o", pyc_lib_path()] + objs + \
+        ["-ldl", "-lpthread"], objs
 
 
 def build_gen(force=False):
@@ -83,27 +100,37 @@ def build_gen(force=False):
     return gen_lib_path()
 
 
-def build_pyc(force=False):
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    cmd, deps = pyc_cmd()
-    if force or not _newer(pyc_lib_path(), deps):
-        _run(cmd)
-    return pyc_lib_path()
-
-
-def build_all(force=False, jobs=None):
-    """Compile both libraries in parallel (independent translation units)."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    steps = [(gen_lib_path(),) + gen_cmd(), (pyc_lib_path(),) + pyc_cmd()]
+def _run_parallel(steps, force):
     procs = []
     for target, cmd, deps in steps:
         if force or not _newer(target, deps):
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
                                                 stderr=subprocess.PIPE, text=True)))
+    errors = []
     for cmd, p in procs:
         out, err = p.communicate()
         if p.returncode != 0:
-            raise RuntimeError("build step failed: %s\n%s\n%s" % (" ".join(cmd), out, err))
+            errors.append("build step failed: %s\n%s\n%s" % (" ".join(cmd), out, err))
+    if errors:
+        raise RuntimeError("\n".join(errors))
+
+
+def build_pyc(force=False):
+    os.makedirs(os.path.join(BUILD_DIR, "obj"), exist_ok=True)
+    _run_parallel(pyc_compile_cmds(), force)
+    cmd, objs = pyc_link_cmd()
+    if force or not _newer(pyc_lib_path(), objs):
+        _run(cmd)
+    return pyc_lib_path()
+
+
+def build_all(force=False):
+    """Compile every native library; translation units build in parallel."""
+    os.makedirs(os.path.join(BUILD_DIR, "obj"), exist_ok=True)
+    _run_parallel([(gen_lib_path(),) + gen_cmd()] + pyc_compile_cmds(), force)
+    cmd, objs = pyc_link_cmd()
+    if force or not _newer(pyc_lib_path(), objs):
+        _run(cmd)
 
 
 if __name__ == "__main__":

@@ -1,0 +1,383 @@
+// C ABI: map and map-reduce creation and launches (see include/pyc.h).
+#include <algorithm>
+#include <cstring>
+
+#include "cudrv.h"
+#include "handles.h"
+
+namespace pyc {
+
+int size_bucket(int64_t n) {
+  int bl = 0;
+  for (uint64_t v = (uint64_t)(n > 0 ? n : 1); v; v >>= 1) ++bl;
+  return bl / 2;
+}
+
+LaunchCfg choose_cfg(HandleBase& h, int64_t n, bool reduce) {
+  LaunchCfg c;
+  c.v = reduce ? Variant{16, 4} : Variant{16, 4};
+  c.block = 256;
+  {
+    std::lock_guard<std::mutex> lk(h.tune.mu);
+    auto it = h.tune.by_bucket.find(size_bucket(n));
+    if (it != h.tune.by_bucket.end()) c = it->second;
+  }
+  if (h.opts.block) c.block = h.opts.block;
+  if (h.opts.vec_bytes) c.v.vec_bytes = h.opts.vec_bytes;
+  if (h.opts.items_per_thread) c.v.unroll = h.opts.items_per_thread;
+  return c;
+}
+
+std::vector<unsigned char> pack_args(const ArgSpec& spec, void* const* ptrs, const void* scalars) {
+  std::vector<unsigned char> a(spec.params.empty() ? 4 : spec.args_bytes, 0);
+  if (spec.num_ptrs > 0 && !ptrs) fail(PYC_E_ARG, "ptrs is NULL but the spec declares arrays");
+  if (spec.scalar_bytes > 0 && !scalars)
+    fail(PYC_E_ARG, "scalars is NULL but the spec declares scalar parameters");
+  const unsigned char* s = static_cast<const unsigned char*>(scalars);
+  for (auto& p : spec.params) {
+    if (p.is_ptr) {
+      void* v = ptrs[p.ptr_slot];
+      std::memcpy(&a[p.args_offset], &v, 8);
+    } else {
+      std::memcpy(&a[p.args_offset], s + p.scalar_offset, type_info(p.dtype).bytes);
+    }
+  }
+  return a;
+}
+
+int64_t vector_head(const ArgSpec& spec, void* const* ptrs, int vec_bytes, int min_bytes,
+                    int64_t n) {
+  bool any = false;
+  for (auto& p : spec.params) {
+    if (!(p.is_ptr && p.lifted)) continue;
+    uintptr_t a = reinterpret_cast<uintptr_t>(ptrs[p.ptr_slot]);
+    int sz = type_info(p.dtype).bytes;
+    if (n > 0 && a == 0) fail(PYC_E_ARG, "array '" + p.name + "' is NULL");
+    if (a % (uintptr_t)sz)
+      fail(PYC_E_ARG, "array '" + p.name + "' is not aligned to its element size");
+    any = true;
+  }
+  if (!any) return 0;
+  const int span = vec_bytes / min_bytes;
+  for (int h = 0; h < span; ++h) {
+    bool ok = true;
+    for (auto& p : spec.params) {
+      if (!(p.is_ptr && p.lifted)) continue;
+      uintptr_t a = reinterpret_cast<uintptr_t>(ptrs[p.ptr_slot]);
+      if ((a + (uintptr_t)h * type_info(p.dtype).bytes) % (uintptr_t)vec_bytes) {
+        ok = false;
+        break;
+      }
+    }
+    if (ok) return h < n ? h : -1;
+  }
+  return -1;
+}
+
+int resident_ctas(CUfunction f, int block) {
+  static std::mutex mu;
+  static std::map<std::pair<CUfunction, int>, int> cache;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({f, block});
+    if (it != cache.end()) return it->second;
+  }
+  int nb = 0;
+  PYC_CU(drv().cuOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, 0));
+  if (nb < 1) fail(PYC_E_ARG, "block size " + std::to_string(block) + " cannot be resident");
+  int r = nb * current_device_props().sm_count;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[{f, block}] = r;
+  return r;
+}
+
+ChunkPlan plan_chunks(int64_t n, int64_t head, int64_t tile, int resident) {
+  ChunkPlan p;
+  p.head = head;
+  int64_t body = n <= 0 ? 0 : (head >= 0 ? n - head : n);
+  if (body <= 0) {
+    p.chunk = tile;
+    p.nchunks = 0;
+    p.grid = 1;
+    return p;
+  }
+  auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
+  int64_t c = std::max<int64_t>(tile, cdiv(cdiv(body, resident), tile) * tile);
+  if (cdiv(body, c) > kMaxChunks) c = cdiv(cdiv(body, kMaxChunks), tile) * tile;
+  p.chunk = c;
+  p.nchunks = cdiv(body, c);
+  p.grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, p.nchunks));
+  return p;
+}
+
+namespace {
+
+void check_cfg(const LaunchCfg& c) {
+  bool vb = c.v.vec_bytes == 16 || c.v.vec_bytes == 32;
+  bool un = c.v.unroll == 1 || c.v.unroll == 2 || c.v.unroll == 4;
+  if (!vb) fail(PYC_E_ARG, "vec_bytes must be 16 or 32");
+  if (!un) fail(PYC_E_ARG, "items_per_thread must be 1, 2 or 4");
+  if (c.block < 32 || c.block > 512 || c.block % 32)
+    fail(PYC_E_ARG, "block must be a multiple of 32 in [32, 512]");
+}
+
+pyc_opts opts_or_zero(const pyc_opts* o) {
+  pyc_opts z{};
+  if (o) z = *o;
+  return z;
+}
+
+void check_opts(const pyc_opts& o) {
+  if (o.block && (o.block < 32 || o.block > 512 || o.block % 32))
+    fail(PYC_E_ARG, "opts.block must be 0 or a multiple of 32 in [32, 512]");
+  if (o.vec_bytes && o.vec_bytes != 16 && o.vec_bytes != 32)
+    fail(PYC_E_ARG, "opts.vec_bytes must be 0, 16 or 32");
+  if (o.items_per_thread && o.items_per_thread != 1 && o.items_per_thread != 2 &&
+      o.items_per_thread != 4)
+    fail(PYC_E_ARG, "opts.items_per_thread must be 0, 1, 2 or 4");
+}
+
+void finish_handle(HandleBase& h, bool reduce) {
+  h.min_bytes = lifted_min_bytes(h.spec);
+  h.mod = get_module(h.source, h.opts.fmad != 0);
+  h.tune_key = digest(h.source + (h.opts.fmad ? "|fmad" : ""));
+  h.param_names.clear();
+  for (auto& p : h.spec.params) h.param_names.push_back(p.name);
+  tune_cache_load(h, reduce);
+}
+
+void fill_param(const HandleBase& h, int idx, pyc_param_info* info) {
+  if (!info) fail(PYC_E_ARG, "info is NULL");
+  if (idx < 0 || idx >= (int)h.spec.params.size()) fail(PYC_E_ARG, "parameter index out of range");
+  const Param& p = h.spec.params[idx];
+  info->name = h.param_names[idx].c_str();
+  info->is_pointer = p.is_ptr;
+  info->dtype = p.dtype;
+  info->elem_bytes = type_info(p.dtype).bytes;
+  info->scalar_offset = p.scalar_offset;
+  info->pointer_slot = p.ptr_slot;
+  info->read = p.read;
+  info->written = p.written;
+  info->lifted = p.lifted;
+}
+
+}  // namespace
+
+void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
+                const void* scalars, CUstream stream) {
+  check_cfg(cfg);
+  if (n < 0) fail(PYC_E_ARG, "n must be >= 0");
+  std::vector<unsigned char> args = pack_args(h->spec, ptrs, scalars);
+  int64_t head = vector_head(h->spec, ptrs, cfg.v.vec_bytes, h->min_bytes, n);
+  if (n == 0) return;
+  CUfunction f = h->mod->function("pyc_map_" + variant_suffix(cfg.v));
+  int resident = resident_ctas(f, cfg.block);
+  int64_t tile = (int64_t)cfg.block * (cfg.v.vec_bytes / h->min_bytes) * cfg.v.unroll;
+  int64_t nfull = head >= 0 ? (n - head) / tile : 0;
+  int64_t want = nfull > 0 ? nfull : (n + cfg.block - 1) / cfg.block;
+  unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, want));
+  void* params[] = {args.data(), &n, &head};
+  PYC_CU(drv().cuLaunchKernel(f, grid, 1, 1, (unsigned)cfg.block, 1, 1, 0, stream, params,
+                              nullptr));
+}
+
+namespace {
+
+pyc_reduce::Workspace& workspace(pyc_reduce* h, CUstream stream) {
+  CUcontext ctx = ensure_context();
+  std::lock_guard<std::mutex> lk(h->ws_mu);
+  auto key = std::make_pair(ctx, stream);
+  auto it = h->ws.find(key);
+  if (it != h->ws.end()) return it->second;
+  pyc_reduce::Workspace w;
+  size_t part_bytes = (size_t)kMaxChunks * h->gen.acc_bytes;
+  size_t total = part_bytes + 256;
+  PYC_CU(drv().cuMemAlloc(&w.base, total));
+  w.part = w.base;
+  w.ticket = w.base + part_bytes;
+  PYC_CU(drv().cuMemsetD8Async(w.ticket, 0, 256, stream));
+  return h->ws.emplace(key, w).first->second;
+}
+
+}  // namespace
+
+void launch_reduce(pyc_reduce* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
+                   const void* scalars, void* d_out, CUstream stream) {
+  check_cfg(cfg);
+  if (n < 0) fail(PYC_E_ARG, "n must be >= 0");
+  if (!d_out) fail(PYC_E_ARG, "d_out is NULL");
+  if (reinterpret_cast<uintptr_t>(d_out) % (uintptr_t)std::min(h->gen.out_bytes, 8))
+    fail(PYC_E_ARG, "d_out is not aligned to the result type");
+  std::vector<unsigned char> args = pack_args(h->spec, ptrs, scalars);
+  int64_t head = vector_head(h->spec, ptrs, cfg.v.vec_bytes, h->min_bytes, n);
+  CUfunction f = h->mod->function("pyc_reduce_" + variant_suffix(cfg.v));
+  int resident = resident_ctas(f, cfg.block);
+  int64_t tile = (int64_t)cfg.block * (cfg.v.vec_bytes / h->min_bytes) * cfg.v.unroll;
+  ChunkPlan cp = plan_chunks(n, head, tile, resident);
+  pyc_reduce::Workspace& w = workspace(h, stream);
+  void* params[] = {args.data(), &n, &cp.head, &cp.chunk, &cp.nchunks, &w.part, &w.ticket, &d_out};
+  PYC_CU(drv().cuLaunchKernel(f, (unsigned)cp.grid, 1, 1, (unsigned)cfg.block, 1, 1, 0, stream,
+                              params, nullptr));
+}
+
+}  // namespace pyc
+
+using namespace pyc;
+
+// ------------------------------------------------------------------ map
+
+PYC_API pyc_status pyc_map_create(const char* argspec, const char* stmt, const char* name,
+                                  const pyc_opts* opts, pyc_map_t* out) {
+  return guarded([&] {
+    if (!out) fail(PYC_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!argspec) fail(PYC_E_ARG, "argspec is NULL");
+    if (!stmt) fail(PYC_E_ARG, "stmt is NULL");
+    auto h = std::make_unique<pyc_map>();
+    h->opts = opts_or_zero(opts);
+    check_opts(h->opts);
+    if (h->opts.compensated) fail(PYC_E_ARG, "opts.compensated applies to map-reduce only");
+    h->preamble = h->opts.preamble ? h->opts.preamble : "";
+    h->opts.preamble = nullptr;
+    h->name = name ? name : "map";
+    h->spec = parse_argspec(argspec);
+    std::string rw = analyze_and_rewrite(h->spec, stmt, false);
+    h->source = generate_map(h->spec, rw, h->preamble).source;
+    finish_handle(*h, false);
+    *out = h.release();
+  });
+}
+
+PYC_API pyc_status pyc_map_launch(pyc_map_t h, int64_t n, void* const* ptrs, const void* scalars,
+                                  pyc_stream_t stream) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    LaunchCfg cfg = choose_cfg(*h, n, false);
+    launch_map(h, cfg, n, ptrs, scalars, reinterpret_cast<CUstream>(stream));
+  });
+}
+
+PYC_API int pyc_map_num_params(pyc_map_t h) { return h ? (int)h->spec.params.size() : -1; }
+
+PYC_API pyc_status pyc_map_param(pyc_map_t h, int idx, pyc_param_info* info) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    fill_param(*h, idx, info);
+  });
+}
+
+PYC_API int pyc_map_scalar_bytes(pyc_map_t h) { return h ? h->spec.scalar_bytes : -1; }
+
+PYC_API const char* pyc_map_source(pyc_map_t h) { return h ? h->source.c_str() : ""; }
+
+PYC_API void pyc_map_destroy(pyc_map_t h) { delete h; }
+
+// ------------------------------------------------------------------ map-reduce
+
+PYC_API pyc_status pyc_reduce_create(pyc_dtype out_dtype, const char* neutral,
+                                     const char* reduce_expr, const char* map_expr,
+                                     const char* argspec, const pyc_opts* opts,
+                                     pyc_reduce_t* out) {
+  return guarded([&] {
+    if (!out) fail(PYC_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!argspec) fail(PYC_E_ARG, "argspec is NULL");
+    auto h = std::make_unique<pyc_reduce>();
+    h->opts = opts_or_zero(opts);
+    check_opts(h->opts);
+    h->preamble = h->opts.preamble ? h->opts.preamble : "";
+    h->opts.preamble = nullptr;
+    h->name = "reduce";
+    h->out_dtype = out_dtype;
+    (void)type_info(out_dtype);  // validates the enum
+    switch (out_dtype) {
+      case PYC_F32: case PYC_F64: case PYC_BF16: case PYC_F16: case PYC_I32: case PYC_I64:
+      case PYC_U32: case PYC_U64: case PYC_ARGMIN_F32: case PYC_ARGMAX_F32:
+        break;
+      default:
+        fail(PYC_E_ARG, "unsupported result type for a map-reduce");
+    }
+    h->spec = parse_argspec(argspec);
+    std::string mexpr;
+    if (map_expr) {
+      mexpr = map_expr;
+    } else {
+      if (h->spec.num_ptrs != 1) fail(PYC_E_ARG, "map_expr may be NULL only for one array");
+      for (auto& p : h->spec.params)
+        if (p.is_ptr) mexpr = p.name + "[i]";
+    }
+    check_expression(mexpr, "map expression");
+    std::string mrw = analyze_and_rewrite(h->spec, mexpr, true);
+    bool arg = out_dtype == PYC_ARGMIN_F32 || out_dtype == PYC_ARGMAX_F32;
+    std::string neu, red;
+    if (arg) {
+      h->kind = ReduceKind::Arg;
+      if (h->opts.compensated) fail(PYC_E_ARG, "compensated needs an F32 result");
+      if (neutral) fail(PYC_E_ARG, "ARGMIN/ARGMAX use the built-in neutral element (pass NULL)");
+      bool mn = out_dtype == PYC_ARGMIN_F32;
+      neu = std::string("pyc_argf32{") + (mn ? "INFINITY" : "-INFINITY") + ", 0, LLONG_MAX}";
+      red = reduce_expr ? check_expression(reduce_expr, "reduce expression")
+                        : (mn ? "(b.v < a.v || (b.v == a.v && b.i < a.i)) ? b : a"
+                              : "(b.v > a.v || (b.v == a.v && b.i < a.i)) ? b : a");
+    } else {
+      if (!neutral) fail(PYC_E_ARG, "neutral is NULL");
+      if (!reduce_expr) fail(PYC_E_ARG, "reduce_expr is NULL");
+      neu = check_expression(neutral, "neutral expression");
+      red = check_expression(reduce_expr, "reduce expression");
+      if (h->opts.compensated) {
+        if (out_dtype != PYC_F32) fail(PYC_E_ARG, "compensated needs an F32 result");
+        std::string r;
+        for (char c : red)
+          if (c != ' ') r += c;
+        if (r != "a+b" && r != "b+a") fail(PYC_E_ARG, "compensated needs the reduce expression a+b");
+        h->kind = ReduceKind::Compensated;
+      }
+    }
+    h->gen = generate_reduce(h->spec, out_dtype, h->kind, neu, red, mrw, h->preamble);
+    h->source = h->gen.source;
+    finish_handle(*h, true);
+    *out = h.release();
+  });
+}
+
+PYC_API pyc_status pyc_reduce_launch(pyc_reduce_t h, int64_t n, void* const* ptrs,
+                                     const void* scalars, void* d_out, pyc_stream_t stream) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    LaunchCfg cfg = choose_cfg(*h, n, true);
+    launch_reduce(h, cfg, n, ptrs, scalars, d_out, reinterpret_cast<CUstream>(stream));
+  });
+}
+
+PYC_API pyc_status pyc_reduce_batched(pyc_reduce_t h, int64_t nseg, const int64_t* seg_offsets,
+                                      void* const* ptrs, const void* scalars, void* d_out,
+                                      pyc_stream_t stream) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    reduce_batched(h, nseg, seg_offsets, ptrs, scalars, d_out, reinterpret_cast<CUstream>(stream));
+  });
+}
+
+PYC_API int pyc_reduce_num_params(pyc_reduce_t h) { return h ? (int)h->spec.params.size() : -1; }
+
+PYC_API pyc_status pyc_reduce_param(pyc_reduce_t h, int idx, pyc_param_info* info) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    fill_param(*h, idx, info);
+  });
+}
+
+PYC_API int pyc_reduce_scalar_bytes(pyc_reduce_t h) { return h ? h->spec.scalar_bytes : -1; }
+PYC_API int pyc_reduce_out_bytes(pyc_reduce_t h) { return h ? h->gen.out_bytes : -1; }
+PYC_API const char* pyc_reduce_source(pyc_reduce_t h) { return h ? h->source.c_str() : ""; }
+
+PYC_API void pyc_reduce_destroy(pyc_reduce_t h) {
+  if (!h) return;
+  try {
+    free_plans(h);
+    for (auto& kv : h->ws)
+      if (kv.second.base) drv().cuMemFree(kv.second.base);
+  } catch (...) {
+  }
+  delete h;
+}

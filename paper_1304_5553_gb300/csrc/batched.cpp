@@ -1,0 +1,259 @@
+// Segmented (batched) map-reduce: many independent reductions in one
+// persistent launch over a work list, replayed as a CUDA graph.
+//
+// Plan (built once per segment table, pointers, scalars, output and stream):
+//  * every segment becomes a task record (its own offset pointers, length,
+//    alignment head, chunk length, output slot);
+//  * segments of at most kSmall elements are reduced by one warp each; they are
+//    packed into "bundles" of blockDim/32 tasks, one CTA item per bundle;
+//  * longer segments are cut into chunks of kChunk elements (a multiple of the
+//    tile); one CTA item per chunk, longest segments first; the last chunk of a
+//    segment to finish (per-segment ticket) combines its partials in order;
+//  * CTAs pull items from an atomic counter, which the last CTA to leave
+//    resets, so replays need no memset.
+// The launch is captured once into a graph on a private stream and replayed on
+// the caller's stream; while the caller's stream is itself being captured the
+// kernel is launched directly so it becomes part of the caller's graph.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "cudrv.h"
+#include "handles.h"
+
+namespace pyc {
+
+namespace {
+constexpr int64_t kSmall = 2048;           // segments up to this length: one warp each
+constexpr int64_t kChunkElems = 1 << 16;   // chunk length of long segments (rounded to tiles)
+constexpr size_t kMaxPlans = 8;
+}  // namespace
+
+struct BatchPlan {
+  std::string key;
+  CUcontext ctx = nullptr;
+  CUdeviceptr mem = 0;
+  CUdeviceptr tasks = 0, items = 0, tickets = 0, ctl = 0, part = 0;
+  int nitems = 0;
+  int grid = 1;
+  LaunchCfg cfg;
+  CUfunction f = nullptr;
+  CUgraph graph = nullptr;
+  CUgraphExec exec = nullptr;
+
+  void launch_direct(CUstream s) {
+    void* params[] = {&tasks, &items, &nitems, &part, &tickets, &ctl};
+    PYC_CU(drv().cuLaunchKernel(f, (unsigned)grid, 1, 1, (unsigned)cfg.block, 1, 1, 0, s, params,
+                                nullptr));
+  }
+  void release() {
+    const Driver& d = drv();
+    if (exec) d.cuGraphExecDestroy(exec);
+    if (graph) d.cuGraphDestroy(graph);
+    if (mem) d.cuMemFree(mem);
+    exec = nullptr;
+    graph = nullptr;
+    mem = 0;
+  }
+};
+
+namespace {
+
+// One private non-blocking stream per context, used only for graph capture.
+CUstream capture_stream() {
+  static std::mutex mu;
+  static std::map<CUcontext, CUstream> streams;
+  CUcontext ctx = ensure_context();
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = streams.find(ctx);
+  if (it != streams.end()) return it->second;
+  CUstream s;
+  PYC_CU(drv().cuStreamCreate(&s, CU_STREAM_NON_BLOCKING));
+  streams[ctx] = s;
+  return s;
+}
+
+struct Item {
+  int32_t task, chunk, count, pad;
+};
+
+std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t* off,
+                                      void* const* ptrs, const void* scalars, void* d_out,
+                                      const LaunchCfg& cfg) {
+  const ArgSpec& spec = h->spec;
+  const ReduceGen& g = h->gen;
+  auto plan = std::make_unique<BatchPlan>();
+  plan->cfg = cfg;
+  plan->ctx = ensure_context();
+  const int E = cfg.v.vec_bytes / h->min_bytes;
+  const int64_t tile = (int64_t)cfg.block * E * cfg.v.unroll;
+  const int64_t chunk = std::max<int64_t>(tile, (kChunkElems + tile - 1) / tile * tile);
+  const int wpb = cfg.block / 32;
+
+  // task order: small segments first (consecutive, for bundles), then long ones
+  std::vector<int64_t> small, large;
+  for (int64_t s = 0; s < nseg; ++s) (off[s + 1] - off[s] <= kSmall ? small : large).push_back(s);
+  std::stable_sort(large.begin(), large.end(), [&](int64_t a, int64_t b) {
+    return off[a + 1] - off[a] > off[b + 1] - off[b];
+  });
+  std::vector<int64_t> order(small);
+  order.insert(order.end(), large.begin(), large.end());
+
+  std::vector<unsigned char> tasks((size_t)nseg * g.task_bytes, 0);
+  std::vector<Item> items;
+  std::vector<void*> tptrs(spec.num_ptrs ? spec.num_ptrs : 1);
+  int64_t slots = 0;
+  for (int64_t t = 0; t < nseg; ++t) {
+    const int64_t s = order[t];
+    const int64_t len = off[s + 1] - off[s];
+    for (auto& p : spec.params)
+      if (p.is_ptr)
+        tptrs[p.ptr_slot] = static_cast<char*>(ptrs[p.ptr_slot]) + off[s] * type_info(p.dtype).bytes;
+    std::vector<unsigned char> args = pack_args(spec, tptrs.data(), scalars);
+    int64_t head = vector_head(spec, tptrs.data(), cfg.v.vec_bytes, h->min_bytes, len);
+    unsigned char* rec = &tasks[(size_t)t * g.task_bytes];
+    std::memcpy(rec, args.data(), args.size());
+    int64_t tchunk, nch;
+    if (len <= kSmall) {
+      tchunk = std::max<int64_t>(len, 1);
+      nch = 0;
+    } else {
+      int64_t body = head >= 0 ? len - head : len;
+      tchunk = chunk;
+      nch = (body + chunk - 1) / chunk;
+    }
+    int32_t nchunks = (int32_t)nch, slot0 = 0;
+    if (nch > 1) {
+      slot0 = (int32_t)slots;
+      slots += nch;
+    }
+    void* out = static_cast<char*>(d_out) + s * g.out_bytes;
+    std::memcpy(rec + g.task_off_n, &len, 8);
+    std::memcpy(rec + g.task_off_head, &head, 8);
+    std::memcpy(rec + g.task_off_chunk, &tchunk, 8);
+    std::memcpy(rec + g.task_off_out, &out, 8);
+    std::memcpy(rec + g.task_off_nchunks, &nchunks, 4);
+    std::memcpy(rec + g.task_off_slot0, &slot0, 4);
+  }
+  if (slots > (int64_t)INT32_MAX) fail(PYC_E_ARG, "too many chunks in one batch");
+  // CTA items: long segments first, chunk-major
+  for (int64_t t = (int64_t)small.size(); t < nseg; ++t) {
+    int32_t nchunks;
+    std::memcpy(&nchunks, &tasks[(size_t)t * g.task_bytes + g.task_off_nchunks], 4);
+    for (int32_t c = 0; c < nchunks; ++c) items.push_back({(int32_t)t, c, 1, 0});
+  }
+  for (int64_t t = 0; t < (int64_t)small.size(); t += wpb) {
+    int32_t cnt = (int32_t)std::min<int64_t>(wpb, (int64_t)small.size() - t);
+    items.push_back({(int32_t)t, -1, cnt, 0});
+  }
+  plan->nitems = (int)items.size();
+
+  auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+  size_t b_tasks = up(tasks.size()), b_items = up(items.size() * sizeof(Item));
+  size_t b_tickets = up((size_t)nseg * 4), b_ctl = 256;
+  size_t b_part = up((size_t)std::max<int64_t>(slots, 1) * g.acc_bytes);
+  const Driver& d = drv();
+  PYC_CU(d.cuMemAlloc(&plan->mem, b_tasks + b_items + b_tickets + b_ctl + b_part));
+  plan->tasks = plan->mem;
+  plan->items = plan->tasks + b_tasks;
+  plan->tickets = plan->items + b_items;
+  plan->ctl = plan->tickets + b_tickets;
+  plan->part = plan->ctl + b_ctl;
+  if (!tasks.empty()) PYC_CU(d.cuMemcpyHtoD(plan->tasks, tasks.data(), tasks.size()));
+  if (!items.empty()) PYC_CU(d.cuMemcpyHtoD(plan->items, items.data(), items.size() * sizeof(Item)));
+  PYC_CU(d.cuMemsetD8(plan->tickets, 0, b_tickets + b_ctl));
+
+  plan->f = h->mod->function("pyc_rbatch_" + variant_suffix(cfg.v));
+  int resident = resident_ctas(plan->f, cfg.block);
+  plan->grid = std::max(1, std::min(resident, plan->nitems));
+
+  CUstream cs = capture_stream();
+  PYC_CU(d.cuStreamBeginCapture(cs, CU_STREAM_CAPTURE_MODE_THREAD_LOCAL));
+  try {
+    plan->launch_direct(cs);
+  } catch (...) {
+    CUgraph tmp = nullptr;
+    d.cuStreamEndCapture(cs, &tmp);
+    if (tmp) d.cuGraphDestroy(tmp);
+    plan->release();
+    throw;
+  }
+  PYC_CU(d.cuStreamEndCapture(cs, &plan->graph));
+  PYC_CU(d.cuGraphInstantiateWithFlags(&plan->exec, plan->graph, 0));
+  return plan;
+}
+
+}  // namespace
+
+void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const* ptrs,
+                    const void* scalars, void* d_out, CUstream stream) {
+  if (nseg < 0) fail(PYC_E_ARG, "nseg must be >= 0");
+  if (nseg == 0) return;
+  if (nseg > (int64_t)INT32_MAX / 2) fail(PYC_E_ARG, "too many segments");
+  if (!off) fail(PYC_E_ARG, "seg_offsets is NULL");
+  if (!d_out) fail(PYC_E_ARG, "d_out is NULL");
+  if (reinterpret_cast<uintptr_t>(d_out) % (uintptr_t)std::min(h->gen.out_bytes, 8))
+    fail(PYC_E_ARG, "d_out is not aligned to the result type");
+  if (off[0] < 0) fail(PYC_E_ARG, "seg_offsets[0] must be >= 0");
+  for (int64_t s = 0; s < nseg; ++s)
+    if (off[s + 1] < off[s]) fail(PYC_E_ARG, "seg_offsets must be non-decreasing");
+  LaunchCfg cfg = choose_cfg(*h, kSmall, true);
+  if (!h->opts.items_per_thread) cfg.v.unroll = 1;
+  if (!h->opts.block) cfg.block = 256;
+
+  // key: everything the plan bakes in
+  std::string k;
+  CUcontext ctx = ensure_context();
+  k.append(reinterpret_cast<const char*>(&ctx), sizeof(ctx));
+  k.append(reinterpret_cast<const char*>(&cfg), sizeof(cfg));
+  k.append(reinterpret_cast<const char*>(&d_out), sizeof(d_out));
+  k.append(reinterpret_cast<const char*>(off), (size_t)(nseg + 1) * 8);
+  if (h->spec.num_ptrs) k.append(reinterpret_cast<const char*>(ptrs), (size_t)h->spec.num_ptrs * 8);
+  if (h->spec.scalar_bytes && scalars)
+    k.append(reinterpret_cast<const char*>(scalars), (size_t)h->spec.scalar_bytes);
+  std::string key = digest(k) + std::to_string(k.size());
+
+  BatchPlan* plan = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(h->plan_mu);
+    for (size_t j = 0; j < h->plans.size(); ++j)
+      if (h->plans[j]->key == key) {
+        std::unique_ptr<BatchPlan> p = std::move(h->plans[j]);
+        h->plans.erase(h->plans.begin() + (long)j);
+        h->plans.push_back(std::move(p));
+        plan = h->plans.back().get();
+        break;
+      }
+    if (!plan) {
+      std::unique_ptr<BatchPlan> p = build_plan(h, nseg, off, ptrs, scalars, d_out, cfg);
+      p->key = key;
+      h->plans.push_back(std::move(p));
+      while (h->plans.size() > kMaxPlans) {
+        h->plans.front()->release();
+        h->plans.erase(h->plans.begin());
+      }
+      plan = h->plans.back().get();
+    }
+  }
+  CUstreamCaptureStatus cap = CU_STREAM_CAPTURE_STATUS_NONE;
+  if (stream) PYC_CU(drv().cuStreamIsCapturing(stream, &cap));
+  if (cap == CU_STREAM_CAPTURE_STATUS_ACTIVE)
+    plan->launch_direct(stream);
+  else
+    PYC_CU(drv().cuGraphLaunch(plan->exec, stream));
+}
+
+}  // namespace pyc
+
+pyc_reduce::pyc_reduce() = default;
+pyc_reduce::~pyc_reduce() = default;
+
+namespace pyc {
+
+void free_plans(pyc_reduce* h) {
+  std::lock_guard<std::mutex> lk(h->plan_mu);
+  for (auto& p : h->plans) p->release();
+  h->plans.clear();
+}
+
+}  // namespace pyc

@@ -1,0 +1,718 @@
+// Source generation for map and map-reduce kernels (see codegen.h).
+//
+// Kernel design (GB300, sm_103a; the path is HBM-bound, so no tensor cores):
+//  * map: persistent grid-stride CTAs over tiles of blockDim * E * U elements.
+//    Thread t of a tile owns U groups of E consecutive elements, group u at
+//    tile_base + (u * blockDim + t) * E, so each vector instruction of a warp
+//    covers one contiguous, fully coalesced span.  Lifted arrays move through
+//    registers with 16- or 32-byte loads/stores (L1 no-allocate); the user
+//    statement runs once per element on the register copies; a scalar loop
+//    covers the unaligned head and the ragged tail.
+//  * map-reduce: the index range is cut into chunks (a multiple of the tile).
+//    A CTA folds a chunk with up to E*U independent accumulators per thread
+//    (short serial chains; at most 128 bytes of them), combines them pairwise, then a warp-shuffle tree and a
+//    shared-memory tree give the chunk's partial.  The last CTA to finish
+//    (atomic ticket after a fence) combines the partials in index order and
+//    writes the result: one launch, no host round trip.  Every order is a
+//    fixed function of (n, tuning), so results are reproducible.
+//  * batched map-reduce: one persistent launch over a work list of CTA items
+//    (chunks of large segments) and warp bundles (one small segment per warp);
+//    a per-segment ticket lets the last chunk of each segment finish it.
+#include "codegen.h"
+
+#include <sstream>
+
+namespace pyc {
+
+namespace {
+
+const char* kPrelude = R"PYC(
+// ---------------------------------------------------------------- pyc prelude
+typedef long long pyc_i64;
+typedef unsigned long long pyc_u64;
+#ifndef INFINITY
+#define INFINITY __int_as_float(0x7f800000)
+#endif
+#ifndef NAN
+#define NAN __int_as_float(0x7fffffff)
+#endif
+#ifndef HUGE_VALF
+#define HUGE_VALF INFINITY
+#endif
+#ifndef FLT_MAX
+#define FLT_MAX 3.402823466e+38F
+#endif
+#ifndef FLT_MIN
+#define FLT_MIN 1.175494351e-38F
+#endif
+#ifndef DBL_MAX
+#define DBL_MAX 1.7976931348623158e+308
+#endif
+#ifndef INT_MAX
+#define INT_MAX 2147483647
+#endif
+#ifndef INT_MIN
+#define INT_MIN (-2147483647 - 1)
+#endif
+#ifndef UINT_MAX
+#define UINT_MAX 4294967295U
+#endif
+#ifndef LLONG_MAX
+#define LLONG_MAX 9223372036854775807LL
+#endif
+#ifndef LLONG_MIN
+#define LLONG_MIN (-9223372036854775807LL - 1LL)
+#endif
+#ifndef ULLONG_MAX
+#define ULLONG_MAX 18446744073709551615ULL
+#endif
+
+// bfloat16 / binary16 storage: read as binary32, rounded to nearest even on
+// assignment (hardware cvt.rn).
+__device__ __forceinline__ unsigned short pyc_f32_to_bf16_bits(float f) {
+  unsigned short h;
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(f));
+  return h;
+}
+__device__ __forceinline__ unsigned short pyc_f32_to_f16_bits(float f) {
+  unsigned short h;
+  asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
+  return h;
+}
+__device__ __forceinline__ float pyc_f16_bits_to_f32(unsigned short h) {
+  float f;
+  asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
+  return f;
+}
+
+struct pyc_bf16 {
+  unsigned short bits;
+  pyc_bf16() = default;
+  __device__ __forceinline__ pyc_bf16(float f) : bits(pyc_f32_to_bf16_bits(f)) {}
+  __device__ __forceinline__ operator float() const { return __uint_as_float(((unsigned)bits) << 16); }
+  __device__ __forceinline__ pyc_bf16& operator=(float f) { bits = pyc_f32_to_bf16_bits(f); return *this; }
+  __device__ __forceinline__ pyc_bf16& operator+=(float f) { return *this = float(*this) + f; }
+  __device__ __forceinline__ pyc_bf16& operator-=(float f) { return *this = float(*this) - f; }
+  __device__ __forceinline__ pyc_bf16& operator*=(float f) { return *this = float(*this) * f; }
+  __device__ __forceinline__ pyc_bf16& operator/=(float f) { return *this = float(*this) / f; }
+};
+
+struct pyc_f16 {
+  unsigned short bits;
+  pyc_f16() = default;
+  __device__ __forceinline__ pyc_f16(float f) : bits(pyc_f32_to_f16_bits(f)) {}
+  __device__ __forceinline__ operator float() const { return pyc_f16_bits_to_f32(bits); }
+  __device__ __forceinline__ pyc_f16& operator=(float f) { bits = pyc_f32_to_f16_bits(f); return *this; }
+  __device__ __forceinline__ pyc_f16& operator+=(float f) { return *this = float(*this) + f; }
+  __device__ __forceinline__ pyc_f16& operator-=(float f) { return *this = float(*this) - f; }
+  __device__ __forceinline__ pyc_f16& operator*=(float f) { return *this = float(*this) * f; }
+  __device__ __forceinline__ pyc_f16& operator/=(float f) { return *this = float(*this) / f; }
+};
+
+// (value, index) pair of argmin / argmax reductions (16 bytes).
+struct pyc_argf32 {
+  float v;
+  int pad;
+  long long i;
+};
+
+// compensated binary32 accumulator: value s plus running error c.
+struct pyc_cf32 {
+  float s;
+  float c;
+};
+
+// Wide global accesses.  Loads skip L1 allocation (streamed once).
+template <int B> struct pyc_vio;
+template <> struct pyc_vio<16> {
+  static __device__ __forceinline__ void ld(void* d, const void* s) {
+    unsigned* r = reinterpret_cast<unsigned*>(d);
+    asm volatile("ld.global.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "l"(s));
+  }
+  static __device__ __forceinline__ void st(void* d, const void* s) {
+    const unsigned* r = reinterpret_cast<const unsigned*>(s);
+    asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};"
+                 :: "l"(d), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
+  }
+};
+template <> struct pyc_vio<32> {
+  static __device__ __forceinline__ void ld(void* d, const void* s) {
+    unsigned* r = reinterpret_cast<unsigned*>(d);
+    asm volatile("ld.global.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]),
+                   "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "l"(s));
+  }
+  static __device__ __forceinline__ void st(void* d, const void* s) {
+    const unsigned* r = reinterpret_cast<const unsigned*>(s);
+    asm volatile("st.global.v8.u32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "l"(d), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]),
+                    "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]) : "memory");
+  }
+};
+// G bytes in pieces of P bytes (G a multiple of P).
+template <int G, int P>
+__device__ __forceinline__ void pyc_ldg(void* d, const void* s) {
+#pragma unroll
+  for (int j = 0; j < G / P; ++j)
+    pyc_vio<P>::ld(reinterpret_cast<char*>(d) + j * P, reinterpret_cast<const char*>(s) + j * P);
+}
+template <int G, int P>
+__device__ __forceinline__ void pyc_stg(void* d, const void* s) {
+#pragma unroll
+  for (int j = 0; j < G / P; ++j)
+    pyc_vio<P>::st(reinterpret_cast<char*>(d) + j * P, reinterpret_cast<const char*>(s) + j * P);
+}
+
+// Word-wise shuffle / L2 load of any trivially copyable 4-byte-multiple type.
+template <typename T>
+union pyc_words {
+  T t;
+  unsigned w[sizeof(T) / 4];
+};
+template <typename T>
+__device__ __forceinline__ T pyc_shfl_down(const T v, int d) {
+  static_assert(sizeof(T) % 4 == 0, "accumulator size must be a multiple of 4 bytes");
+  pyc_words<T> u;
+  u.t = v;
+#pragma unroll
+  for (int j = 0; j < (int)(sizeof(T) / 4); ++j) u.w[j] = __shfl_down_sync(0xffffffffu, u.w[j], d);
+  return u.t;
+}
+template <typename T>
+__device__ __forceinline__ T pyc_ld_cg(const T* p) {
+  pyc_words<T> u;
+  const unsigned* q = reinterpret_cast<const unsigned*>(p);
+#pragma unroll
+  for (int j = 0; j < (int)(sizeof(T) / 4); ++j)
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(u.w[j]) : "l"(q + j));
+  return u.t;
+}
+
+// Fixed-shape trees: lane j combines with lane j+d (left operand = lower
+// index), so the result does not depend on timing.
+template <typename T, typename Op>
+__device__ __forceinline__ T pyc_warp_reduce(T v, Op op) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    T o = pyc_shfl_down(v, d);
+    v = op(v, o);
+  }
+  return v;  // valid in lane 0
+}
+template <typename T, typename Op>
+__device__ __forceinline__ T pyc_block_reduce(T v, Op op, const T neutral) {
+  __shared__ T pyc_sm[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = pyc_warp_reduce(v, op);
+  __syncthreads();  // pyc_sm may still be read from a previous call
+  if (lane == 0) pyc_sm[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < nw ? pyc_sm[lane] : neutral;
+    v = pyc_warp_reduce(v, op);
+  }
+  return v;  // valid in thread 0
+}
+
+// Error-free transformation of a sum (Knuth's two-sum): s + e == a + b exactly.
+__device__ __forceinline__ void pyc_two_sum(const float a, const float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+__device__ __forceinline__ void pyc_two_sum_d(const double a, const double b, double& s, double& e) {
+  s = a + b;
+  const double bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+// ------------------------------------------------------------ end of prelude
+)PYC";
+
+}  // namespace
+
+std::string device_type(pyc_dtype t) { return type_info(t).device_name; }
+
+const std::vector<Variant>& all_variants() {
+  static const std::vector<Variant> v = {{16, 1}, {16, 2}, {16, 4}, {32, 1}, {32, 2}, {32, 4}};
+  return v;
+}
+
+std::string variant_suffix(const Variant& v) {
+  return "v" + std::to_string(v.vec_bytes) + "_u" + std::to_string(v.unroll);
+}
+
+int lifted_min_bytes(const ArgSpec& spec) {
+  int m = 0;
+  for (auto& p : spec.params)
+    if (p.is_ptr && p.lifted) {
+      int b = type_info(p.dtype).bytes;
+      if (m == 0 || b < m) m = b;
+    }
+  return m == 0 ? 4 : m;
+}
+
+namespace {
+
+std::string args_struct(const ArgSpec& spec) {
+  std::ostringstream o;
+  o << "struct pyc_args {\n";
+  for (auto& p : spec.params) {
+    o << "  " << (p.is_const && p.is_ptr ? "const " : "") << device_type(p.dtype)
+      << (p.is_ptr ? "* " : " ") << p.name << ";\n";
+  }
+  if (spec.params.empty()) o << "  int pyc_unused;\n";
+  o << "};\n";
+  o << "static_assert(sizeof(pyc_args) == " << (spec.params.empty() ? 4 : spec.args_bytes)
+    << ", \"argument struct layout\");\n";
+  return o.str();
+}
+
+// Local names for the declared parameters (the statement refers to them).
+std::string aliases(const ArgSpec& spec, const char* src) {
+  std::ostringstream o;
+  for (auto& p : spec.params) {
+    std::string t = device_type(p.dtype);
+    if (p.is_ptr)
+      o << "  " << (p.is_const ? "const " : "") << t << "* const " << p.name << " = " << src
+        << "." << p.name << ";\n";
+    else
+      o << "  const " << t << " " << p.name << " = " << src << "." << p.name << ";\n";
+  }
+  // keep unused-variable diagnostics quiet
+  for (auto& p : spec.params) o << "  (void)" << p.name << ";\n";
+  return o.str();
+}
+
+// Register copies of the lifted arrays, `count` elements each.
+std::string reg_decls(const ArgSpec& spec, const std::string& count) {
+  std::ostringstream o;
+  for (auto& p : spec.params)
+    if (p.is_ptr && p.lifted)
+      o << "      __align__(32) " << device_type(p.dtype) << " pyc_r_" << p.name << "[" << count
+        << "];\n";
+  return o.str();
+}
+
+// Vector loads (reads) of group u for every lifted array that is read.
+std::string group_io(const ArgSpec& spec, bool load) {
+  std::ostringstream o;
+  for (auto& p : spec.params) {
+    if (!(p.is_ptr && p.lifted)) continue;
+    if (load ? !p.read : !p.written) continue;
+    int b = type_info(p.dtype).bytes;
+    if (load)
+      o << "        pyc_ldg<E * " << b << ", VB>(&pyc_r_" << p.name << "[pyc_u * E], " << p.name
+        << " + pyc_e0);\n";
+    else
+      o << "        pyc_stg<E * " << b << ", VB>(" << p.name << " + pyc_e0, &pyc_r_" << p.name
+        << "[pyc_u * E]);\n";
+  }
+  return o.str();
+}
+
+std::string scalar_io(const ArgSpec& spec, bool load) {
+  std::ostringstream o;
+  for (auto& p : spec.params) {
+    if (!(p.is_ptr && p.lifted)) continue;
+    if (load && p.read) o << "      pyc_r_" << p.name << "[0] = " << p.name << "[i];\n";
+    if (!load && p.written) o << "      " << p.name << "[i] = pyc_r_" << p.name << "[0];\n";
+  }
+  return o.str();
+}
+
+}  // namespace
+
+MapGen generate_map(const ArgSpec& spec, const std::string& stmt, const std::string& preamble) {
+  const int mins = lifted_min_bytes(spec);
+  std::ostringstream o;
+  o << "// pyc map kernel: " << spec.canonical << "\n";
+  o << kPrelude;
+  if (!preamble.empty()) o << "// ---- user preamble\n" << preamble << "\n";
+  o << args_struct(spec);
+  o << "#define PYC_MIN_BYTES " << mins << "\n";
+  o << R"PYC(
+template <int VB, int U>
+__device__ __forceinline__ void pyc_map_body(const pyc_args& pyc_p, const pyc_i64 n,
+                                             const pyc_i64 pyc_head) {
+  constexpr int E = VB / PYC_MIN_BYTES;  // elements per vector group
+  constexpr int T = E * U;               // elements per thread per tile
+)PYC";
+  o << aliases(spec, "pyc_p");
+  o << R"PYC(  const pyc_i64 pyc_step = (pyc_i64)blockDim.x * E;
+  const pyc_i64 pyc_tile = pyc_step * U;
+  // aligned body [h, h + nfull * tile) in whole tiles; head [0, h) and tail scalar
+  const pyc_i64 pyc_h = pyc_head < 0 ? 0 : (pyc_head < n ? pyc_head : n);
+  const pyc_i64 pyc_nfull = pyc_head < 0 ? 0 : (n - pyc_h) / pyc_tile;
+  for (pyc_i64 pyc_t = blockIdx.x; pyc_t < pyc_nfull; pyc_t += gridDim.x) {
+    const pyc_i64 pyc_b0 = pyc_h + pyc_t * pyc_tile + (pyc_i64)threadIdx.x * E;
+    {
+)PYC";
+  o << reg_decls(spec, "T");
+  o << R"PYC(#pragma unroll
+      for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+)PYC";
+  o << group_io(spec, true);
+  o << R"PYC(      }
+#pragma unroll
+      for (int pyc_k = 0; pyc_k < T; ++pyc_k) {
+        const pyc_i64 i = pyc_b0 + (pyc_i64)(pyc_k / E) * pyc_step + (pyc_k % E);
+        (void)i;
+        { )PYC" << stmt << R"PYC( ; }
+      }
+#pragma unroll
+      for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+)PYC";
+  o << group_io(spec, false);
+  o << R"PYC(      }
+    }
+  }
+  const pyc_i64 pyc_tail0 = pyc_h + pyc_nfull * pyc_tile;
+  const pyc_i64 pyc_nrem = pyc_h + (n - pyc_tail0);
+  for (pyc_i64 pyc_j = (pyc_i64)blockIdx.x * blockDim.x + threadIdx.x; pyc_j < pyc_nrem;
+       pyc_j += (pyc_i64)gridDim.x * blockDim.x) {
+    const pyc_i64 i = pyc_j < pyc_h ? pyc_j : pyc_tail0 + (pyc_j - pyc_h);
+)PYC";
+  o << reg_decls(spec, "1");
+  o << scalar_io(spec, true);
+  o << "      { const int pyc_k = 0; (void)pyc_k; " << stmt << " ; }\n";
+  o << scalar_io(spec, false);
+  o << "  }\n}\n\n";
+  for (auto& v : all_variants()) {
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_map_" << variant_suffix(v)
+      << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 pyc_head) {\n"
+      << "  pyc_map_body<" << v.vec_bytes << ", " << v.unroll << ">(pyc_p, n, pyc_head);\n}\n";
+  }
+  return {o.str()};
+}
+
+ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind kind,
+                          const std::string& neutral, const std::string& reduce_expr,
+                          const std::string& map_expr, const std::string& preamble) {
+  ReduceGen g;
+  const int mins = lifted_min_bytes(spec);
+  std::string acc_t, out_t;
+  switch (kind) {
+    case ReduceKind::Arg:
+      acc_t = out_t = "pyc_argf32";
+      g.acc_bytes = g.out_bytes = 16;
+      break;
+    case ReduceKind::Compensated:
+      acc_t = "pyc_cf32";
+      out_t = "float";
+      g.acc_bytes = 8;
+      g.out_bytes = 4;
+      break;
+    case ReduceKind::Plain:
+      if (out_dtype == PYC_BF16 || out_dtype == PYC_F16) {
+        acc_t = "float";
+        g.acc_bytes = 4;
+      } else {
+        acc_t = device_type(out_dtype);
+        g.acc_bytes = type_info(out_dtype).bytes;
+      }
+      out_t = device_type(out_dtype);
+      g.out_bytes = type_info(out_dtype).bytes;
+      break;
+  }
+  // batched task record: args, then n, head, chunk, out, nchunks, slot0
+  int off = (spec.params.empty() ? 4 : spec.args_bytes);
+  off = (off + 7) / 8 * 8;
+  g.task_off_n = off;
+  g.task_off_head = off + 8;
+  g.task_off_chunk = off + 16;
+  g.task_off_out = off + 24;
+  g.task_off_nchunks = off + 32;
+  g.task_off_slot0 = off + 36;
+  g.task_bytes = off + 40;
+
+  std::ostringstream o;
+  o << "// pyc map-reduce kernel: " << spec.canonical << "\n";
+  o << kPrelude;
+  if (!preamble.empty()) o << "// ---- user preamble\n" << preamble << "\n";
+  o << args_struct(spec);
+  o << "#define PYC_MIN_BYTES " << mins << "\n";
+  o << "typedef " << acc_t << " pyc_acc_t;\n";
+  o << "typedef " << out_t << " pyc_out_t;\n";
+  o << "static_assert(sizeof(pyc_acc_t) == " << g.acc_bytes << ", \"accumulator size\");\n";
+  o << "static_assert(sizeof(pyc_out_t) == " << g.out_bytes << ", \"result size\");\n";
+  // neutral, combine, fold, finalize
+  switch (kind) {
+    case ReduceKind::Plain:
+      o << "__device__ __forceinline__ pyc_acc_t pyc_neutral() { return (pyc_acc_t)(" << neutral
+        << "); }\n";
+      o << "__device__ __forceinline__ pyc_acc_t pyc_combine(const pyc_acc_t a, const pyc_acc_t b) "
+           "{ return (pyc_acc_t)(" << reduce_expr << "); }\n";
+      o << "template <typename V> __device__ __forceinline__ void pyc_fold(pyc_acc_t& pyc_a, const V pyc_v, "
+           "const pyc_i64) { pyc_a = pyc_combine(pyc_a, (pyc_acc_t)(pyc_v)); }\n";
+      if (out_dtype == PYC_BF16 || out_dtype == PYC_F16)
+        o << "__device__ __forceinline__ pyc_out_t pyc_finalize(const pyc_acc_t a) { return pyc_out_t(a); }\n";
+      else
+        o << "__device__ __forceinline__ pyc_out_t pyc_finalize(const pyc_acc_t a) { return a; }\n";
+      break;
+    case ReduceKind::Arg:
+      o << "__device__ __forceinline__ pyc_acc_t pyc_neutral() { return " << neutral << "; }\n";
+      o << "__device__ __forceinline__ pyc_acc_t pyc_combine(const pyc_acc_t a, const pyc_acc_t b) "
+           "{ return (" << reduce_expr << "); }\n";
+      o << "template <typename V> __device__ __forceinline__ void pyc_fold(pyc_acc_t& pyc_a, const V pyc_v, "
+           "const pyc_i64 pyc_i) { pyc_argf32 pyc_e; pyc_e.v = (float)(pyc_v); pyc_e.pad = 0; "
+           "pyc_e.i = pyc_i; pyc_a = pyc_combine(pyc_a, pyc_e); }\n";
+      o << "__device__ __forceinline__ pyc_out_t pyc_finalize(const pyc_acc_t a) { return a; }\n";
+      break;
+    case ReduceKind::Compensated:
+      o << R"PYC(__device__ __forceinline__ pyc_acc_t pyc_neutral() { pyc_cf32 z; z.s = 0.0f; z.c = 0.0f; return z; }
+// (s1 + c1) + (s2 + c2): exact two-sum of the leading parts, errors summed.
+__device__ __forceinline__ pyc_acc_t pyc_combine(const pyc_acc_t a, const pyc_acc_t b) {
+  pyc_cf32 r; float e;
+  pyc_two_sum(a.s, b.s, r.s, e);
+  r.c = (a.c + b.c) + e;
+  return r;
+}
+template <typename V> __device__ __forceinline__ void pyc_fold(pyc_acc_t& pyc_a, const V pyc_v, const pyc_i64) {
+  float s, e;
+  pyc_two_sum(pyc_a.s, (float)(pyc_v), s, e);
+  pyc_a.s = s;
+  pyc_a.c += e;
+}
+__device__ __forceinline__ pyc_out_t pyc_finalize(const pyc_acc_t a) {
+  return __double2float_rn((double)a.s + (double)a.c);
+}
+)PYC";
+      break;
+  }
+  o << R"PYC(
+struct pyc_combine_op {
+  __device__ __forceinline__ pyc_acc_t operator()(const pyc_acc_t a, const pyc_acc_t b) const { return pyc_combine(a, b); }
+};
+
+// Fold [vs, ve) (vs aligned to VB for every lifted array) with vector groups,
+// plus the scalar range [ss, se), by a group of `nthr` threads (a CTA or a
+// warp); returns this thread's accumulator.
+template <int VB, int U>
+__device__ __forceinline__ pyc_acc_t pyc_reduce_span(const pyc_args& pyc_p, const pyc_i64 n,
+    const pyc_i64 pyc_vs, const pyc_i64 pyc_ve, const pyc_i64 pyc_ss, const pyc_i64 pyc_se,
+    const int pyc_tid, const int pyc_nthr) {
+  constexpr int E = VB / PYC_MIN_BYTES;
+  constexpr int T = E * U;
+  // independent accumulators: element position k folds into acc[k % A]
+  constexpr int AMAX = 128 / (int)sizeof(pyc_acc_t) > 0 ? 128 / (int)sizeof(pyc_acc_t) : 1;
+  constexpr int A = T < AMAX ? T : AMAX;
+)PYC";
+  o << aliases(spec, "pyc_p");
+  o << R"PYC(  (void)n;
+  pyc_acc_t pyc_acc[A];
+#pragma unroll
+  for (int k = 0; k < A; ++k) pyc_acc[k] = pyc_neutral();
+  const pyc_i64 pyc_step = (pyc_i64)pyc_nthr * E;
+  const pyc_i64 pyc_tile = pyc_step * U;
+  const pyc_i64 pyc_nt = pyc_ve > pyc_vs ? (pyc_ve - pyc_vs) / pyc_tile : 0;
+  for (pyc_i64 pyc_t = 0; pyc_t < pyc_nt; ++pyc_t) {
+    const pyc_i64 pyc_b0 = pyc_vs + pyc_t * pyc_tile + (pyc_i64)pyc_tid * E;
+    {
+)PYC";
+  o << reg_decls(spec, "T");
+  o << R"PYC(#pragma unroll
+      for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+)PYC";
+  o << group_io(spec, true);
+  o << R"PYC(      }
+#pragma unroll
+      for (int pyc_k = 0; pyc_k < T; ++pyc_k) {
+        const pyc_i64 i = pyc_b0 + (pyc_i64)(pyc_k / E) * pyc_step + (pyc_k % E);
+        pyc_fold(pyc_acc[pyc_k % A], ()PYC" << map_expr << R"PYC(), i);
+      }
+    }
+  }
+  const pyc_i64 pyc_r0 = pyc_vs + pyc_nt * pyc_tile;
+  const pyc_i64 pyc_ns = pyc_se - pyc_ss;
+  const pyc_i64 pyc_nr = (pyc_ve > pyc_r0 ? pyc_ve - pyc_r0 : 0) + pyc_ns;
+  for (pyc_i64 pyc_j = pyc_tid; pyc_j < pyc_nr; pyc_j += pyc_nthr) {
+    const pyc_i64 i = pyc_j < pyc_ns ? pyc_ss + pyc_j : pyc_r0 + (pyc_j - pyc_ns);
+)PYC";
+  o << reg_decls(spec, "1");
+  o << scalar_io(spec, true);
+  o << "      { const int pyc_k = 0; (void)pyc_k; pyc_fold(pyc_acc[0], (" << map_expr << "), i); }\n";
+  o << R"PYC(  }
+#pragma unroll
+  for (int s = 1; s < A; s *= 2)
+#pragma unroll
+    for (int k = 0; k + s < A; k += 2 * s) pyc_acc[k] = pyc_combine(pyc_acc[k], pyc_acc[k + s]);
+  return pyc_acc[0];
+}
+
+// Fold the chunk c of a range of length n whose vector body starts at head
+// (head < 0: no vector body).  Chunk 0 also takes the scalar head [0, head).
+template <int VB, int U>
+__device__ __forceinline__ pyc_acc_t pyc_chunk(const pyc_args& pyc_p, const pyc_i64 n,
+    const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 c, const int tid, const int nthr) {
+  if (head >= 0) {
+    const pyc_i64 vs = head + c * chunk;
+    const pyc_i64 ve = vs + chunk < n ? vs + chunk : n;
+    return pyc_reduce_span<VB, U>(pyc_p, n, vs, ve, 0, c == 0 ? head : 0, tid, nthr);
+  }
+  const pyc_i64 ss = c * chunk;
+  const pyc_i64 se = ss + chunk < n ? ss + chunk : n;
+  return pyc_reduce_span<VB, U>(pyc_p, n, 0, 0, ss, se, tid, nthr);
+}
+
+)PYC";
+  // partial combine (shared by the single reduction and the batched one)
+  if (kind == ReduceKind::Compensated) {
+    o << R"PYC(// Final combine of compensated partials in binary64: each thread sums its
+// partials' (s, c) with a binary64 two-sum, then a fixed tree; thread 0 rounds.
+struct pyc_dd { double hi; double lo; };
+struct pyc_dd_op {
+  __device__ __forceinline__ pyc_dd operator()(const pyc_dd a, const pyc_dd b) const {
+    pyc_dd r; double e;
+    pyc_two_sum_d(a.hi, b.hi, r.hi, e);
+    r.lo = (a.lo + b.lo) + e;
+    return r;
+  }
+};
+__device__ __forceinline__ pyc_out_t pyc_combine_partials(const pyc_acc_t* part, const int count) {
+  pyc_dd acc; acc.hi = 0.0; acc.lo = 0.0;
+  pyc_dd_op op;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    const pyc_acc_t p = pyc_ld_cg(part + j);
+    pyc_dd t; t.hi = (double)p.s; t.lo = (double)p.c;
+    acc = op(acc, t);
+  }
+  pyc_dd z; z.hi = 0.0; z.lo = 0.0;
+  acc = pyc_block_reduce(acc, op, z);
+  return __double2float_rn(acc.hi + acc.lo);
+}
+)PYC";
+  } else {
+    o << R"PYC(__device__ __forceinline__ pyc_out_t pyc_combine_partials(const pyc_acc_t* part, const int count) {
+  pyc_acc_t acc = pyc_neutral();
+  for (int j = threadIdx.x; j < count; j += blockDim.x) acc = pyc_combine(acc, pyc_ld_cg(part + j));
+  acc = pyc_block_reduce(acc, pyc_combine_op(), pyc_neutral());
+  return pyc_finalize(acc);
+}
+)PYC";
+  }
+  o << R"PYC(
+// Single reduction: CTAs take chunks c = blockIdx.x, blockIdx.x + gridDim.x, ...;
+// the last CTA to arrive combines the partials and resets the ticket.
+template <int VB, int U>
+__device__ __forceinline__ void pyc_reduce_body(const pyc_args& pyc_p, const pyc_i64 n,
+    const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 nchunks,
+    pyc_acc_t* __restrict__ part, unsigned* __restrict__ ticket, pyc_out_t* __restrict__ out) {
+  __shared__ unsigned pyc_last;
+  for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    pyc_acc_t v = pyc_chunk<VB, U>(pyc_p, n, head, chunk, c, threadIdx.x, blockDim.x);
+    v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
+    if (threadIdx.x == 0) part[c] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) pyc_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!pyc_last) return;
+  __threadfence();
+  const pyc_out_t r = pyc_combine_partials(part, (int)nchunks);
+  if (threadIdx.x == 0) {
+    *out = r;
+    *ticket = 0u;
+  }
+}
+
+// Batched reduction: one task per segment.
+struct pyc_task {
+  pyc_args args;
+  pyc_i64 n;
+  pyc_i64 head;
+  pyc_i64 chunk;
+  pyc_out_t* out;
+  int nchunks;   // 0: the task is reduced by one warp of a bundle item
+  int slot0;     // first partial slot (tasks with nchunks > 1)
+};
+// chunk >= 0: a CTA reduces chunk `chunk` of task `task`;
+// chunk <  0: warp w reduces task `task + w` for w < count.
+struct pyc_item {
+  int task;
+  int chunk;
+  int count;
+  int pad;
+};
+)PYC";
+  o << "static_assert(sizeof(pyc_task) == " << g.task_bytes << ", \"task layout\");\n";
+  o << R"PYC(
+template <int VB, int U>
+__device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ tasks,
+    const pyc_item* __restrict__ items, const int nitems, pyc_acc_t* __restrict__ part,
+    unsigned* __restrict__ tickets, unsigned* __restrict__ ctl) {
+  __shared__ int pyc_it;
+  __shared__ unsigned pyc_last;
+  for (;;) {
+    if (threadIdx.x == 0) pyc_it = (int)atomicAdd(&ctl[0], 1u);
+    __syncthreads();
+    const int it = pyc_it;
+    __syncthreads();
+    if (it >= nitems) break;
+    const pyc_item I = items[it];
+    if (I.chunk < 0) {
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      if (w < I.count) {
+        const pyc_task& T = tasks[I.task + w];
+        pyc_acc_t v = pyc_chunk<VB, U>(T.args, T.n, T.head, T.chunk, 0, lane, 32);
+        v = pyc_warp_reduce(v, pyc_combine_op());
+        if (lane == 0) *T.out = pyc_finalize(v);
+      }
+    } else {
+      const pyc_task& T = tasks[I.task];
+      pyc_acc_t v = pyc_chunk<VB, U>(T.args, T.n, T.head, T.chunk, I.chunk, threadIdx.x, blockDim.x);
+      v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
+      if (T.nchunks == 1) {
+        if (threadIdx.x == 0) *T.out = pyc_finalize(v);
+      } else {
+        if (threadIdx.x == 0) {
+          part[T.slot0 + I.chunk] = v;
+          __threadfence();
+          pyc_last = atomicAdd(&tickets[I.task], 1u) == (unsigned)(T.nchunks - 1) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (pyc_last) {
+          __threadfence();
+          const pyc_out_t r = pyc_combine_partials(part + T.slot0, T.nchunks);
+          if (threadIdx.x == 0) {
+            *T.out = r;
+            tickets[I.task] = 0u;
+          }
+        }
+      }
+    }
+  }
+  // the last CTA to leave resets the work counter for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[1], 1u) == gridDim.x - 1) {
+      ctl[0] = 0u;
+      ctl[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+)PYC";
+  for (auto& v : all_variants()) {
+    std::string sfx = variant_suffix(v);
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_reduce_" << sfx
+      << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
+         "const pyc_i64 nchunks, pyc_acc_t* part, unsigned* ticket, pyc_out_t* out) {\n"
+      << "  pyc_reduce_body<" << v.vec_bytes << ", " << v.unroll
+      << ">(pyc_p, n, head, chunk, nchunks, part, ticket, out);\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rbatch_" << sfx
+      << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
+         "unsigned* tickets, unsigned* ctl) {\n"
+      << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll
+      << ">(tasks, items, nitems, part, tickets, ctl);\n}\n";
+  }
+  g.source = o.str();
+  return g;
+}
+
+}  // namespace pyc

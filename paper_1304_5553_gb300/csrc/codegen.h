@@ -1,0 +1,56 @@
+// Source generation for map and map-reduce kernels (run-time code
+// generation, Sec. 3.3: types, constants and unroll counts are written into
+// the source just in time; variants are kept side by side for the tuner).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "spec.h"
+
+namespace pyc {
+
+// One compiled variant: vector access width in bytes and vectors per thread
+// per tile.  Block size is a launch-time choice.
+struct Variant {
+  int vec_bytes;
+  int unroll;
+};
+
+// All variants compiled into every module.
+const std::vector<Variant>& all_variants();
+std::string variant_suffix(const Variant& v);
+
+// Narrowest element size among the lifted arrays (4 if there are none).
+int lifted_min_bytes(const ArgSpec& spec);
+
+struct MapGen {
+  std::string source;
+};
+
+MapGen generate_map(const ArgSpec& spec, const std::string& stmt_rewritten,
+                    const std::string& preamble);
+
+enum class ReduceKind { Plain, Arg, Compensated };
+
+struct ReduceGen {
+  std::string source;
+  int acc_bytes = 0;
+  int out_bytes = 0;
+  int task_bytes = 0;       // size of one batched task record
+  int task_off_n = 0;       // offsets of the fixed task fields
+  int task_off_head = 0;
+  int task_off_chunk = 0;
+  int task_off_out = 0;
+  int task_off_nchunks = 0;
+  int task_off_slot0 = 0;
+};
+
+ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind kind,
+                          const std::string& neutral, const std::string& reduce_expr,
+                          const std::string& map_rewritten, const std::string& preamble);
+
+// Device-side spelling of a dtype (pyc_bf16 for BF16, ...).
+std::string device_type(pyc_dtype t);
+
+}  // namespace pyc

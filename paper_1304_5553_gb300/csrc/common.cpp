@@ -1,0 +1,44 @@
+// Thread-local error text and element-type tables.
+#include "common.h"
+
+namespace pyc {
+
+namespace {
+thread_local std::string t_last_error;
+}
+
+void set_last_error(const std::string& m) { t_last_error = m; }
+void clear_last_error() { t_last_error.clear(); }
+
+const TypeInfo& type_info(pyc_dtype t) {
+  static const TypeInfo table[] = {
+      {PYC_F32, 4, "float"},
+      {PYC_F64, 8, "double"},
+      {PYC_BF16, 2, "pyc_bf16"},
+      {PYC_F16, 2, "pyc_f16"},
+      {PYC_I32, 4, "int"},
+      {PYC_I64, 8, "long long"},
+      {PYC_ARGMIN_F32, 16, "pyc_argf32"},
+      {PYC_ARGMAX_F32, 16, "pyc_argf32"},
+      {PYC_U8, 1, "unsigned char"},
+      {PYC_I8, 1, "signed char"},
+      {PYC_U32, 4, "unsigned int"},
+      {PYC_U64, 8, "unsigned long long"},
+      {PYC_I16, 2, "short"},
+      {PYC_U16, 2, "unsigned short"},
+  };
+  int k = (int)t;
+  if (k < 0 || k >= (int)(sizeof(table) / sizeof(table[0])))
+    fail(PYC_E_ARG, "unknown dtype " + std::to_string(k));
+  return table[k];
+}
+
+bool is_float_type(pyc_dtype t) {
+  return t == PYC_F32 || t == PYC_F64 || t == PYC_BF16 || t == PYC_F16;
+}
+
+}  // namespace pyc
+
+PYC_API const char* pyc_last_error(void) { return pyc::t_last_error.c_str(); }
+
+PYC_API const char* pyc_version(void) { return "pyc 0.1 (sm_103a)"; }

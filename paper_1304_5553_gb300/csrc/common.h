@@ -1,0 +1,55 @@
+// Internal helpers shared by the library's translation units: status
+// exceptions, the thread-local last-error message, and element-type tables.
+#pragma once
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+
+#include "pyc.h"
+
+#define PYC_API extern "C" __attribute__((visibility("default")))
+
+namespace pyc {
+
+// Thrown inside the library; converted to a pyc_status at the C boundary.
+struct Error : std::runtime_error {
+  pyc_status status;
+  Error(pyc_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+[[noreturn]] inline void fail(pyc_status s, const std::string& m) { throw Error(s, m); }
+
+void set_last_error(const std::string& m);
+void clear_last_error();
+
+// Runs f(); maps exceptions to a status and records the message.
+template <class F>
+pyc_status guarded(F&& f) {
+  try {
+    clear_last_error();
+    f();
+    return PYC_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return PYC_E_NOMEM;
+  } catch (const std::exception& e) {
+    set_last_error(std::string("internal error: ") + e.what());
+    return PYC_E_INTERNAL;
+  }
+}
+
+// Element types that may appear in an argument list.
+struct TypeInfo {
+  pyc_dtype dtype;
+  int bytes;
+  const char* device_name;  // spelling used in generated source
+};
+
+const TypeInfo& type_info(pyc_dtype t);
+bool is_float_type(pyc_dtype t);
+
+}  // namespace pyc

@@ -1,0 +1,118 @@
+// Run-time loading of the CUDA driver (see cudrv.h).
+#include "cudrv.h"
+
+#include <dlfcn.h>
+
+#include <cstdlib>
+#include <map>
+#include <mutex>
+
+#include "common.h"
+
+namespace pyc {
+
+namespace {
+
+Driver g_drv;
+bool g_loaded = false;
+std::string g_load_error;
+std::once_flag g_once;
+
+void load_driver() {
+  void* h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_GLOBAL);
+  if (!h) h = dlopen("libcuda.so", RTLD_NOW | RTLD_GLOBAL);
+  if (!h) {
+    g_load_error = "CUDA driver (libcuda.so.1) not found: no GPU driver on this machine";
+    return;
+  }
+  auto gpa = reinterpret_cast<decltype(&::cuGetProcAddress)>(dlsym(h, "cuGetProcAddress_v2"));
+  if (!gpa) {
+    g_load_error = "CUDA driver too old: cuGetProcAddress_v2 missing";
+    return;
+  }
+  std::string missing;
+  auto resolve = [&](void** slot, const char* name) {
+    CUdriverProcAddressQueryResult q;
+    if (gpa(name, slot, 13000, CU_GET_PROC_ADDRESS_DEFAULT, &q) != CUDA_SUCCESS ||
+        q != CU_GET_PROC_ADDRESS_SUCCESS || *slot == nullptr) {
+      *slot = nullptr;
+      missing += std::string(missing.empty() ? "" : ", ") + name;
+    }
+  };
+  Driver& d = g_drv;
+#define PYC_DRV_FN(name) resolve(reinterpret_cast<void**>(&d.name), #name);
+#include "cudrv_fns.inc"
+#undef PYC_DRV_FN
+  if (!missing.empty()) {
+    g_load_error = "CUDA driver lacks entry points: " + missing;
+    return;
+  }
+  CUresult r = d.cuInit(0);
+  if (r != CUDA_SUCCESS) {
+    const char* s = nullptr;
+    d.cuGetErrorString(r, &s);
+    g_load_error = std::string("cuInit failed: ") + (s ? s : "unknown error");
+    return;
+  }
+  g_loaded = true;
+}
+
+}  // namespace
+
+const Driver& drv() {
+  std::call_once(g_once, load_driver);
+  if (!g_loaded) fail(PYC_E_CUDA, g_load_error);
+  return g_drv;
+}
+
+void check(CUresult r, const char* what) {
+  if (r == CUDA_SUCCESS) return;
+  const char* name = nullptr;
+  const char* s = nullptr;
+  if (g_loaded) {
+    g_drv.cuGetErrorName(r, &name);
+    g_drv.cuGetErrorString(r, &s);
+  }
+  pyc_status st = (r == CUDA_ERROR_OUT_OF_MEMORY) ? PYC_E_NOMEM : PYC_E_CUDA;
+  fail(st, std::string(what) + " failed: " + (name ? name : "?") + " (" + (s ? s : "?") + ")");
+}
+
+CUcontext ensure_context() {
+  const Driver& d = drv();
+  CUcontext ctx = nullptr;
+  PYC_CU(d.cuCtxGetCurrent(&ctx));
+  if (ctx) return ctx;
+  int ordinal = 0;
+  if (const char* e = std::getenv("CUDA_DEVICE")) ordinal = std::atoi(e);
+  CUdevice dev;
+  PYC_CU(d.cuDeviceGet(&dev, ordinal));
+  PYC_CU(d.cuDevicePrimaryCtxRetain(&ctx, dev));
+  PYC_CU(d.cuCtxSetCurrent(ctx));
+  return ctx;
+}
+
+const DeviceProps& current_device_props() {
+  static std::mutex mu;
+  static std::map<int, DeviceProps> cache;
+  const Driver& d = drv();
+  ensure_context();
+  CUdevice dev;
+  PYC_CU(d.cuCtxGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find((int)dev);
+  if (it != cache.end()) return it->second;
+  DeviceProps p;
+  p.device = (int)dev;
+  PYC_CU(d.cuDeviceGetAttribute(&p.sm_count, CU_DEVICE_ATTRIBUTE_MULTIPROCESSOR_COUNT, dev));
+  PYC_CU(d.cuDeviceGetAttribute(&p.cc_major, CU_DEVICE_ATTRIBUTE_COMPUTE_CAPABILITY_MAJOR, dev));
+  PYC_CU(d.cuDeviceGetAttribute(&p.cc_minor, CU_DEVICE_ATTRIBUTE_COMPUTE_CAPABILITY_MINOR, dev));
+  PYC_CU(d.cuDeviceGetAttribute(&p.max_threads_per_sm,
+                                CU_DEVICE_ATTRIBUTE_MAX_THREADS_PER_MULTIPROCESSOR, dev));
+  PYC_CU(d.cuDeviceGetAttribute(&p.l2_bytes, CU_DEVICE_ATTRIBUTE_L2_CACHE_SIZE, dev));
+  char name[256] = {0};
+  PYC_CU(d.cuDeviceGetName(name, sizeof(name) - 1, dev));
+  p.name = name;
+  return cache.emplace((int)dev, p).first->second;
+}
+
+}  // namespace pyc

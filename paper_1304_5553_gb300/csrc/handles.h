@@ -1,0 +1,120 @@
+// Handle objects behind the opaque pyc_map_t / pyc_reduce_t pointers, and the
+// launch-configuration helpers shared by launches, the batched reducer, the
+// tuner and the server.
+#pragma once
+
+#include <cuda.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "codegen.h"
+#include "common.h"
+#include "kcache.h"
+#include "spec.h"
+
+namespace pyc {
+
+// One tuned (or chosen) launch configuration.
+struct LaunchCfg {
+  Variant v{16, 4};
+  int block = 256;
+};
+
+// Size buckets for tuning: bucket b holds n with bit length in [2b, 2b+1].
+int size_bucket(int64_t n);
+
+// Per-handle tuning results by size bucket.
+struct TuneTable {
+  std::mutex mu;
+  std::map<int, LaunchCfg> by_bucket;
+};
+
+struct BatchPlan;  // batched reducer plan (batched.cpp)
+
+struct HandleBase {
+  ArgSpec spec;
+  std::string name;
+  pyc_opts opts{};
+  std::string preamble;
+  std::string source;
+  std::shared_ptr<Module> mod;
+  int min_bytes = 4;
+  TuneTable tune;
+  std::string tune_key;  // digest of the source: key of the persistent tuning cache
+  std::vector<std::string> param_names;  // stable storage for pyc_param_info.name
+};
+
+}  // namespace pyc
+
+struct pyc_map : pyc::HandleBase {};
+
+struct pyc_reduce : pyc::HandleBase {
+  pyc_reduce();
+  ~pyc_reduce();  // defined where BatchPlan is complete
+  pyc_dtype out_dtype = PYC_F32;
+  pyc::ReduceKind kind = pyc::ReduceKind::Plain;
+  pyc::ReduceGen gen;
+  // workspace (partials + ticket) per (context, stream)
+  struct Workspace {
+    CUdeviceptr base = 0;
+    CUdeviceptr part = 0;
+    CUdeviceptr ticket = 0;
+  };
+  std::mutex ws_mu;
+  std::map<std::pair<CUcontext, CUstream>, Workspace> ws;
+  std::mutex plan_mu;
+  std::vector<std::unique_ptr<pyc::BatchPlan>> plans;  // most recent last
+};
+
+namespace pyc {
+
+// Maximum number of chunks of one reduction (bounds the partial workspace).
+constexpr int64_t kMaxChunks = 4096;
+
+// Configuration for a launch of n elements: explicit options first, then the
+// tuned value of n's bucket, then the built-in default.
+LaunchCfg choose_cfg(HandleBase& h, int64_t n, bool reduce);
+
+// Device-side argument struct bytes from the caller's pointers and scalars.
+std::vector<unsigned char> pack_args(const ArgSpec& spec, void* const* ptrs, const void* scalars);
+
+// First element index at which every lifted array is vec_bytes-aligned, or -1
+// if their alignments are incompatible.  Throws PYC_E_ARG on a null lifted
+// array (when n > 0) or an array not aligned to its element size.
+int64_t vector_head(const ArgSpec& spec, void* const* ptrs, int vec_bytes, int min_bytes,
+                    int64_t n);
+
+// Resident CTAs of `f` at `block` threads on the current device.
+int resident_ctas(CUfunction f, int block);
+
+// Chunking of a single reduction of n elements (head from vector_head).
+struct ChunkPlan {
+  int64_t head = -1;
+  int64_t chunk = 0;
+  int64_t nchunks = 0;
+  int grid = 1;
+};
+ChunkPlan plan_chunks(int64_t n, int64_t head, int64_t tile, int resident);
+
+// Enqueue one reduction (used by pyc_reduce_launch and the tuner).
+void launch_reduce(pyc_reduce* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
+                   const void* scalars, void* d_out, CUstream stream);
+// Enqueue one map.
+void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
+                const void* scalars, CUstream stream);
+
+// Persistent tuning cache (JSON lines in the kernel cache directory).
+void tune_cache_load(HandleBase& h, bool reduce);
+void tune_cache_store(const HandleBase& h, bool reduce, int bucket, const LaunchCfg& c,
+                      double us);
+
+// Batched reducer (batched.cpp).
+void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* offsets, void* const* ptrs,
+                    const void* scalars, void* d_out, CUstream stream);
+void free_plans(pyc_reduce* h);
+
+}  // namespace pyc

@@ -1,0 +1,296 @@
+// NVRTC driver and kernel cache (see kcache.h).
+#include "kcache.h"
+
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
+
+#include "common.h"
+#include "cudrv.h"
+
+namespace pyc {
+
+namespace {
+
+// NVRTC entry points, resolved with dlopen so that the library loads on
+// machines without the toolkit (compilation then fails with a clear error).
+struct Nvrtc {
+  decltype(&::nvrtcVersion) version = nullptr;
+  decltype(&::nvrtcCreateProgram) create = nullptr;
+  decltype(&::nvrtcCompileProgram) compile = nullptr;
+  decltype(&::nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&::nvrtcGetProgramLog) log = nullptr;
+  decltype(&::nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&::nvrtcGetCUBIN) cubin = nullptr;
+  decltype(&::nvrtcDestroyProgram) destroy = nullptr;
+  decltype(&::nvrtcGetErrorString) error_string = nullptr;
+  int major = 0, minor = 0;
+};
+
+Nvrtc g_nv;
+bool g_nv_ok = false;
+std::string g_nv_err;
+std::once_flag g_nv_once;
+
+void load_nvrtc() {
+  const char* names[] = {"libnvrtc.so.13", "libnvrtc.so", nullptr};
+  void* h = nullptr;
+  for (int j = 0; names[j] && !h; ++j) h = dlopen(names[j], RTLD_NOW | RTLD_LOCAL);
+  if (!h) {
+    std::string home;
+    if (const char* c = std::getenv("CUDA_HOME")) home = c;
+    if (home.empty()) home = "/usr/local/cuda";
+    h = dlopen((home + "/lib64/libnvrtc.so").c_str(), RTLD_NOW | RTLD_LOCAL);
+  }
+  if (!h) {
+    g_nv_err = "NVRTC (libnvrtc.so.13) not found";
+    return;
+  }
+  bool ok = true;
+  auto sym = [&](auto& slot, const char* name) {
+    slot = reinterpret_cast<std::remove_reference_t<decltype(slot)>>(dlsym(h, name));
+    if (!slot) ok = false;
+  };
+  sym(g_nv.version, "nvrtcVersion");
+  sym(g_nv.create, "nvrtcCreateProgram");
+  sym(g_nv.compile, "nvrtcCompileProgram");
+  sym(g_nv.log_size, "nvrtcGetProgramLogSize");
+  sym(g_nv.log, "nvrtcGetProgramLog");
+  sym(g_nv.cubin_size, "nvrtcGetCUBINSize");
+  sym(g_nv.cubin, "nvrtcGetCUBIN");
+  sym(g_nv.destroy, "nvrtcDestroyProgram");
+  sym(g_nv.error_string, "nvrtcGetErrorString");
+  if (!ok) {
+    g_nv_err = "NVRTC library lacks required entry points";
+    return;
+  }
+  g_nv.version(&g_nv.major, &g_nv.minor);
+  g_nv_ok = true;
+}
+
+const Nvrtc& nvrtc() {
+  std::call_once(g_nv_once, load_nvrtc);
+  if (!g_nv_ok) fail(PYC_E_COMPILE, g_nv_err);
+  return g_nv;
+}
+
+std::atomic<long long> g_compiled{0}, g_disk{0}, g_mem{0};
+
+std::mutex g_cache_mu;
+std::map<std::string, std::weak_ptr<Module>> g_mem_cache;
+// keep recently used modules alive even when no handle holds them; never
+// destroyed, so no driver call runs during static destruction at exit
+std::vector<std::shared_ptr<Module>>* g_recent = new std::vector<std::shared_ptr<Module>>();
+
+const char* kArch = "sm_103a";
+const char* kLibTag = "pyc-0.1-t1";
+
+std::string read_file(const std::string& path, bool* ok) {
+  std::ifstream f(path, std::ios::binary);
+  if (!f) {
+    *ok = false;
+    return {};
+  }
+  std::ostringstream ss;
+  ss << f.rdbuf();
+  *ok = true;
+  return ss.str();
+}
+
+void mkdirs(const std::string& path) {
+  std::string cur;
+  for (size_t j = 0; j < path.size(); ++j) {
+    cur += path[j];
+    if ((path[j] == '/' && j > 0) || j + 1 == path.size()) mkdir(cur.c_str(), 0755);
+  }
+}
+
+// On-disk record: magic, key text length + text, cubin length + bytes.  The
+// full key text (source + options) is compared on read, so a hash collision
+// can never return the wrong binary.
+std::string pack_record(const std::string& key_text, const std::string& cubin) {
+  std::string r = "PYCK1\n";
+  r += std::to_string(key_text.size()) + "\n" + key_text;
+  r += std::to_string(cubin.size()) + "\n" + cubin;
+  return r;
+}
+
+bool unpack_record(const std::string& r, const std::string& key_text, std::string* cubin) {
+  if (r.compare(0, 6, "PYCK1\n") != 0) return false;
+  size_t p = 6;
+  size_t nl = r.find('\n', p);
+  if (nl == std::string::npos) return false;
+  size_t klen = std::strtoull(r.c_str() + p, nullptr, 10);
+  p = nl + 1;
+  if (p + klen > r.size() || r.compare(p, klen, key_text) != 0 || klen != key_text.size())
+    return false;
+  p += klen;
+  nl = r.find('\n', p);
+  if (nl == std::string::npos) return false;
+  size_t clen = std::strtoull(r.c_str() + p, nullptr, 10);
+  p = nl + 1;
+  if (p + clen != r.size()) return false;
+  *cubin = r.substr(p, clen);
+  return true;
+}
+
+std::string compile_nvrtc(const std::string& source, bool fmad) {
+  const Nvrtc& nv = nvrtc();
+  nvrtcProgram prog;
+  nvrtcResult r = nv.create(&prog, source.c_str(), "pyc_kernel.cu", 0, nullptr, nullptr);
+  if (r != NVRTC_SUCCESS) fail(PYC_E_COMPILE, std::string("nvrtcCreateProgram: ") + nv.error_string(r));
+  std::string arch = std::string("-arch=") + kArch;
+  const char* opts[] = {arch.c_str(), "-std=c++17", fmad ? "--fmad=true" : "--fmad=false",
+                        "-lineinfo", "-DNDEBUG"};
+  r = nv.compile(prog, 5, opts);
+  size_t ls = 0;
+  nv.log_size(prog, &ls);
+  std::string log(ls, '\0');
+  if (ls) nv.log(prog, &log[0]);
+  if (r != NVRTC_SUCCESS) {
+    nv.destroy(&prog);
+    fail(PYC_E_COMPILE, std::string("run-time compilation failed (") + nv.error_string(r) +
+                            "):\n" + log);
+  }
+  size_t cs = 0;
+  nv.cubin_size(prog, &cs);
+  std::string cubin(cs, '\0');
+  nv.cubin(prog, &cubin[0]);
+  nv.destroy(&prog);
+  return cubin;
+}
+
+}  // namespace
+
+std::string digest(const std::string& data) {
+  uint64_t h1 = 1469598103934665603ULL, h2 = 0x9E3779B97F4A7C15ULL;
+  for (unsigned char c : data) {
+    h1 = (h1 ^ c) * 1099511628211ULL;
+    h2 = (h2 ^ c) * 0x100000001B3ULL + 0x632BE59BD9B4E019ULL;
+    h2 ^= h2 >> 29;
+  }
+  char buf[40];
+  std::snprintf(buf, sizeof(buf), "%016llx%016llx", (unsigned long long)h1,
+                (unsigned long long)h2);
+  return buf;
+}
+
+std::string cache_dir() {
+  if (const char* d = std::getenv("PYC_CACHE_DIR")) return d;  // "" disables
+  std::string base;
+  if (const char* x = std::getenv("XDG_CACHE_HOME")) base = x;
+  if (base.empty()) {
+    if (const char* h = std::getenv("HOME")) base = std::string(h) + "/.cache";
+  }
+  if (base.empty()) return "";
+  return base + "/pyc";
+}
+
+std::shared_ptr<Module> get_module(const std::string& source, bool fmad) {
+  int maj = 0, mnr = 0;
+  {
+    const Nvrtc& nv = nvrtc();
+    maj = nv.major;
+    mnr = nv.minor;
+  }
+  std::string key_text = std::string(kLibTag) + "|" + kArch + "|nvrtc" + std::to_string(maj) +
+                         "." + std::to_string(mnr) + "|fmad=" + (fmad ? "1" : "0") + "\n" + source;
+  std::string key = digest(key_text);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_mem_cache.find(key);
+    if (it != g_mem_cache.end()) {
+      if (auto m = it->second.lock()) {
+        ++g_mem;
+        return m;
+      }
+    }
+  }
+  std::string dir = cache_dir();
+  std::string path = dir.empty() ? "" : dir + "/" + key + ".pyck";
+  std::string cubin;
+  bool have = false;
+  if (!path.empty()) {
+    bool ok = false;
+    std::string rec = read_file(path, &ok);
+    if (ok && unpack_record(rec, key_text, &cubin)) {
+      have = true;
+      ++g_disk;
+    }
+  }
+  if (!have) {
+    cubin = compile_nvrtc(source, fmad);
+    ++g_compiled;
+    if (!path.empty()) {
+      mkdirs(dir);
+      std::string tmp = path + ".tmp" + std::to_string(getpid());
+      {
+        std::ofstream f(tmp, std::ios::binary);
+        std::string rec = pack_record(key_text, cubin);
+        f.write(rec.data(), (std::streamsize)rec.size());
+      }
+      std::rename(tmp.c_str(), path.c_str());  // atomic publish
+    }
+  }
+  auto m = std::make_shared<Module>(cubin);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  g_mem_cache[key] = m;
+  g_recent->push_back(m);
+  if (g_recent->size() > 64) g_recent->erase(g_recent->begin());
+  return m;
+}
+
+CacheStats cache_stats() {
+  CacheStats s;
+  s.compiled = g_compiled;
+  s.disk_hits = g_disk;
+  s.mem_hits = g_mem;
+  return s;
+}
+
+Module::~Module() {
+  // Modules are unloaded only if the driver is present and the context lives;
+  // errors at teardown are ignored on purpose.
+  for (auto& kv : loaded_) {
+    try {
+      drv().cuModuleUnload(kv.second);
+    } catch (...) {
+    }
+  }
+}
+
+CUfunction Module::function(const std::string& name) {
+  CUcontext ctx = ensure_context();
+  std::lock_guard<std::mutex> lk(mu_);
+  auto fk = std::make_pair(ctx, name);
+  auto fit = funcs_.find(fk);
+  if (fit != funcs_.end()) return fit->second;
+  auto it = loaded_.find(ctx);
+  CUmodule mod;
+  if (it == loaded_.end()) {
+    PYC_CU(drv().cuModuleLoadData(&mod, cubin_.data()));
+    loaded_[ctx] = mod;
+  } else {
+    mod = it->second;
+  }
+  CUfunction f;
+  PYC_CU(drv().cuModuleGetFunction(&f, mod, name.c_str()));
+  funcs_[fk] = f;
+  return f;
+}
+
+}  // namespace pyc
+
+PYC_API void pyc_cache_stats(int64_t* compiled, int64_t* disk_hits, int64_t* mem_hits) {
+  pyc::CacheStats s = pyc::cache_stats();
+  if (compiled) *compiled = s.compiled;
+  if (disk_hits) *disk_hits = s.disk_hits;
+  if (mem_hits) *mem_hits = s.mem_hits;
+}

@@ -1,0 +1,389 @@
+"""Python binding of the pyc C ABI (``include/pyc.h``).
+
+Argument marshalling only: every entry point keeps the C name and forwards to
+``libpyc.so``; all work runs in the library and its generated kernels.  Device
+pointers are ints (e.g. ``tensor.data_ptr()``) and streams are raw handles
+(e.g. ``torch.cuda.current_stream().cuda_stream``).
+
+The paper-style front ends ``ElementwiseKernel`` and ``ReductionKernel`` (Sec.
+3.2.4 and 3.2.5) take torch tensors and Python scalars and marshal them in the
+declared order.  If the native library is missing, importing this module
+raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+
+from . import buildlib
+
+PYC_OK, PYC_E_PARSE, PYC_E_COMPILE, PYC_E_ARG, PYC_E_CUDA, PYC_E_NOMEM, PYC_E_BUSY, \
+    PYC_E_TIMEOUT, PYC_E_INTERNAL, PYC_E_NOTFOUND = range(10)
+STATUS_NAMES = {0: "PYC_OK", 1: "PYC_E_PARSE", 2: "PYC_E_COMPILE", 3: "PYC_E_ARG",
+                4: "PYC_E_CUDA", 5: "PYC_E_NOMEM", 6: "PYC_E_BUSY", 7: "PYC_E_TIMEOUT",
+                8: "PYC_E_INTERNAL", 9: "PYC_E_NOTFOUND"}
+
+PYC_F32, PYC_F64, PYC_BF16, PYC_F16, PYC_I32, PYC_I64, PYC_ARGMIN_F32, PYC_ARGMAX_F32, \
+    PYC_U8, PYC_I8, PYC_U32, PYC_U64, PYC_I16, PYC_U16 = range(14)
+
+# struct-module codes for packing scalars of each dtype (bf16/half packed as raw bits)
+_SCALAR_FMT = {PYC_F32: "f", PYC_F64: "d", PYC_I32: "i", PYC_I64: "q", PYC_U8: "B",
+               PYC_I8: "b", PYC_U32: "I", PYC_U64: "Q", PYC_I16: "h", PYC_U16: "H",
+               PYC_BF16: "H", PYC_F16: "e"}
+
+
+class PycError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+        self.message = message
+
+
+class pyc_opts(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("vec_bytes", ctypes.c_int),
+                ("items_per_thread", ctypes.c_int), ("compensated", ctypes.c_int),
+                ("fmad", ctypes.c_int), ("preamble", ctypes.c_char_p)]
+
+
+class pyc_param_info(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("is_pointer", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("elem_bytes", ctypes.c_int),
+                ("scalar_offset", ctypes.c_int), ("pointer_slot", ctypes.c_int),
+                ("read", ctypes.c_int), ("written", ctypes.c_int), ("lifted", ctypes.c_int)]
+
+
+class pyc_argf32(ctypes.Structure):
+    _fields_ = [("v", ctypes.c_float), ("pad", ctypes.c_int32), ("i", ctypes.c_int64)]
+
+
+# every symbol include/pyc.h declares (checked by the tests)
+EXPORTED = [
+    "pyc_last_error", "pyc_version",
+    "pyc_map_create", "pyc_map_launch", "pyc_map_num_params", "pyc_map_param",
+    "pyc_map_scalar_bytes", "pyc_map_source", "pyc_map_autotune", "pyc_map_destroy",
+    "pyc_reduce_create", "pyc_reduce_launch", "pyc_reduce_batched", "pyc_reduce_num_params",
+    "pyc_reduce_param", "pyc_reduce_scalar_bytes", "pyc_reduce_out_bytes", "pyc_reduce_source",
+    "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats",
+]
+
+_lib = None
+
+
+def default_cache_dir():
+    return os.path.join(buildlib.REPO_DIR, ".pyc_kcache")
+
+
+def load(build_if_missing=True):
+    """Load libpyc.so (building it in-tree if absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = buildlib.pyc_lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError("libpyc.so is not built: run __graft_entry__.build()")
+        buildlib.build_all()
+    os.environ.setdefault("PYC_CACHE_DIR", default_cache_dir())
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, cp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_char_p
+    st = ctypes.c_int
+    sig = {
+        "pyc_last_error": (cp, []),
+        "pyc_version": (cp, []),
+        "pyc_map_create": (st, [cp, cp, cp, ctypes.POINTER(pyc_opts), ctypes.POINTER(vp)]),
+        "pyc_map_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp]),
+        "pyc_map_num_params": (i32, [vp]),
+        "pyc_map_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
+        "pyc_map_scalar_bytes": (i32, [vp]),
+        "pyc_map_source": (cp, [vp]),
+        "pyc_map_autotune": (st, [vp, i64, vp]),
+        "pyc_map_destroy": (None, [vp]),
+        "pyc_reduce_create": (st, [i32, cp, cp, cp, cp, ctypes.POINTER(pyc_opts),
+                                   ctypes.POINTER(vp)]),
+        "pyc_reduce_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, vp]),
+        "pyc_reduce_batched": (st, [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(vp), vp, vp,
+                                    vp]),
+        "pyc_reduce_num_params": (i32, [vp]),
+        "pyc_reduce_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
+        "pyc_reduce_scalar_bytes": (i32, [vp]),
+        "pyc_reduce_out_bytes": (i32, [vp]),
+        "pyc_reduce_source": (cp, [vp]),
+        "pyc_reduce_autotune": (st, [vp, i64, vp]),
+        "pyc_reduce_destroy": (None, [vp]),
+        "pyc_cache_stats": (None, [ctypes.POINTER(i64)] * 3),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != PYC_OK:
+        raise PycError(status, load().pyc_last_error().decode(errors="replace"))
+
+
+def _enc(s):
+    return None if s is None else s.encode()
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, pyc_opts):
+        return ctypes.byref(opts)
+    o = pyc_opts()
+    for k, v in dict(opts).items():
+        if k == "preamble":
+            v = _enc(v)
+        setattr(o, k, v)
+    # keep the preamble bytes alive for the call
+    return ctypes.byref(o)
+
+
+def _ptr_array(ptrs):
+    ptrs = list(ptrs or [])
+    arr = (ctypes.c_void_p * max(1, len(ptrs)))(*[int(p) if p else None for p in ptrs])
+    return arr
+
+
+def _stream(stream):
+    return None if not stream else ctypes.c_void_p(int(stream))
+
+
+# ------------------------------------------------------------------ C-named calls
+
+def pyc_last_error() -> str:
+    return load().pyc_last_error().decode(errors="replace")
+
+
+def pyc_version() -> str:
+    return load().pyc_version().decode()
+
+
+def pyc_map_create(argspec, stmt, name=None, opts=None):
+    h = ctypes.c_void_p()
+    _check(load().pyc_map_create(_enc(argspec), _enc(stmt), _enc(name), _opts(opts),
+                                 ctypes.byref(h)))
+    return h
+
+
+def pyc_map_launch(h, n, ptrs, scalars=None, stream=None):
+    _check(load().pyc_map_launch(h, int(n), _ptr_array(ptrs), scalars, _stream(stream)))
+
+
+def pyc_map_destroy(h):
+    load().pyc_map_destroy(h)
+
+
+def pyc_map_source(h) -> str:
+    return load().pyc_map_source(h).decode()
+
+
+def pyc_map_autotune(h, n, stream=None):
+    _check(load().pyc_map_autotune(h, int(n), _stream(stream)))
+
+
+def pyc_reduce_create(out_dtype, neutral, reduce_expr, map_expr, argspec, opts=None):
+    h = ctypes.c_void_p()
+    _check(load().pyc_reduce_create(int(out_dtype), _enc(neutral), _enc(reduce_expr),
+                                    _enc(map_expr), _enc(argspec), _opts(opts), ctypes.byref(h)))
+    return h
+
+
+def pyc_reduce_launch(h, n, ptrs, scalars, d_out, stream=None):
+    _check(load().pyc_reduce_launch(h, int(n), _ptr_array(ptrs), scalars, d_out,
+                                    _stream(stream)))
+
+
+def pyc_reduce_batched(h, nseg, seg_offsets, ptrs, scalars, d_out, stream=None):
+    import numpy as np
+    off = np.ascontiguousarray(seg_offsets, dtype=np.int64)
+    if off.size != int(nseg) + 1:
+        raise ValueError("seg_offsets must hold nseg + 1 entries")
+    _check(load().pyc_reduce_batched(h, int(nseg),
+                                     off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     _ptr_array(ptrs), scalars, d_out, _stream(stream)))
+
+
+def pyc_reduce_destroy(h):
+    load().pyc_reduce_destroy(h)
+
+
+def pyc_reduce_source(h) -> str:
+    return load().pyc_reduce_source(h).decode()
+
+
+def pyc_reduce_out_bytes(h) -> int:
+    return load().pyc_reduce_out_bytes(h)
+
+
+def pyc_reduce_autotune(h, n, stream=None):
+    _check(load().pyc_reduce_autotune(h, int(n), _stream(stream)))
+
+
+def pyc_cache_stats():
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    load().pyc_cache_stats(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return {"compiled": a.value, "disk_hits": b.value, "mem_hits": c.value}
+
+
+def params(h, reduce=False):
+    """Declared parameters as dicts (name, is_pointer, dtype, ... )."""
+    lib = load()
+    num = (lib.pyc_reduce_num_params if reduce else lib.pyc_map_num_params)(h)
+    get = lib.pyc_reduce_param if reduce else lib.pyc_map_param
+    out = []
+    for k in range(num):
+        info = pyc_param_info()
+        _check(get(h, k, ctypes.byref(info)))
+        out.append({f: getattr(info, f) for f, _ in pyc_param_info._fields_})
+        out[-1]["name"] = out[-1]["name"].decode()
+    return out
+
+
+def pack_scalars(h, values, reduce=False):
+    """Pack scalar values in declaration order into the layout the handle expects
+    (Python ints/floats are converted to the declared C type, as in Listing 3a)."""
+    lib = load()
+    size = (lib.pyc_reduce_scalar_bytes if reduce else lib.pyc_map_scalar_bytes)(h)
+    buf = ctypes.create_string_buffer(max(size, 1))
+    scal = [p for p in params(h, reduce) if not p["is_pointer"]]
+    if len(scal) != len(values):
+        raise ValueError("expected %d scalars, got %d" % (len(scal), len(values)))
+    for p, v in zip(scal, values):
+        if p["dtype"] == PYC_BF16:
+            import torch
+            bits = torch.tensor([float(v)], dtype=torch.float32).to(torch.bfloat16).view(
+                torch.int16).item() & 0xFFFF
+            struct.pack_into("H", buf, p["scalar_offset"], bits)
+        else:
+            fmt = _SCALAR_FMT[p["dtype"]]
+            struct.pack_into(fmt, buf, p["scalar_offset"],
+                             float(v) if fmt in "fde" else int(v))
+    return buf
+
+
+# ------------------------------------------------------------------ paper-style front ends
+
+_TORCH_DT = None
+
+
+def _torch_dtype(d):
+    import torch
+    return {PYC_F32: torch.float32, PYC_F64: torch.float64, PYC_BF16: torch.bfloat16,
+            PYC_F16: torch.float16, PYC_I32: torch.int32, PYC_I64: torch.int64,
+            PYC_U8: torch.uint8, PYC_I8: torch.int8, PYC_I16: torch.int16,
+            PYC_U32: torch.uint32, PYC_U64: torch.uint64, PYC_U16: torch.uint16}[d]
+
+
+class _Front:
+    _reduce = False
+
+    def _marshal(self, args):
+        import torch
+        ps = self._params
+        if len(args) != len(ps):
+            raise TypeError("expected %d arguments, got %d" % (len(ps), len(args)))
+        ptrs, scal, n = [], [], None
+        for p, a in zip(ps, args):
+            if p["is_pointer"]:
+                if not isinstance(a, torch.Tensor) or not a.is_cuda:
+                    raise TypeError("argument %r must be a CUDA tensor" % p["name"])
+                if not a.is_contiguous():
+                    raise ValueError("argument %r must be contiguous" % p["name"])
+                if a.dtype != _torch_dtype(p["dtype"]):
+                    raise TypeError("argument %r has dtype %s, spec says %s"
+                                    % (p["name"], a.dtype, _torch_dtype(p["dtype"])))
+                if n is None:
+                    n = a.numel()
+                elif a.numel() != n:  # all arrays have the same length (Sec. 3.2.4)
+                    raise ValueError("all array arguments must have the same length")
+                ptrs.append(a.data_ptr())
+            else:
+                scal.append(a)
+        return ptrs, pack_scalars(self._h, scal, self._reduce), (n or 0)
+
+
+class ElementwiseKernel(_Front):
+    """z = ElementwiseKernel("float a, float *x, float b, float *y, float *z",
+    "z[i] = a*x[i] + b*y[i]"); z(5, x, 6, y, out) -- Listing 3a."""
+
+    def __init__(self, arguments, operation, name="kernel", **opts):
+        self._h = pyc_map_create(arguments, operation, name, opts or None)
+        self._params = params(self._h)
+
+    def __call__(self, *args, stream=None, n=None):
+        import torch
+        ptrs, sc, nn = self._marshal(args)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        pyc_map_launch(self._h, nn if n is None else n, ptrs, sc, s)
+
+    def autotune(self, n, stream=None):
+        pyc_map_autotune(self._h, n, stream)
+
+    @property
+    def source(self):
+        return pyc_map_source(self._h)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            pyc_map_destroy(self._h)
+
+
+class ReductionKernel(_Front):
+    """ReductionKernel(PYC_F32, neutral="0", reduce_expr="a+b", map_expr="x[i]*y[i]",
+    arguments="float *x, float *y") -- Listing 3b.  Calling it returns a one-element
+    device tensor: the result stays on the GPU (Sec. 3.2.5)."""
+    _reduce = True
+
+    def __init__(self, dtype_out, neutral, reduce_expr, map_expr=None, arguments=None, **opts):
+        self._h = pyc_reduce_create(dtype_out, neutral, reduce_expr, map_expr, arguments,
+                                    opts or None)
+        self._params = params(self._h, True)
+        self._out_dtype = dtype_out
+
+    def _out(self, count=1):
+        import torch
+        if self._out_dtype in (PYC_ARGMIN_F32, PYC_ARGMAX_F32):
+            return torch.empty((count, 2), dtype=torch.int64, device="cuda")
+        return torch.empty(count, dtype=_torch_dtype(self._out_dtype), device="cuda")
+
+    def __call__(self, *args, out=None, stream=None, n=None):
+        import torch
+        ptrs, sc, nn = self._marshal(args)
+        out = self._out() if out is None else out
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        pyc_reduce_launch(self._h, nn if n is None else n, ptrs, sc, out.data_ptr(), s)
+        return out
+
+    def batched(self, seg_offsets, *args, out=None, stream=None):
+        import torch
+        ptrs, sc, _ = self._marshal(args)
+        nseg = len(seg_offsets) - 1
+        out = self._out(nseg) if out is None else out
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        pyc_reduce_batched(self._h, nseg, seg_offsets, ptrs, sc, out.data_ptr(), s)
+        return out
+
+    def autotune(self, n, stream=None):
+        pyc_reduce_autotune(self._h, n, stream)
+
+    @property
+    def source(self):
+        return pyc_reduce_source(self._h)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            pyc_reduce_destroy(self._h)
+
+
+def argf32_from_tensor(t):
+    """Decode ARGMIN/ARGMAX results stored as int64 pairs: returns (values, indices)."""
+    import torch
+    t = t.reshape(-1, 2).contiguous()
+    words = t.view(torch.int32).reshape(-1, 4)  # little endian: word 0 is the value
+    return words[:, 0].contiguous().view(torch.float32), t[:, 1]

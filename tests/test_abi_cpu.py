@@ -1,0 +1,205 @@
+"""C-ABI checks that need no GPU: the library loads and exports every symbol
+include/pyc.h declares; arg-spec parsing, statement analysis, run-time
+compilation (NVRTC needs no GPU), the kernel cache and argument validation."""
+import json
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+from paper_1304_5553_gb300 import pyc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def test_exports_match_header():
+    hdr = open(os.path.join(ROOT, "include", "pyc.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    declared = set(re.findall(r"\b(pyc_[a-z_0-9]+)\s*\(", hdr))
+    lib = pyc.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(pyc.EXPORTED)
+    assert pyc.pyc_version().startswith("pyc ")
+
+
+@pytest.mark.parametrize("spec", [
+    "", "float", "float *", "char *x", "float **x", "float *x, float *x", "float i",
+    "float n", "float pyc_x", "float x;", "float *x) { } __global__ void evil(float *y",
+    "struct foo *x", "float *x,", "unsigned mystery x", "float *restrict", "float *__x",
+    "float # x", "float *x, int",
+])
+def test_bad_argspec(spec):
+    with pytest.raises(pyc.PycError) as e:
+        pyc.pyc_map_create(spec, "1")
+    assert e.value.status == pyc.PYC_E_PARSE, (spec, str(e.value))
+
+
+@pytest.mark.parametrize("stmt", [
+    "z[i] = 1; #include <stdio.h>", "z[i] = (1", "z[i] = 1)", "return", "goto out",
+    "z[i] = 1; /* open", "z[i] = 'a", "z[i] = pyc_r_z[0]", "z[i] = 1 }", "z[i] = `1`",
+    "asm(\"trap;\")",
+])
+def test_bad_statement(stmt):
+    with pytest.raises(pyc.PycError) as e:
+        pyc.pyc_map_create("float *z", stmt)
+    assert e.value.status == pyc.PYC_E_PARSE, (stmt, str(e.value))
+
+
+def test_compile_error_carries_log():
+    with pytest.raises(pyc.PycError) as e:
+        pyc.pyc_map_create("float *x", "x[i] = undefined_name * 2")
+    assert e.value.status == pyc.PYC_E_COMPILE
+    assert "undefined_name" in e.value.message and "error" in e.value.message
+
+
+def _info(spec, stmt):
+    h = pyc.pyc_map_create(spec, stmt)
+    try:
+        return {p["name"]: p for p in pyc.params(h)}, pyc.pyc_map_source(h)
+    finally:
+        pyc.pyc_map_destroy(h)
+
+
+def test_statement_analysis():
+    p, src = _info("float a, float *x, float b, float *y, float *z", "z[i] = a*x[i] + b*y[i]")
+    assert p["x"]["lifted"] and p["x"]["read"] and not p["x"]["written"]
+    assert p["z"]["lifted"] and p["z"]["written"] and not p["z"]["read"]
+    assert not p["a"]["is_pointer"] and p["a"]["scalar_offset"] == 0 and p["b"]["scalar_offset"] == 4
+    assert [p[k]["pointer_slot"] for k in "xyz"] == [0, 1, 2]
+    # in-place compound assignment (Listing 1): read and written
+    p, _ = _info("float *a", "a[i] *= 2")
+    assert p["a"]["lifted"] and p["a"]["read"] and p["a"]["written"]
+    # a conditional write must keep unwritten elements: the array is loaded too
+    p, _ = _info("float *x, float *z", "if (x[i] > 0) z[i] = 1")
+    assert p["z"]["read"] and p["z"]["written"]
+    p, _ = _info("float *x, float *z", "float t = x[i]; z[i] = t * t")
+    assert not p["z"]["read"] and p["z"]["written"]
+    # other index expressions or address-of keep the raw pointer
+    p, _ = _info("float *x, float *z", "z[i] = i + 1 < n ? x[i+1] : 0")
+    assert not p["x"]["lifted"] and p["z"]["lifted"]
+    p, _ = _info("float *x, float *z", "const float *q = &x[i]; z[i] = *q")
+    assert not p["x"]["lifted"]
+    # a binary '&' after an operand is not address-of
+    p, _ = _info("int *x, int *z", "z[i] = 3 & x[i]")
+    assert p["x"]["lifted"]
+    # member-like names are not the parameter
+    p, _ = _info("float *x, float *z", "float2 v; v.x = 1.f; z[i] = v.x + x[i]")
+    assert p["x"]["lifted"]
+
+
+def test_scalar_layout_and_source():
+    h = pyc.pyc_map_create("double a, float b, int *x, short c, __nv_bfloat16 d, float *z",
+                           "z[i] = a*x[i] + b + c + d")
+    try:
+        p = {q["name"]: q for q in pyc.params(h)}
+        assert (p["a"]["scalar_offset"], p["b"]["scalar_offset"], p["c"]["scalar_offset"],
+                p["d"]["scalar_offset"]) == (0, 8, 12, 14)
+        assert pyc.load().pyc_map_scalar_bytes(h) == 16
+        assert p["d"]["dtype"] == pyc.PYC_BF16 and p["x"]["dtype"] == pyc.PYC_I32
+        src = pyc.pyc_map_source(h)
+        for v in ("v16_u1", "v16_u2", "v16_u4", "v32_u1", "v32_u2", "v32_u4"):
+            assert "pyc_map_" + v in src
+        assert "ld.global.L1::no_allocate.v4.u32" in src and "ld.global.L1::no_allocate.v8.u32" in src
+        assert re.search(r"pyc_r_x\s*\[\s*pyc_k\s*\]", src)
+        assert re.search(r"pyc_r_z\s*\[\s*pyc_k\s*\]", src)
+    finally:
+        pyc.pyc_map_destroy(h)
+
+
+def test_reduce_create_validation():
+    cases = [
+        (pyc.PYC_F32, "-INFINITY", "a > b ? a : b", None, "float *x", {"compensated": 1}),
+        (pyc.PYC_F64, "0", "a+b", None, "double *x", {"compensated": 1}),
+        (pyc.PYC_ARGMIN_F32, "0", None, None, "float *x", {}),
+        (pyc.PYC_F32, "0", "a+b", None, "float *x, float *y", {}),
+        (pyc.PYC_U8, "0", "a+b", None, "unsigned char *x", {}),
+        (pyc.PYC_F32, None, "a+b", None, "float *x", {}),
+        (pyc.PYC_F32, "0", "a+b", None, "float *x", {"block": 100}),
+        (pyc.PYC_F32, "0", "a+b", None, "float *x", {"items_per_thread": 3}),
+        (pyc.PYC_F32, "0", "a+b; }", None, "float *x", {}),
+    ]
+    for dt, neu, red, m, spec, o in cases:
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_reduce_create(dt, neu, red, m, spec, o or None)
+        assert e.value.status in (pyc.PYC_E_ARG, pyc.PYC_E_PARSE), (dt, neu, red, spec, o)
+    h = pyc.pyc_reduce_create(pyc.PYC_ARGMIN_F32, None, None, None, "float *x")
+    assert pyc.pyc_reduce_out_bytes(h) == 16
+    pyc.pyc_reduce_destroy(h)
+    h = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", None, "float *x", {"compensated": 1})
+    assert "pyc_two_sum" in pyc.pyc_reduce_source(h) and pyc.pyc_reduce_out_bytes(h) == 4
+    pyc.pyc_reduce_destroy(h)
+
+
+def test_batched_validation_before_any_gpu_work():
+    h = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i]", "float *x, float *y")
+    try:
+        with pytest.raises(pyc.PycError) as e:  # decreasing offsets
+            pyc.pyc_reduce_batched(h, 2, [0, 5, 3], [1 << 20, 1 << 21], None, 1 << 22)
+        assert e.value.status == pyc.PYC_E_ARG
+        pyc.pyc_reduce_batched(h, 0, [0], [1 << 20, 1 << 21], None, 1 << 22)  # no-op
+    finally:
+        pyc.pyc_reduce_destroy(h)
+
+
+@pytest.mark.skipif(_has_gpu(), reason="checks the no-driver error path")
+def test_launch_without_driver_is_an_error():
+    h = pyc.pyc_map_create("float *x", "x[i] = 1")
+    try:
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_map_launch(h, 10, [1 << 20])
+        assert e.value.status == pyc.PYC_E_CUDA
+    finally:
+        pyc.pyc_map_destroy(h)
+
+
+_CACHE_CHILD = r"""
+import json, sys
+sys.path.insert(0, %r)
+from paper_1304_5553_gb300 import pyc
+h = pyc.pyc_map_create("float *x, float *z", sys.argv[1])
+h2 = pyc.pyc_map_create("float *x, float *z", sys.argv[1])
+print(json.dumps(pyc.pyc_cache_stats()))
+"""
+
+
+def test_kernel_cache_memory_and_disk(tmp_path):
+    env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
+    code = _CACHE_CHILD % ROOT
+
+    def run(stmt):
+        out = subprocess.run([sys.executable, "-c", code, stmt], env=env, capture_output=True,
+                             text=True, check=True).stdout
+        return json.loads(out.strip().splitlines()[-1])
+
+    a = run("z[i] = 3 * x[i]")
+    assert a == {"compiled": 1, "disk_hits": 0, "mem_hits": 1}
+    b = run("z[i] = 3 * x[i]")  # new process: loaded from disk, no compile
+    assert b == {"compiled": 0, "disk_hits": 1, "mem_hits": 1}
+    c = run("z[i] = 4 * x[i]")  # a changed kernel recompiles
+    assert c["compiled"] == 1
+    # a corrupted cache file is ignored and rewritten
+    for f in os.listdir(tmp_path):
+        if f.endswith(".pyck"):
+            open(os.path.join(tmp_path, f), "wb").write(b"garbage")
+    d = run("z[i] = 3 * x[i]")
+    assert d["compiled"] == 1 and d["disk_hits"] == 0
+
+
+def test_front_end_params():
+    k = pyc.ElementwiseKernel("float a, float *x, float b, float *y, float *z",
+                              "z[i] = a*x[i] + b*y[i]", "linear_combination")
+    assert [p["name"] for p in k._params] == ["a", "x", "b", "y", "z"]
+    buf = pyc.pack_scalars(k._h, [5, 6])  # Listing 3a passes ints for float params
+    import struct
+    assert struct.unpack_from("ff", buf, 0) == (5.0, 6.0)

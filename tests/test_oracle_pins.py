@@ -131,6 +131,29 @@ def test_map_lin_comb_listing3a_int_scalars():
     assert z[0] == 294.0 and z[49] == 5 * 49 * 0.25
 
 
+@pytest.mark.parametrize("out_bf16", [False, True])
+def test_map_lin_comb_f32ops_rounds_each_op(out_bf16):
+    # each binary32 operation is the correctly rounded exact result (checked with
+    # fractions), applied in source order; numpy's binary32 arithmetic agrees
+    n = 2000
+    x = inputs.uniform_f32(16, 0, n, -2.0, 2.0)
+    y = inputs.uniform_f32(16, 1, n, -2.0, 2.0)
+    a, b = np.float32(2.5), np.float32(-0.75)
+    z = oracle.map_lin_comb_f32ops(a, x, b, y, out_bf16=out_bf16)
+    ref = (a * x + b * y).astype(np.float32)
+    if out_bf16:
+        ref = inputs.to_bf16_values(ref)
+    assert np.array_equal(z, ref)
+    for i in range(0, n, 37):
+        p = Fraction(float(a)) * _fr(x[i])
+        lo, hi = _neighbours_f32(np.float32(a) * x[i])
+        assert _is_nearest(p, float(np.float32(a) * x[i]), lo, hi)
+    # differs from the binary64-then-round reference somewhere (cancellation)
+    z64r, _, _ = oracle.map_lin_comb(2.5, x, -0.75, y)
+    if not out_bf16:
+        assert not np.array_equal(z, z64r)
+
+
 def test_map_gauss_sin_mpmath():
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 40
@@ -288,7 +311,10 @@ def test_max_min_argmin_argmax():
         assert i == int(np.argmax(x)) and v == x.max()
         assert oracle.argmin_f32(-x)[1] == int(np.argmax(x))
     # neutral for n = 0
-    assert oracle.argmin_f32(np.zeros(0, np.float32)) == (float("inf"), -1)
+    assert oracle.argmin_f32(np.zeros(0, np.float32)) == (float("inf"), 2 ** 63 - 1)
+    assert oracle.argmax_f32(np.zeros(0, np.float32)) == (float("-inf"), 2 ** 63 - 1)
+    # infinities are values like any other: the first one wins
+    assert oracle.argmin_f32(np.full(3, np.inf, np.float32)) == (float("inf"), 0)
     assert oracle.max_f32(np.zeros(0, np.float32)) == float("-inf")
     # minima only at the last index; all equal -> index 0
     x = np.ones(1000, np.float32)
