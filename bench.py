@@ -1,0 +1,452 @@
+"""Benchmark of the map / map-reduce path on GB300.
+
+One step = the three elementwise maps at n = 2^28 (the headline workload):
+  z = a*x + b*y in binary32, the same in bfloat16 storage, and the four-input
+  z = x*exp(-y*y) + sin(u)*w in binary32; a = 2.5, b = -0.75, inputs
+  uniform[-2, 2) from the seeded generator.
+value = algorithmic HBM bytes of a step / device time of a step (GB/s); each
+input is 0.5-1 GiB, far above the 129 MB L2, so no flush is needed.
+
+Also measured (in "details"): the n = 2^28 reductions, the n = 2^20 dot
+latency, and the 20,000-segment batched dot against per-segment launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs the same workload on its own GPU (independent
+replicas, weak scaling); rank 0 prints one JSON line.  --impl reference times
+the CPU oracle on the host cores instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "achieved HBM GB/s (% of GB300 peak) for map/map-reduce; batched reqs/s with p50/p99 latency"
+N_MAP = 1 << 28  # may be lowered by --n-log2 (profiling captures only)
+A, B = 2.5, -0.75
+MAP_BYTES = {"lin_comb_f32": 12, "lin_comb_bf16": 6, "gauss_sin_f32": 20}  # per element
+WORKLOAD = ("maps n=2^28: z=a*x+b*y f32 + z=a*x+b*y bf16 storage + "
+            "z=x*exp(-y*y)+sin(u)*w f32; a=2.5 b=-0.75; inputs uniform[-2,2) seeded")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def make_map_inputs(torch, dev, only=None):
+    from paper_1304_5553_gb300 import inputs
+    n = N_MAP
+    want = set(only.split(",")) if only else set(MAP_BYTES)
+    host = {}
+    if want & {"lin_comb_f32", "lin_comb_bf16"}:
+        x = inputs.uniform_f32(0, 0, n, -2.0, 2.0)
+        y = inputs.uniform_f32(0, 1, n, -2.0, 2.0)
+        if "lin_comb_f32" in want:
+            host["lin_comb_f32"] = [x, y]
+        if "lin_comb_bf16" in want:
+            host["lin_comb_bf16"] = [inputs.to_bf16_values(x), inputs.to_bf16_values(y)]
+    if "gauss_sin_f32" in want:
+        host["gauss_sin_f32"] = [inputs.uniform_f32(1, s, n, -2.0, 2.0) for s in range(4)]
+    d = {}
+    for k, arrs in host.items():
+        dt = torch.bfloat16 if k.endswith("bf16") else torch.float32
+        ins = [torch.from_numpy(a).to(dt).to(dev) for a in arrs]
+        d[k] = ins + [torch.empty(n, dtype=dt, device=dev)]
+    return host, d
+
+
+def map_launchers(torch, pyc, stock, d, stream):
+    """name -> zero-argument launch of that map through the C ABI."""
+    out = {}
+    for k, bufs in d.items():
+        h = stock.create(k)
+        sc = pyc.pack_scalars(h, [A, B]) if k.startswith("lin_comb") else None
+        ptrs = [b.data_ptr() for b in bufs]
+        out[k] = (lambda h=h, ptrs=ptrs, sc=sc: pyc.pyc_map_launch(h, N_MAP, ptrs, sc, stream))
+    return out
+
+
+def time_steps(torch, launchers, names, steps, warmup, barrier):
+    """Time `steps` steps (each: every named launch once), recording an event pair
+    around every launch on the launching stream."""
+    for _ in range(warmup):
+        for k in names:
+            launchers[k]()
+    torch.cuda.synchronize()
+    ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)] for k in names}
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t0.record()
+    for s in range(steps):
+        for k in names:
+            ev[k][s][0].record()
+            launchers[k]()
+            ev[k][s][1].record()
+    t1.record()
+    torch.cuda.synchronize()
+    barrier()
+    total_ms = t0.elapsed_time(t1)
+    per = {k: [a.elapsed_time(b) for a, b in ev[k]] for k in names}
+    return total_ms, per
+
+
+def bench_e2e(torch, pyc, stock, host, dev, steps=3, warmup=1):
+    """Same step through the C ABI with HOST buffers: pinned inputs copied in, the
+    three maps, outputs copied back, all inside the timed region."""
+    pinned = {k: [torch.from_numpy(a).to(torch.bfloat16 if k.endswith("bf16") else torch.float32)
+                  .pin_memory() for a in arrs] for k, arrs in host.items()}
+    outs_h = {k: torch.empty(N_MAP, dtype=pinned[k][0].dtype).pin_memory() for k in pinned}
+    dbufs = {k: [torch.empty(N_MAP, dtype=p[0].dtype, device=dev) for _ in range(len(p) + 1)]
+             for k, p in pinned.items()}
+    stream = torch.cuda.current_stream()
+    launch = map_launchers(torch, pyc, stock, dbufs, stream.cuda_stream)
+    h2d = sum(t.numel() * t.element_size() for p in pinned.values() for t in p)
+    d2h = sum(t.numel() * t.element_size() for t in outs_h.values())
+
+    def step():
+        for k in pinned:
+            for src, dst in zip(pinned[k], dbufs[k]):
+                dst.copy_(src, non_blocking=True)
+            launch[k]()
+            outs_h[k].copy_(dbufs[k][-1], non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    alg = sum(MAP_BYTES[k] for k in pinned) * N_MAP
+    del dbufs, pinned, outs_h
+    return {"value": round(alg / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
+            "steps": steps}
+
+
+def bench_reductions(torch, pyc, stock, dev, reps=20):
+    """n = 2^28 reductions and the n = 2^20 dot: mean device time over reps."""
+    from paper_1304_5553_gb300 import inputs
+    n = N_MAP
+    res = {}
+    s = torch.cuda.current_stream().cuda_stream
+    ln = torch.from_numpy(inputs.lognormal_signed_f32(0, 0, n)).to(dev)
+    xi = torch.from_numpy(inputs.int_uniform_i32(0, 0, n)).to(dev)
+    xa = torch.from_numpy(inputs.argmin_with_minima(0, n)).to(dev)
+    out = torch.zeros(2, dtype=torch.int64, device=dev)
+    cases = [("sum_f32", ln, 4), ("sum_f32_comp", ln, 4), ("sum_i32_i64", xi, 4),
+             ("max_f32", ln, 4), ("argmin_f32", xa, 4)]
+    for name, arr, bpe in cases:
+        h = stock.create(name)
+        f = (lambda h=h, arr=arr: pyc.pyc_reduce_launch(h, n, [arr.data_ptr()], None,
+                                                         out.data_ptr(), s))
+        ms = _time_fn(torch, f, reps)
+        res[name] = {"n": n, "us": round(ms * 1e3, 2), "GB/s": round(bpe * n / (ms * 1e-3) / 1e9, 1)}
+    del ln, xi, xa
+    # small dot: latency-bound (8 MiB fits in L2: warm timing)
+    m = 1 << 20
+    x = torch.from_numpy(inputs.uniform_f32(0, 0, m, -1.0, 1.0)).to(dev)
+    y = torch.from_numpy(inputs.uniform_f32(0, 1, m, -1.0, 1.0)).to(dev)
+    h = stock.create("dot_f32")
+    f = lambda: pyc.pyc_reduce_launch(h, m, [x.data_ptr(), y.data_ptr()], None, out.data_ptr(), s)
+    ms = _time_fn(torch, f, 200)
+    res["dot_f32_n2^20"] = {"n": m, "us": round(ms * 1e3, 2),
+                            "GB/s": round(8 * m / (ms * 1e-3) / 1e9, 1), "cache": "warm (fits L2)"}
+    return res
+
+
+def _time_fn(torch, f, reps, warmup=3):
+    for _ in range(warmup):
+        f()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        f()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_batched(torch, pyc, stock, dev, reps=5):
+    """20,000 segments, lengths log-uniform in [1, 2^20], dot per segment: one
+    persistent launch (graph replay) vs one launch per segment."""
+    from paper_1304_5553_gb300 import inputs
+    lens = inputs.segment_lengths()
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    total = int(off[-1])
+    res = {"segments": int(lens.size), "elements": total}
+    s = torch.cuda.current_stream().cuda_stream
+    for name, dt, bpe in (("dot_f32", torch.float32, 8), ("dot_bf16", torch.bfloat16, 4)):
+        x = torch.from_numpy(inputs.uniform_f32(2, 0, total, -1.0, 1.0)).to(dt).to(dev)
+        y = torch.from_numpy(inputs.uniform_f32(2, 1, total, -1.0, 1.0)).to(dt).to(dev)
+        out = torch.zeros(lens.size, dtype=torch.float32, device=dev)
+        h = stock.create(name)
+        ptrs = [x.data_ptr(), y.data_ptr()]
+        fb = lambda: pyc.pyc_reduce_batched(h, lens.size, off, ptrs, None, out.data_ptr(), s)
+        ms_b = _time_fn(torch, fb, reps)
+
+        def per_seg():
+            es = x.element_size()
+            for k in range(lens.size):
+                pyc.pyc_reduce_launch(h, int(lens[k]), [x.data_ptr() + int(off[k]) * es,
+                                                       y.data_ptr() + int(off[k]) * es],
+                                      None, out.data_ptr() + 4 * k, s)
+        ms_p = _time_fn(torch, per_seg, 1, warmup=1)
+        res[name] = {"batched_ms": round(ms_b, 3), "per_segment_launches_ms": round(ms_p, 3),
+                     "speedup": round(ms_p / ms_b, 2),
+                     "batched_GB/s": round(bpe * total / (ms_b * 1e-3) / 1e9, 1),
+                     "reqs/s": round(lens.size / (ms_b * 1e-3), 1)}
+        del x, y
+        torch.cuda.empty_cache()
+    return res
+
+
+def cpu_oracle_maps(n_sample, steps=1):
+    """The oracle (single-threaded C) on the three maps over n_sample elements."""
+    import oracle
+    from paper_1304_5553_gb300 import inputs
+    x = inputs.uniform_f32(0, 0, n_sample, -2.0, 2.0)
+    y = inputs.uniform_f32(0, 1, n_sample, -2.0, 2.0)
+    bx, by = inputs.to_bf16_values(x), inputs.to_bf16_values(y)
+    g = [inputs.uniform_f32(1, s, n_sample, -2.0, 2.0) for s in range(4)]
+    oracle.map_lin_comb(A, x[:16], B, y[:16])  # load the library outside the timing
+    t = time.perf_counter()
+    for _ in range(steps):
+        oracle.map_lin_comb(A, x, B, y)
+        oracle.map_lin_comb(A, bx, B, by, out_bf16=True)
+        oracle.map_gauss_sin(*g)
+    sec = (time.perf_counter() - t) / steps
+    alg = sum(MAP_BYTES.values()) * n_sample
+    return alg / sec / 1e9, sec
+
+
+def run_gpu(args):
+    import torch
+    from paper_1304_5553_gb300 import pyc, stock
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stock.compile_all()
+    host, d = make_map_inputs(torch, dev, args.only)
+    stream = torch.cuda.current_stream().cuda_stream
+    launch = map_launchers(torch, pyc, stock, d, stream)
+    if args.autotune == "on":
+        for k in launch:
+            pyc.pyc_map_autotune(stock.create(k), N_MAP, stream)
+    torch.cuda.synchronize()
+
+    # CPU baseline first (rank 0, N = 1 only): the oracle on a bounded sample
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n_s = 1 << 25
+        gbs, sec = cpu_oracle_maps(n_s)
+        cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "the three maps over the first 2^25 elements of the same inputs "
+                         "(%.1f s on one host core)" % sec}
+
+    names = [k for k in MAP_BYTES if not args.only or k in args.only.split(",")]
+    with ClockSampler(local) as clk:
+        total_ms, per = time_steps(torch, launch, names, args.steps, args.warmup, barrier)
+    clocks = clk.summary()
+    ms_step = total_ms / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    step_bytes = sum(MAP_BYTES[k] for k in names) * N_MAP
+    if args.n_log2 != 28 or args.only:
+        print("note: reduced profiling configuration, not a bench value", file=sys.stderr)
+    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    avg = {k: statistics.mean(v) for k, v in per.items()}
+    dom = max(avg, key=lambda k: avg[k])
+    ach = MAP_BYTES[dom] * N_MAP / (avg[dom] * 1e-3) / 1e9
+    kernels = {k: {"avg_us": round(avg[k] * 1e3, 2),
+                   "GB/s": round(MAP_BYTES[k] * N_MAP / (avg[k] * 1e-3) / 1e9, 1),
+                   "frac_of_%s_peak" % peak_kind: round(MAP_BYTES[k] * N_MAP / (avg[k] * 1e-3) / 1e9 / peak, 4)}
+               for k in names}
+
+    details = {"maps": kernels}
+    e2e = None
+    if rank == 0 and not args.quick:
+        details["reductions"] = bench_reductions(torch, pyc, stock, dev)
+        details["batched"] = bench_batched(torch, pyc, stock, dev)
+    if not args.quick:
+        del d, launch
+        torch.cuda.empty_cache()
+        e2e = bench_e2e(torch, pyc, stock, host, dev)
+        e2e["value"] = round(e2e["value"] * world, 2)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic (seeded uniform[-2,2))",
+            "config": {"workload": WORKLOAD, "n": N_MAP, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "traffic": None,
+                         "kernel": "pyc_map (%s)" % dom, "peak_kind": peak_kind},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(names) * args.steps,
+            "clocks": clocks, "details": details,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_s = 1 << 20  # bounded sample per step
+    import oracle
+    oracle.build()
+    cpu_oracle_maps(1 << 12)
+    for _ in range(args.warmup):
+        cpu_oracle_maps(n_s)
+    t = time.perf_counter()
+    secs = []
+    for _ in range(args.steps):
+        _, sec = cpu_oracle_maps(n_s)
+        secs.append(sec)
+    total = sum(secs)
+    alg = sum(MAP_BYTES.values()) * n_s
+    value = alg * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded uniform[-2,2))",
+        "config": {"workload": WORKLOAD, "n": N_MAP, "sample_per_step": n_s},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: the three maps over 2^20 elements of the same "
+                                   "inputs (binary64 oracle, one host core)"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": round(time.perf_counter() - t, 2),
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pyc", choices=["pyc", "reference"])
+    ap.add_argument("--quick", action="store_true", help="maps only (no details, no e2e)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--only", default="", help="comma-separated subset of the maps (profiling)")
+    ap.add_argument("--n-log2", type=int, default=28, help="map size (profiling captures only)")
+    ap.add_argument("--autotune", default="on", choices=["on", "off"],
+                    help="off: use the tuning cache / defaults without timing candidates")
+    args = ap.parse_args()
+    global N_MAP
+    N_MAP = 1 << args.n_log2
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -18,6 +18,15 @@ bool g_loaded = false;
 std::string g_load_error;
 std::once_flag g_once;
 
+// Stringise a name after macro expansion: cuda.h maps e.g. cuMemAlloc to
+// cuMemAlloc_v2, so this yields the exact exported symbol whose signature the
+// header declares -- the binding a link against libcuda would make.  (A
+// version-keyed lookup is not used: for some entry points, e.g.
+// cuCtxGetDevice, the CUDA 13 table returns a newer form with an extra
+// argument that the header does not remap.)
+#define PYC_XSTR(x) PYC_STR(x)
+#define PYC_STR(x) #x
+
 void load_driver() {
   void* h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_GLOBAL);
   if (!h) h = dlopen("libcuda.so", RTLD_NOW | RTLD_GLOBAL);
@@ -25,22 +34,13 @@ void load_driver() {
     g_load_error = "CUDA driver (libcuda.so.1) not found: no GPU driver on this machine";
     return;
   }
-  auto gpa = reinterpret_cast<decltype(&::cuGetProcAddress)>(dlsym(h, "cuGetProcAddress_v2"));
-  if (!gpa) {
-    g_load_error = "CUDA driver too old: cuGetProcAddress_v2 missing";
-    return;
-  }
   std::string missing;
   auto resolve = [&](void** slot, const char* name) {
-    CUdriverProcAddressQueryResult q;
-    if (gpa(name, slot, 13000, CU_GET_PROC_ADDRESS_DEFAULT, &q) != CUDA_SUCCESS ||
-        q != CU_GET_PROC_ADDRESS_SUCCESS || *slot == nullptr) {
-      *slot = nullptr;
-      missing += std::string(missing.empty() ? "" : ", ") + name;
-    }
+    *slot = dlsym(h, name);
+    if (!*slot) missing += std::string(missing.empty() ? "" : ", ") + name;
   };
   Driver& d = g_drv;
-#define PYC_DRV_FN(name) resolve(reinterpret_cast<void**>(&d.name), #name);
+#define PYC_DRV_FN(name) resolve(reinterpret_cast<void**>(&d.name), PYC_XSTR(name));
 #include "cudrv_fns.inc"
 #undef PYC_DRV_FN
   if (!missing.empty()) {

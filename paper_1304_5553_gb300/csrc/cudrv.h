@@ -3,7 +3,8 @@
 // The library is usable without a GPU for everything up to a launch
 // (parsing, source generation, run-time compilation, caching), so it does not
 // link libcuda: the driver is opened with dlopen on first use and every entry
-// point is resolved through cuGetProcAddress for the CUDA 13.0 ABI.
+// point is resolved by the exact (versioned) symbol its cuda.h declaration
+// names.
 #pragma once
 
 #include <cuda.h>
