@@ -1,5 +1,6 @@
 // C ABI: map and map-reduce creation and launches (see include/pyc.h).
 #include <algorithm>
+#include <cctype>
 #include <cstring>
 
 #include "cudrv.h"
@@ -11,6 +12,15 @@ int size_bucket(int64_t n) {
   int bl = 0;
   for (uint64_t v = (uint64_t)(n > 0 ? n : 1); v; v >>= 1) ++bl;
   return bl / 2;
+}
+
+std::string kernel_tag(const char* name, char prefix, const std::string& spec_text) {
+  std::string t;
+  if (name)
+    for (const char* c = name; *c && t.size() < 40; ++c)
+      t += (std::isalnum((unsigned char)*c) ? *c : '_');
+  if (t.empty()) t = std::string(1, prefix) + digest(spec_text).substr(0, 8);
+  return t;
 }
 
 LaunchCfg choose_cfg(HandleBase& h, int64_t n, bool reduce) {
@@ -170,7 +180,7 @@ void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
   std::vector<unsigned char> args = pack_args(h->spec, ptrs, scalars);
   int64_t head = vector_head(h->spec, ptrs, cfg.v.vec_bytes, h->min_bytes, n);
   if (n == 0) return;
-  CUfunction f = h->mod->function("pyc_map_" + variant_suffix(cfg.v));
+  CUfunction f = h->mod->function(h->kname("pyc_map", cfg.v));
   int resident = resident_ctas(f, cfg.block);
   int64_t tile = (int64_t)cfg.block * (cfg.v.vec_bytes / h->min_bytes) * cfg.v.unroll;
   int64_t nfull = head >= 0 ? (n - head) / tile : 0;
@@ -210,7 +220,7 @@ void launch_reduce(pyc_reduce* h, const LaunchCfg& cfg, int64_t n, void* const* 
     fail(PYC_E_ARG, "d_out is not aligned to the result type");
   std::vector<unsigned char> args = pack_args(h->spec, ptrs, scalars);
   int64_t head = vector_head(h->spec, ptrs, cfg.v.vec_bytes, h->min_bytes, n);
-  CUfunction f = h->mod->function("pyc_reduce_" + variant_suffix(cfg.v));
+  CUfunction f = h->mod->function(h->kname("pyc_reduce", cfg.v));
   int resident = resident_ctas(f, cfg.block);
   int64_t tile = (int64_t)cfg.block * (cfg.v.vec_bytes / h->min_bytes) * cfg.v.unroll;
   ChunkPlan cp = plan_chunks(n, head, tile, resident);
@@ -242,7 +252,9 @@ PYC_API pyc_status pyc_map_create(const char* argspec, const char* stmt, const c
     h->name = name ? name : "map";
     h->spec = parse_argspec(argspec);
     std::string rw = analyze_and_rewrite(h->spec, stmt, false);
-    h->source = generate_map(h->spec, rw, h->preamble).source;
+    h->tag = kernel_tag(name, 'm', h->spec.canonical + "|" + rw);
+    h->gen = generate_map(h->spec, rw, h->preamble, h->tag);
+    h->source = h->gen.source;
     finish_handle(*h, false);
     *out = h.release();
   });
@@ -333,7 +345,10 @@ PYC_API pyc_status pyc_reduce_create(pyc_dtype out_dtype, const char* neutral,
         h->kind = ReduceKind::Compensated;
       }
     }
-    h->gen = generate_reduce(h->spec, out_dtype, h->kind, neu, red, mrw, h->preamble);
+    h->tag = kernel_tag(nullptr, 'r',
+                        h->spec.canonical + "|" + std::to_string((int)out_dtype) + "|" + neu +
+                            "|" + red + "|" + mrw + "|" + std::to_string((int)h->kind));
+    h->gen = generate_reduce(h->spec, out_dtype, h->kind, neu, red, mrw, h->preamble, h->tag);
     h->source = h->gen.source;
     finish_handle(*h, true);
     *out = h.release();

@@ -163,7 +163,7 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
   if (!items.empty()) PYC_CU(d.cuMemcpyHtoD(plan->items, items.data(), items.size() * sizeof(Item)));
   PYC_CU(d.cuMemsetD8(plan->tickets, 0, b_tickets + b_ctl));
 
-  plan->f = h->mod->function("pyc_rbatch_" + variant_suffix(cfg.v));
+  plan->f = h->mod->function(h->kname("pyc_rbatch", cfg.v));
   int resident = resident_ctas(plan->f, cfg.block);
   plan->grid = std::max(1, std::min(resident, plan->nitems));
 

@@ -323,7 +323,8 @@ std::string scalar_io(const ArgSpec& spec, bool load) {
 
 }  // namespace
 
-MapGen generate_map(const ArgSpec& spec, const std::string& stmt, const std::string& preamble) {
+MapGen generate_map(const ArgSpec& spec, const std::string& stmt, const std::string& preamble,
+                    const std::string& tag) {
   const int mins = lifted_min_bytes(spec);
   std::ostringstream o;
   o << "// pyc map kernel: " << spec.canonical << "\n";
@@ -380,17 +381,130 @@ __device__ __forceinline__ void pyc_map_body(const pyc_args& pyc_p, const pyc_i6
   o << "      { const int pyc_k = 0; (void)pyc_k; " << stmt << " ; }\n";
   o << scalar_io(spec, false);
   o << "  }\n}\n\n";
-  for (auto& v : all_variants()) {
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_map_" << variant_suffix(v)
-      << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 pyc_head) {\n"
-      << "  pyc_map_body<" << v.vec_bytes << ", " << v.unroll << ">(pyc_p, n, pyc_head);\n}\n";
+  // Span form for batched launches: [vs, ve) aligned vector body plus the
+  // scalar range [ss, se), processed by a group of nthr threads (a CTA).
+  o << R"PYC(template <int VB, int U>
+__device__ __forceinline__ void pyc_map_span(const pyc_args& pyc_p, const pyc_i64 n,
+    const pyc_i64 pyc_vs, const pyc_i64 pyc_ve, const pyc_i64 pyc_ss, const pyc_i64 pyc_se,
+    const int pyc_tid, const int pyc_nthr) {
+  constexpr int E = VB / PYC_MIN_BYTES;
+  constexpr int T = E * U;
+)PYC";
+  o << aliases(spec, "pyc_p");
+  o << R"PYC(  (void)n;
+  const pyc_i64 pyc_step = (pyc_i64)pyc_nthr * E;
+  const pyc_i64 pyc_tile = pyc_step * U;
+  const pyc_i64 pyc_nt = pyc_ve > pyc_vs ? (pyc_ve - pyc_vs) / pyc_tile : 0;
+  for (pyc_i64 pyc_t = 0; pyc_t < pyc_nt; ++pyc_t) {
+    const pyc_i64 pyc_b0 = pyc_vs + pyc_t * pyc_tile + (pyc_i64)pyc_tid * E;
+    {
+)PYC";
+  o << reg_decls(spec, "T");
+  o << R"PYC(#pragma unroll
+      for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+)PYC";
+  o << group_io(spec, true);
+  o << R"PYC(      }
+#pragma unroll
+      for (int pyc_k = 0; pyc_k < T; ++pyc_k) {
+        const pyc_i64 i = pyc_b0 + (pyc_i64)(pyc_k / E) * pyc_step + (pyc_k % E);
+        (void)i;
+        { )PYC" << stmt << R"PYC( ; }
+      }
+#pragma unroll
+      for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+)PYC";
+  o << group_io(spec, false);
+  o << R"PYC(      }
+    }
   }
-  return {o.str()};
+  const pyc_i64 pyc_r0 = pyc_vs + pyc_nt * pyc_tile;
+  const pyc_i64 pyc_ns = pyc_se - pyc_ss;
+  const pyc_i64 pyc_nr = (pyc_ve > pyc_r0 ? pyc_ve - pyc_r0 : 0) + pyc_ns;
+  for (pyc_i64 pyc_j = pyc_tid; pyc_j < pyc_nr; pyc_j += pyc_nthr) {
+    const pyc_i64 i = pyc_j < pyc_ns ? pyc_ss + pyc_j : pyc_r0 + (pyc_j - pyc_ns);
+)PYC";
+  o << reg_decls(spec, "1");
+  o << scalar_io(spec, true);
+  o << "      { const int pyc_k = 0; (void)pyc_k; " << stmt << " ; }\n";
+  o << scalar_io(spec, false);
+  o << R"PYC(  }
+}
+
+// Batched map: one record per request, one work item per chunk.
+struct pyc_mtask {
+  pyc_args args;
+  pyc_i64 n;
+  pyc_i64 head;   // vector body start (-1: scalar only)
+  pyc_i64 chunk;  // chunk length (a multiple of the tile)
+};
+struct pyc_mitem {
+  int task;
+  int chunk;
+};
+
+template <int VB, int U>
+__device__ __forceinline__ void pyc_map_batched_body(const pyc_mtask* __restrict__ tasks,
+    const pyc_mitem* __restrict__ items, const int nitems, unsigned* __restrict__ ctl) {
+  __shared__ int pyc_it;
+  for (;;) {
+    if (threadIdx.x == 0) pyc_it = (int)atomicAdd(&ctl[0], 1u);
+    __syncthreads();
+    const int it = pyc_it;
+    __syncthreads();
+    if (it >= nitems) break;
+    const pyc_mitem I = items[it];
+    const pyc_mtask& T = tasks[I.task];
+    const pyc_i64 n = T.n, head = T.head, chunk = T.chunk, c = I.chunk;
+    if (head >= 0) {
+      const pyc_i64 vs = head + c * chunk;
+      const pyc_i64 ve = vs + chunk < n ? vs + chunk : n;
+      pyc_map_span<VB, U>(T.args, n, vs, ve, 0, c == 0 ? head : 0, threadIdx.x, blockDim.x);
+    } else {
+      const pyc_i64 ss = c * chunk;
+      const pyc_i64 se = ss + chunk < n ? ss + chunk : n;
+      pyc_map_span<VB, U>(T.args, n, 0, 0, ss, se, threadIdx.x, blockDim.x);
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[1], 1u) == gridDim.x - 1) {
+      ctl[0] = 0u;
+      ctl[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+)PYC";
+  MapGen g;
+  int off = (spec.params.empty() ? 4 : spec.args_bytes);
+  off = (off + 7) / 8 * 8;
+  g.task_off_n = off;
+  g.task_off_head = off + 8;
+  g.task_off_chunk = off + 16;
+  g.task_bytes = off + 24;
+  o << "static_assert(sizeof(pyc_mtask) == " << g.task_bytes << ", \"task layout\");\n";
+  for (auto& v : all_variants()) {
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_map_" << tag << "_"
+      << variant_suffix(v) << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 pyc_head) {\n"
+      << "  pyc_map_body<" << v.vec_bytes << ", " << v.unroll << ">(pyc_p, n, pyc_head);\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_mbatch_" << tag << "_"
+      << variant_suffix(v)
+      << "(const pyc_mtask* tasks, const pyc_mitem* items, const int nitems, unsigned* ctl) {\n"
+      << "  pyc_map_batched_body<" << v.vec_bytes << ", " << v.unroll
+      << ">(tasks, items, nitems, ctl);\n}\n";
+  }
+  g.source = o.str();
+  return g;
 }
 
 ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind kind,
                           const std::string& neutral, const std::string& reduce_expr,
-                          const std::string& map_expr, const std::string& preamble) {
+                          const std::string& map_expr, const std::string& preamble,
+                          const std::string& tag) {
   ReduceGen g;
   const int mins = lifted_min_bytes(spec);
   std::string acc_t, out_t;
@@ -700,12 +814,12 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
 )PYC";
   for (auto& v : all_variants()) {
     std::string sfx = variant_suffix(v);
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_reduce_" << sfx
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_reduce_" << tag << "_" << sfx
       << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
          "const pyc_i64 nchunks, pyc_acc_t* part, unsigned* ticket, pyc_out_t* out) {\n"
       << "  pyc_reduce_body<" << v.vec_bytes << ", " << v.unroll
       << ">(pyc_p, n, head, chunk, nchunks, part, ticket, out);\n}\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rbatch_" << sfx
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rbatch_" << tag << "_" << sfx
       << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
          "unsigned* tickets, unsigned* ctl) {\n"
       << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll

@@ -26,10 +26,15 @@ int lifted_min_bytes(const ArgSpec& spec);
 
 struct MapGen {
   std::string source;
+  int task_bytes = 0;  // size of one batched map task record
+  int task_off_n = 0;
+  int task_off_head = 0;
+  int task_off_chunk = 0;
 };
 
+// `tag` names the kernels (pyc_map_<tag>_v16_u4, ...) so profiles tell specs apart.
 MapGen generate_map(const ArgSpec& spec, const std::string& stmt_rewritten,
-                    const std::string& preamble);
+                    const std::string& preamble, const std::string& tag);
 
 enum class ReduceKind { Plain, Arg, Compensated };
 
@@ -48,7 +53,8 @@ struct ReduceGen {
 
 ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind kind,
                           const std::string& neutral, const std::string& reduce_expr,
-                          const std::string& map_rewritten, const std::string& preamble);
+                          const std::string& map_rewritten, const std::string& preamble,
+                          const std::string& tag);
 
 // Device-side spelling of a dtype (pyc_bf16 for BF16, ...).
 std::string device_type(pyc_dtype t);

@@ -46,11 +46,22 @@ struct HandleBase {
   TuneTable tune;
   std::string tune_key;  // digest of the source: key of the persistent tuning cache
   std::vector<std::string> param_names;  // stable storage for pyc_param_info.name
+  std::string tag;                       // kernel-name tag of this spec
+  // Kernel function name, e.g. kname("pyc_map", v) = "pyc_map_<tag>_v16_u4".
+  std::string kname(const char* kind, const Variant& v) const {
+    return std::string(kind) + "_" + tag + "_" + variant_suffix(v);
+  }
 };
+
+// Identifier-safe kernel tag: the sanitised name, or "<prefix><8 hex digits>"
+// of the spec text when no name is given.
+std::string kernel_tag(const char* name, char prefix, const std::string& spec_text);
 
 }  // namespace pyc
 
-struct pyc_map : pyc::HandleBase {};
+struct pyc_map : pyc::HandleBase {
+  pyc::MapGen gen;
+};
 
 struct pyc_reduce : pyc::HandleBase {
   pyc_reduce();

@@ -109,7 +109,8 @@ def test_scalar_layout_and_source():
         assert p["d"]["dtype"] == pyc.PYC_BF16 and p["x"]["dtype"] == pyc.PYC_I32
         src = pyc.pyc_map_source(h)
         for v in ("v16_u1", "v16_u2", "v16_u4", "v32_u1", "v32_u2", "v32_u4"):
-            assert "pyc_map_" + v in src
+            assert re.search(r"pyc_map_m[0-9a-f]{8}_" + v + r"\b", src)
+            assert re.search(r"pyc_mbatch_m[0-9a-f]{8}_" + v + r"\b", src)
         assert "ld.global.L1::no_allocate.v4.u32" in src and "ld.global.L1::no_allocate.v8.u32" in src
         assert re.search(r"pyc_r_x\s*\[\s*pyc_k\s*\]", src)
         assert re.search(r"pyc_r_z\s*\[\s*pyc_k\s*\]", src)
