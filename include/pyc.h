@@ -217,6 +217,28 @@ pyc_status pyc_reduce_batched(pyc_reduce_t h, int64_t nseg, const int64_t* seg_o
                               void* const* ptrs, const void* scalars, void* d_out,
                               pyc_stream_t stream);
 
+/* Map-reduce launch that allocates nothing.  The paper has no counterpart.
+ * For callers that cannot allocate device memory when they launch: programs
+ * that reserve all device memory at start-up and must not allocate afterwards
+ * (a fixed memory footprint), hosts whose device memory belongs to an outside
+ * memory manager, and latency-critical loops where an allocation would
+ * synchronise the device.  Arguments, kernel, chunk plan and result are those
+ * of pyc_reduce_launch; the difference is where the per-CTA partials and the
+ * finishing ticket live: in one static scratch area compiled into the library,
+ * 65,792 bytes per GPU (4096 partial slots of up to 16 bytes, then the ticket),
+ * which every GPU that loads the library holds until the process exits.  A
+ * reduction whose chunk plan needs more partial bytes than that is rejected with
+ * PYC_E_ARG (the planner caps a reduction at 4096 chunks, so none does today).
+ * The first call on a device is its set-up: it looks up the scratch address and
+ * loads the kernels there, which may allocate; make that first call before any
+ * stream capture.  Later calls allocate nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.  All calls share the one scratch area and it keeps
+ * what the last call left: each call clears the ticket itself, but calls that
+ * overlap on the GPU (e.g. on two streams with no ordering between them) race
+ * and give wrong results, so serialise them.  Errors as for pyc_reduce_launch. */
+pyc_status pyc_reduce_launch_static(pyc_reduce_t h, int64_t n, void* const* ptrs,
+                                    const void* scalars, void* d_out, pyc_stream_t stream);
+
 int pyc_reduce_num_params(pyc_reduce_t h);
 pyc_status pyc_reduce_param(pyc_reduce_t h, int idx, pyc_param_info* info);
 int pyc_reduce_scalar_bytes(pyc_reduce_t h);

@@ -2,7 +2,8 @@
 
 * ``libpyc.so``    -- the C-ABI library (C++ host code: spec parser, code
   generator, NVRTC driver + kernel cache, launches, batched reducer,
-  autotuner, server).  Device code is generated per spec and compiled by
+  autotuner; plus one nvcc-compiled sm_103a unit with the library's own
+  device objects, linked with the static CUDA runtime).  Device code is generated per spec and compiled by
   NVRTC for sm_103a at run time; :func:`check_templates` compiles the stock
   templates ahead of time so that a template error fails the build.
 * ``libpycgen.so`` -- the seeded input generator (plain C).
@@ -76,20 +77,38 @@ def _obj_path(src):
     return os.path.join(BUILD_DIR, "obj", os.path.basename(src) + ".o")
 
 
+def _cu_sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def nvcc_path():
+    p = os.path.join(cuda_home(), "bin", "nvcc")
+    return p if os.path.exists(p) else (shutil.which("nvcc") or "nvcc")
+
+
 def pyc_compile_cmds():
-    """One compile command per translation unit (run in parallel)."""
+    """One compile command per translation unit (run in parallel).  The .cpp
+    files are host code (g++); the .cu files hold device objects of the library
+    itself and are compiled by nvcc for sm_103a."""
     srcs, hdrs = _pyc_sources()
+    inc = ["-I", INCLUDE_DIR, "-I", os.path.join(cuda_home(), "include")]
     base = [os.environ.get("CXX", "g++"), "-O2", "-std=c++17", "-fPIC",
-            "-Wall", "-Wno-unused-function", "-fvisibility=hidden",
-            "-I", INCLUDE_DIR, "-I", os.path.join(cuda_home(), "include")]
-    return [(_obj_path(s), base + ["-c", s, "-o", _obj_path(s)], [s] + hdrs) for s in srcs]
+            "-Wall", "-Wno-unused-function", "-fvisibility=hidden"] + inc
+    cmds = [(_obj_path(s), base + ["-c", s, "-o", _obj_path(s)], [s] + hdrs) for s in srcs]
+    for cu in _cu_sources():
+        cmds.append((_obj_path(cu),
+                     [nvcc_path(), "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
+                      "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden"] + inc +
+                     ["-I", CSRC, "-c", cu, "-o", _obj_path(cu)], [cu] + hdrs))
+    return cmds
 
 
 def pyc_link_cmd():
     srcs, _ = _pyc_sources()
-    objs = [_obj_path(s) for s in srcs]
+    objs = [_obj_path(s) for s in srcs + _cu_sources()]
+    libdir = os.path.join(cuda_home(), "lib64")
     return [os.environ.get("CXX", "g++"), "-shared", "-o", pyc_lib_path()] + objs + \
-        ["-ldl", "-lpthread"], objs
+        ["-L", libdir, "-lcudart_static", "-ldl", "-lpthread", "-lrt"], objs
 
 
 def build_gen(force=False):

@@ -79,6 +79,12 @@ struct pyc_reduce : pyc::HandleBase {
   std::map<std::pair<CUcontext, CUstream>, Workspace> ws;
   std::mutex plan_mu;
   std::vector<std::unique_ptr<pyc::BatchPlan>> plans;  // most recent last
+  // Set-up of pyc_reduce_launch_static for the context it was last called in:
+  // kernel handles of every variant and resident CTAs per (variant, block / 32).
+  std::mutex static_mu;
+  CUcontext static_ctx = nullptr;
+  CUfunction static_fn[6] = {};
+  int static_resident[6][17] = {};
 };
 
 namespace pyc {

@@ -64,7 +64,7 @@ EXPORTED = [
     "pyc_map_scalar_bytes", "pyc_map_source", "pyc_map_autotune", "pyc_map_destroy",
     "pyc_reduce_create", "pyc_reduce_launch", "pyc_reduce_batched", "pyc_reduce_num_params",
     "pyc_reduce_param", "pyc_reduce_scalar_bytes", "pyc_reduce_out_bytes", "pyc_reduce_source",
-    "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats",
+    "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats", "pyc_reduce_launch_static",
 ]
 
 _lib = None
@@ -104,6 +104,7 @@ def load(build_if_missing=True):
         "pyc_reduce_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, vp]),
         "pyc_reduce_batched": (st, [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(vp), vp, vp,
                                     vp]),
+        "pyc_reduce_launch_static": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, vp]),
         "pyc_reduce_num_params": (i32, [vp]),
         "pyc_reduce_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
         "pyc_reduce_scalar_bytes": (i32, [vp]),
@@ -197,6 +198,12 @@ def pyc_reduce_create(out_dtype, neutral, reduce_expr, map_expr, argspec, opts=N
 def pyc_reduce_launch(h, n, ptrs, scalars, d_out, stream=None):
     _check(load().pyc_reduce_launch(h, int(n), _ptr_array(ptrs), scalars, d_out,
                                     _stream(stream)))
+
+
+def pyc_reduce_launch_static(h, n, ptrs, scalars, d_out, stream=None):
+    """pyc_reduce_launch without any device allocation (static scratch area)."""
+    _check(load().pyc_reduce_launch_static(h, int(n), _ptr_array(ptrs), scalars, d_out,
+                                           _stream(stream)))
 
 
 def pyc_reduce_batched(h, nseg, seg_offsets, ptrs, scalars, d_out, stream=None):
