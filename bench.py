@@ -282,6 +282,81 @@ def bench_batched(torch, pyc, stock, dev, reps=5):
     return res
 
 
+def bench_serving(torch, pyc, stock, dev, nreq=50000, rate=20000.0, budget=40 << 30):
+    """The request trace: Poisson arrivals (mean 20k/s), 60% map-reduce (dot) /
+    40% map (a*x+b*y), dtype uniform over {f32, bf16, i32}, sizes log-uniform in
+    [2^10, 2^26], inputs at random offsets of resident pools, 40 GB admission cap.
+    Open loop (arrivals as drawn) and closed loop (all queued at t=0), through the
+    serving loop and as one plain launch per request."""
+    from paper_1304_5553_gb300 import inputs
+    P = 1 << 26
+    x = inputs.uniform_f32(4, 0, P, -1.0, 1.0)
+    y = inputs.uniform_f32(4, 1, P, -1.0, 1.0)
+    pools = {
+        "f32": (torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)),
+        "bf16": (torch.from_numpy(x).to(torch.bfloat16).to(dev),
+                 torch.from_numpy(y).to(torch.bfloat16).to(dev)),
+        "i32": (torch.from_numpy(inputs.int_uniform_i32(4, 2, P)).to(dev),
+                torch.from_numpy(inputs.int_uniform_i32(4, 3, P)).to(dev)),
+    }
+    del x, y
+    maps = {"f32": "lin_comb_f32", "bf16": "lin_comb_bf16", "i32": "lin_comb_i32"}
+    reds = {"f32": "dot_f32", "bf16": "dot_bf16", "i32": "dot_i32_i64"}
+    scal = {k: bytes(pyc.pack_scalars(stock.create(v), [3, -2] if k == "i32" else [2.5, -0.75]))
+            for k, v in maps.items()}
+    u_kind = inputs.unit_f64(5, 0, nreq)
+    u_dt = inputs.unit_f64(5, 1, nreq)
+    sizes = inputs.loguniform_i64(5, 2, nreq, 10.0, 16.0, 1 << 10, 1 << 26)
+    u_off = inputs.unit_f64(5, 3, nreq)
+    arrival = np.cumsum(inputs.exponential_f64(5, 4, nreq, rate) * 1e9).astype(np.int64)
+    table = pyc.RequestTable(nreq)
+    dts = ["f32", "bf16", "i32"]
+    total_bytes = 0
+    for k in range(nreq):
+        dt = dts[min(2, int(u_dt[k] * 3))]
+        n = int(sizes[k])
+        off = int(u_off[k] * (P - n + 1))
+        a, b = pools[dt]
+        es = a.element_size()
+        ptrs = [a.data_ptr() + off * es, b.data_ptr() + off * es]
+        if u_kind[k] < 0.6:
+            table.set(k, pyc.PYC_REQ_REDUCE, stock.create(reds[dt]), n, ptrs)
+            total_bytes += 2 * es * n
+        else:
+            table.set(k, pyc.PYC_REQ_MAP, stock.create(maps[dt]), n, ptrs + [0], scal[dt])
+            total_bytes += 3 * es * n
+    srv = pyc.pyc_server_create(budget)
+    out = {"requests": nreq, "rate_per_s": rate, "budget_bytes": budget,
+           "algorithmic_bytes": total_bytes}
+    try:
+        # warm: every handle's batched and single kernels loaded
+        pyc.pyc_server_replay(srv, table, None, pyc.PYC_REPLAY_SERVER)
+        for label, arr in (("open_loop", arrival), ("closed_loop", None)):
+            for mode, mname in ((pyc.PYC_REPLAY_SERVER, "server"), (pyc.PYC_REPLAY_DIRECT, "direct")):
+                res = pyc.pyc_server_replay(srv, table, arr, mode)
+                ok = sum(1 for r in res if r.status == pyc.PYC_OK)
+                sub_t = np.array([r.t_submit_ns for r in res], np.int64)
+                done_t = np.array([r.t_done_ns for r in res], np.int64)
+                lat = (done_t - sub_t) / 1e3
+                span = (done_t.max() - sub_t.min()) / 1e9
+                bs = np.array([r.batch_size for r in res])
+                out["%s_%s" % (label, mname)] = {
+                    "ok": ok, "p50_us": round(float(np.percentile(lat, 50)), 1),
+                    "p99_us": round(float(np.percentile(lat, 99)), 1),
+                    "reqs_per_s": round(nreq / span, 1),
+                    "GB/s": round(total_bytes / span / 1e9, 1),
+                    "mean_batch": round(float(bs.mean()), 2)}
+        st = pyc.pyc_server_get_stats(srv)
+        out["peak_admitted_bytes"] = st["peak_admitted_bytes"]
+        c = out["closed_loop_server"]["reqs_per_s"] / out["closed_loop_direct"]["reqs_per_s"]
+        out["closed_loop_throughput_vs_direct"] = round(c, 2)
+    finally:
+        pyc.pyc_server_destroy(srv)
+    del pools
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_oracle_maps(n_sample, steps=1):
     """The oracle (single-threaded C) on the three maps over n_sample elements."""
     import oracle
@@ -364,6 +439,7 @@ def run_gpu(args):
     if rank == 0 and not args.quick:
         details["reductions"] = bench_reductions(torch, pyc, stock, dev)
         details["batched"] = bench_batched(torch, pyc, stock, dev)
+        details["serving"] = bench_serving(torch, pyc, stock, dev)
     if not args.quick:
         del d, launch
         torch.cuda.empty_cache()

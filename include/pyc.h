@@ -248,6 +248,98 @@ const char* pyc_reduce_source(pyc_reduce_t h);
 pyc_status pyc_reduce_autotune(pyc_reduce_t h, int64_t n, pyc_stream_t stream);
 void pyc_reduce_destroy(pyc_reduce_t h);
 
+/* ------------------------------------------------------------------ serving */
+
+/* A request-serving loop over map and map-reduce handles (continuous
+ * batching).  Not in the paper: it serves many independent map / map-reduce
+ * requests of different sizes that arrive over time.  A scheduler thread
+ * admits queued requests in arrival order while the logical bytes of admitted,
+ * unreleased requests (every array of the request, n elements each, plus the
+ * result) stay within mem_budget_bytes; groups admitted requests by handle into
+ * one batched launch each (chunks of long requests across CTAs, short
+ * reductions one warp each); spreads the batches over num_streams streams, at
+ * most max_inflight at a time; and retires them by completion events.  A
+ * request's result depends only on the request itself, never on the other
+ * requests of its batch.  The server owns a device arena (arena_bytes) for map
+ * outputs it allocates: a written-only array of a map request may be passed as
+ * NULL and is then allocated from the arena (returned in pyc_result.d_out) and
+ * kept until pyc_server_release. */
+typedef struct pyc_server* pyc_server_t;
+
+#define PYC_REQ_MAP 0
+#define PYC_REQ_REDUCE 1
+
+typedef struct {
+  int64_t mem_budget_bytes; /* admission cap in bytes (> 0) */
+  int64_t arena_bytes;      /* device arena for server-allocated outputs; 0 = min(budget, 8 GiB) */
+  int num_streams;          /* 0 = 4 (at most 64) */
+  int max_batch;            /* requests per batched launch; 0 = 256 (at most 4096) */
+  int max_inflight;         /* launched, unfinished batches; 0 = 8 (at most 256) */
+  int max_queue;            /* waiting requests before submit answers PYC_E_BUSY; 0 = 2^20 */
+} pyc_server_cfg;
+
+typedef struct {
+  int kind;             /* PYC_REQ_MAP or PYC_REQ_REDUCE */
+  int pad;
+  void* handle;         /* pyc_map_t or pyc_reduce_t; must outlive the request */
+  int64_t n;            /* elements, 0 <= n <= 2^34 */
+  void* const* ptrs;    /* device arrays in declaration order (copied at submit) */
+  const void* scalars;  /* packed scalars as for the launch calls (copied at submit) */
+  int64_t deadline_us;  /* > 0: fail with PYC_E_TIMEOUT if not admitted within this time */
+} pyc_request;
+
+typedef struct {
+  int status;           /* PYC_OK, or why the request failed */
+  int batch_size;       /* requests in the launch that ran it */
+  void* d_out;          /* map: first server-allocated output (NULL if none) */
+  unsigned char value[16];  /* map-reduce: the result, pyc_reduce_out_bytes bytes */
+  int64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns; /* steady clock; done = completion seen */
+} pyc_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, batches;
+  int64_t admitted_bytes;      /* current logical bytes of admitted, unreleased requests */
+  int64_t peak_admitted_bytes; /* never above mem_budget_bytes */
+  int64_t queued;              /* waiting for admission */
+  int64_t arena_in_use;        /* bytes of server-allocated outputs */
+} pyc_server_stats;
+
+/* Create a server on the current context (allocates its streams, arena and
+ * per-batch slots: 16 MiB device + 16 MiB pinned host each).  Errors:
+ * PYC_E_ARG, PYC_E_CUDA, PYC_E_NOMEM. */
+pyc_status pyc_server_create(const pyc_server_cfg* cfg, pyc_server_t* out);
+
+/* Queue a request; *id identifies it until pyc_server_release.  Errors:
+ * PYC_E_ARG (bad request), PYC_E_NOMEM (larger than the whole budget),
+ * PYC_E_BUSY (queue full or shutting down). */
+pyc_status pyc_server_submit(pyc_server_t s, const pyc_request* req, uint64_t* id);
+
+/* Wait up to timeout_us (0 = do not wait) for request id to finish.  PYC_OK
+ * fills *res (res->status says whether the request succeeded); PYC_E_TIMEOUT
+ * if it is still running; PYC_E_NOTFOUND for an unknown id. */
+pyc_status pyc_server_poll(pyc_server_t s, uint64_t id, pyc_result* res, int64_t timeout_us);
+
+/* Forget a finished request: frees its server-allocated outputs and returns its
+ * bytes to the budget.  PYC_E_BUSY if it has not finished. */
+pyc_status pyc_server_release(pyc_server_t s, uint64_t id);
+
+pyc_status pyc_server_get_stats(pyc_server_t s, pyc_server_stats* st);
+
+/* Fail queued requests, wait for launched batches, free everything. */
+void pyc_server_destroy(pyc_server_t s);
+
+/* Trace replay for load measurement.  Submits reqs[k] at t0 + arrival_ns[k]
+ * (an open loop; all at t0 when arrival_ns is NULL), collects and releases every
+ * request as it finishes and stores its pyc_result in results[k], with
+ * t_submit_ns set to the request's arrival time.  mode PYC_REPLAY_SERVER goes
+ * through the serving loop; PYC_REPLAY_DIRECT is the per-request baseline: each
+ * request launched alone as it arrives with pyc_map_launch / pyc_reduce_launch
+ * kernels on one stream.  Returns when every request has finished. */
+#define PYC_REPLAY_SERVER 0
+#define PYC_REPLAY_DIRECT 1
+pyc_status pyc_server_replay(pyc_server_t s, int64_t nreq, const pyc_request* reqs,
+                             const int64_t* arrival_ns, int mode, pyc_result* results);
+
 /* ------------------------------------------------------------------ cache */
 
 /* Kernel cache statistics since process start: compiled = NVRTC compilations,

@@ -1,16 +1,11 @@
 // Segmented (batched) map-reduce: many independent reductions in one
 // persistent launch over a work list, replayed as a CUDA graph.
 //
-// Plan (built once per segment table, pointers, scalars, output and stream):
-//  * every segment becomes a task record (its own offset pointers, length,
-//    alignment head, chunk length, output slot);
-//  * segments of at most kSmall elements are reduced by one warp each; they are
-//    packed into "bundles" of blockDim/32 tasks, one CTA item per bundle;
-//  * longer segments are cut into chunks of kChunk elements (a multiple of the
-//    tile); one CTA item per chunk, longest segments first; the last chunk of a
-//    segment to finish (per-segment ticket) combines its partials in order;
-//  * CTAs pull items from an atomic counter, which the last CTA to leave
-//    resets, so replays need no memset.
+// Plan (built once per segment table, pointers, scalars and output): every
+// segment becomes a task over its own offset pointers, and the work list is
+// written by write_reduce_work (short segments one warp each, long ones in
+// chunks with a per-segment ticket).  CTAs pull items from an atomic counter,
+// which the last CTA to leave resets, so replays need no memset.
 // The launch is captured once into a graph on a private stream and replayed on
 // the caller's stream; while the caller's stream is itself being captured the
 // kernel is launched directly so it becomes part of the caller's graph.
@@ -24,8 +19,6 @@
 namespace pyc {
 
 namespace {
-constexpr int64_t kSmall = 2048;           // segments up to this length: one warp each
-constexpr int64_t kChunkElems = 1 << 16;   // chunk length of long segments (rounded to tiles)
 constexpr size_t kMaxPlans = 8;
 }  // namespace
 
@@ -73,10 +66,6 @@ CUstream capture_stream() {
   return s;
 }
 
-struct Item {
-  int32_t task, chunk, count, pad;
-};
-
 std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t* off,
                                       void* const* ptrs, const void* scalars, void* d_out,
                                       const LaunchCfg& cfg) {
@@ -85,71 +74,24 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
   auto plan = std::make_unique<BatchPlan>();
   plan->cfg = cfg;
   plan->ctx = ensure_context();
-  const int E = cfg.v.vec_bytes / h->min_bytes;
-  const int64_t tile = (int64_t)cfg.block * E * cfg.v.unroll;
-  const int64_t chunk = std::max<int64_t>(tile, (kChunkElems + tile - 1) / tile * tile);
-  const int wpb = cfg.block / 32;
-
-  // task order: small segments first (consecutive, for bundles), then long ones
-  std::vector<int64_t> small, large;
-  for (int64_t s = 0; s < nseg; ++s) (off[s + 1] - off[s] <= kSmall ? small : large).push_back(s);
-  std::stable_sort(large.begin(), large.end(), [&](int64_t a, int64_t b) {
-    return off[a + 1] - off[a] > off[b + 1] - off[b];
-  });
-  std::vector<int64_t> order(small);
-  order.insert(order.end(), large.begin(), large.end());
-
-  std::vector<unsigned char> tasks((size_t)nseg * g.task_bytes, 0);
-  std::vector<Item> items;
-  std::vector<void*> tptrs(spec.num_ptrs ? spec.num_ptrs : 1);
-  int64_t slots = 0;
-  for (int64_t t = 0; t < nseg; ++t) {
-    const int64_t s = order[t];
-    const int64_t len = off[s + 1] - off[s];
+  // every segment becomes a task over its own offset pointers
+  const size_t np = spec.num_ptrs ? spec.num_ptrs : 1;
+  std::vector<void*> tptrs((size_t)nseg * np, nullptr);
+  std::vector<ReduceTaskIn> in((size_t)nseg);
+  for (int64_t s = 0; s < nseg; ++s) {
+    void** tp = &tptrs[(size_t)s * np];
     for (auto& p : spec.params)
       if (p.is_ptr)
-        tptrs[p.ptr_slot] = static_cast<char*>(ptrs[p.ptr_slot]) + off[s] * type_info(p.dtype).bytes;
-    std::vector<unsigned char> args = pack_args(spec, tptrs.data(), scalars);
-    int64_t head = vector_head(spec, tptrs.data(), cfg.v.vec_bytes, h->min_bytes, len);
-    unsigned char* rec = &tasks[(size_t)t * g.task_bytes];
-    std::memcpy(rec, args.data(), args.size());
-    int64_t tchunk, nch;
-    if (len <= kSmall) {
-      tchunk = std::max<int64_t>(len, 1);
-      nch = 0;
-    } else {
-      int64_t body = head >= 0 ? len - head : len;
-      tchunk = chunk;
-      nch = (body + chunk - 1) / chunk;
-    }
-    int32_t nchunks = (int32_t)nch, slot0 = 0;
-    if (nch > 1) {
-      slot0 = (int32_t)slots;
-      slots += nch;
-    }
-    void* out = static_cast<char*>(d_out) + s * g.out_bytes;
-    std::memcpy(rec + g.task_off_n, &len, 8);
-    std::memcpy(rec + g.task_off_head, &head, 8);
-    std::memcpy(rec + g.task_off_chunk, &tchunk, 8);
-    std::memcpy(rec + g.task_off_out, &out, 8);
-    std::memcpy(rec + g.task_off_nchunks, &nchunks, 4);
-    std::memcpy(rec + g.task_off_slot0, &slot0, 4);
+        tp[p.ptr_slot] = static_cast<char*>(ptrs[p.ptr_slot]) + off[s] * type_info(p.dtype).bytes;
+    in[s] = {tp, scalars, off[s + 1] - off[s], static_cast<char*>(d_out) + s * g.out_bytes};
   }
-  if (slots > (int64_t)INT32_MAX) fail(PYC_E_ARG, "too many chunks in one batch");
-  // CTA items: long segments first, chunk-major
-  for (int64_t t = (int64_t)small.size(); t < nseg; ++t) {
-    int32_t nchunks;
-    std::memcpy(&nchunks, &tasks[(size_t)t * g.task_bytes + g.task_off_nchunks], 4);
-    for (int32_t c = 0; c < nchunks; ++c) items.push_back({(int32_t)t, c, 1, 0});
-  }
-  for (int64_t t = 0; t < (int64_t)small.size(); t += wpb) {
-    int32_t cnt = (int32_t)std::min<int64_t>(wpb, (int64_t)small.size() - t);
-    items.push_back({(int32_t)t, -1, cnt, 0});
-  }
+  std::vector<unsigned char> tasks;
+  std::vector<ReduceItem> items;
+  int64_t slots = write_reduce_work(h, cfg, in, tasks, items);
   plan->nitems = (int)items.size();
 
   auto up = [](size_t v) { return (v + 255) / 256 * 256; };
-  size_t b_tasks = up(tasks.size()), b_items = up(items.size() * sizeof(Item));
+  size_t b_tasks = up(tasks.size()), b_items = up(items.size() * sizeof(ReduceItem));
   size_t b_tickets = up((size_t)nseg * 4), b_ctl = 256;
   size_t b_part = up((size_t)std::max<int64_t>(slots, 1) * g.acc_bytes);
   const Driver& d = drv();
@@ -160,7 +102,8 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
   plan->ctl = plan->tickets + b_tickets;
   plan->part = plan->ctl + b_ctl;
   if (!tasks.empty()) PYC_CU(d.cuMemcpyHtoD(plan->tasks, tasks.data(), tasks.size()));
-  if (!items.empty()) PYC_CU(d.cuMemcpyHtoD(plan->items, items.data(), items.size() * sizeof(Item)));
+  if (!items.empty())
+    PYC_CU(d.cuMemcpyHtoD(plan->items, items.data(), items.size() * sizeof(ReduceItem)));
   PYC_CU(d.cuMemsetD8(plan->tickets, 0, b_tickets + b_ctl));
 
   plan->f = h->mod->function(h->kname("pyc_rbatch", cfg.v));
@@ -197,7 +140,7 @@ void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const
   if (off[0] < 0) fail(PYC_E_ARG, "seg_offsets[0] must be >= 0");
   for (int64_t s = 0; s < nseg; ++s)
     if (off[s + 1] < off[s]) fail(PYC_E_ARG, "seg_offsets must be non-decreasing");
-  LaunchCfg cfg = choose_cfg(*h, kSmall, true);
+  LaunchCfg cfg = choose_cfg(*h, kSmallTask, true);
   if (!h->opts.items_per_thread) cfg.v.unroll = 1;
   if (!h->opts.block) cfg.block = 256;
 

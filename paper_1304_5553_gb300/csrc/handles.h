@@ -129,6 +129,38 @@ void tune_cache_load(HandleBase& h, bool reduce);
 void tune_cache_store(const HandleBase& h, bool reduce, int bucket, const LaunchCfg& c,
                       double us);
 
+// Work lists of batched launches (worklist.cpp), shared by the segmented
+// reducer and the server.  Each task is one independent map / reduction over
+// its own (already offset) arrays.
+constexpr int64_t kSmallTask = 2048;       // reductions up to this length: one warp each
+constexpr int64_t kChunkElems = 1 << 16;   // chunk length of long tasks (rounded to tiles)
+
+struct ReduceTaskIn {
+  void* const* ptrs;
+  const void* scalars;
+  int64_t n;
+  void* out;
+};
+struct ReduceItem {
+  int32_t task, chunk, count, pad;  // chunk < 0: warp bundle of `count` short tasks
+};
+// Writes task records (short tasks first, then long ones, longest first) and
+// work items; returns the number of partial slots the list needs.
+int64_t write_reduce_work(const pyc_reduce* h, const LaunchCfg& cfg,
+                          const std::vector<ReduceTaskIn>& in, std::vector<unsigned char>& tasks,
+                          std::vector<ReduceItem>& items);
+
+struct MapTaskIn {
+  void* const* ptrs;
+  const void* scalars;
+  int64_t n;
+};
+struct MapItem {
+  int32_t task, chunk;
+};
+void write_map_work(const pyc_map* h, const LaunchCfg& cfg, const std::vector<MapTaskIn>& in,
+                    std::vector<unsigned char>& tasks, std::vector<MapItem>& items);
+
 // Batched reducer (batched.cpp).
 void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* offsets, void* const* ptrs,
                     const void* scalars, void* d_out, CUstream stream);

@@ -57,6 +57,35 @@ class pyc_argf32(ctypes.Structure):
     _fields_ = [("v", ctypes.c_float), ("pad", ctypes.c_int32), ("i", ctypes.c_int64)]
 
 
+PYC_REQ_MAP, PYC_REQ_REDUCE = 0, 1
+PYC_REPLAY_SERVER, PYC_REPLAY_DIRECT = 0, 1
+
+
+class pyc_server_cfg(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
+                ("num_streams", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("max_inflight", ctypes.c_int), ("max_queue", ctypes.c_int)]
+
+
+class pyc_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("pad", ctypes.c_int), ("handle", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("ptrs", ctypes.POINTER(ctypes.c_void_p)),
+                ("scalars", ctypes.c_void_p), ("deadline_us", ctypes.c_int64)]
+
+
+class pyc_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_int), ("d_out", ctypes.c_void_p),
+                ("value", ctypes.c_ubyte * 16), ("t_submit_ns", ctypes.c_int64),
+                ("t_admit_ns", ctypes.c_int64), ("t_launch_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class pyc_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "batches",
+                                              "admitted_bytes", "peak_admitted_bytes", "queued",
+                                              "arena_in_use")]
+
+
 # every symbol include/pyc.h declares (checked by the tests)
 EXPORTED = [
     "pyc_last_error", "pyc_version",
@@ -65,6 +94,8 @@ EXPORTED = [
     "pyc_reduce_create", "pyc_reduce_launch", "pyc_reduce_batched", "pyc_reduce_num_params",
     "pyc_reduce_param", "pyc_reduce_scalar_bytes", "pyc_reduce_out_bytes", "pyc_reduce_source",
     "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats", "pyc_reduce_launch_static",
+    "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
+    "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay",
 ]
 
 _lib = None
@@ -113,6 +144,14 @@ def load(build_if_missing=True):
         "pyc_reduce_autotune": (st, [vp, i64, vp]),
         "pyc_reduce_destroy": (None, [vp]),
         "pyc_cache_stats": (None, [ctypes.POINTER(i64)] * 3),
+        "pyc_server_create": (st, [ctypes.POINTER(pyc_server_cfg), ctypes.POINTER(vp)]),
+        "pyc_server_submit": (st, [vp, ctypes.POINTER(pyc_request), ctypes.POINTER(ctypes.c_uint64)]),
+        "pyc_server_poll": (st, [vp, ctypes.c_uint64, ctypes.POINTER(pyc_result), i64]),
+        "pyc_server_release": (st, [vp, ctypes.c_uint64]),
+        "pyc_server_get_stats": (st, [vp, ctypes.POINTER(pyc_server_stats)]),
+        "pyc_server_destroy": (None, [vp]),
+        "pyc_server_replay": (st, [vp, i64, ctypes.POINTER(pyc_request), ctypes.POINTER(i64),
+                                   ctypes.c_int, ctypes.POINTER(pyc_result)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +311,99 @@ def pack_scalars(h, values, reduce=False):
             struct.pack_into(fmt, buf, p["scalar_offset"],
                              float(v) if fmt in "fde" else int(v))
     return buf
+
+
+# ------------------------------------------------------------------ serving
+
+def pyc_server_create(mem_budget_bytes, arena_bytes=0, num_streams=0, max_batch=0,
+                      max_inflight=0, max_queue=0):
+    cfg = pyc_server_cfg(int(mem_budget_bytes), int(arena_bytes), num_streams, max_batch,
+                         max_inflight, max_queue)
+    h = ctypes.c_void_p()
+    _check(load().pyc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def make_request(kind, handle, n, ptrs, scalars=None, deadline_us=0):
+    """A pyc_request plus the buffers it points to (keep the tuple alive)."""
+    arr = _ptr_array(ptrs)
+    req = pyc_request(kind, 0, handle.value if isinstance(handle, ctypes.c_void_p) else handle,
+                      int(n), ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)),
+                      ctypes.cast(scalars, ctypes.c_void_p) if scalars is not None else None,
+                      int(deadline_us))
+    return req, arr, scalars
+
+
+def pyc_server_submit(s, req):
+    rid = ctypes.c_uint64()
+    r = req[0] if isinstance(req, tuple) else req
+    _check(load().pyc_server_submit(s, ctypes.byref(r), ctypes.byref(rid)))
+    return rid.value
+
+
+def pyc_server_poll(s, rid, timeout_us=0):
+    """pyc_result, or None while the request is still running."""
+    res = pyc_result()
+    st = load().pyc_server_poll(s, rid, ctypes.byref(res), int(timeout_us))
+    if st == PYC_E_TIMEOUT:
+        return None
+    _check(st)
+    return res
+
+
+def pyc_server_release(s, rid):
+    _check(load().pyc_server_release(s, rid))
+
+
+def pyc_server_get_stats(s):
+    st = pyc_server_stats()
+    _check(load().pyc_server_get_stats(s, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in pyc_server_stats._fields_}
+
+
+def pyc_server_destroy(s):
+    load().pyc_server_destroy(s)
+
+
+class RequestTable:
+    """A contiguous array of pyc_request (for pyc_server_replay) with every
+    request's pointer list and scalars in two shared buffers."""
+
+    def __init__(self, nreq, max_ptrs=4, scalar_bytes=16):
+        self.n = nreq
+        self.reqs = (pyc_request * nreq)()
+        self.ptrs = (ctypes.c_void_p * (nreq * max_ptrs))()
+        self.scal = ctypes.create_string_buffer(nreq * scalar_bytes)
+        self.max_ptrs, self.sb = max_ptrs, scalar_bytes
+
+    def set(self, k, kind, handle, n, ptrs, scalar_bytes=b""):
+        base = k * self.max_ptrs
+        for j, p in enumerate(ptrs):
+            self.ptrs[base + j] = int(p) if p else None
+        r = self.reqs[k]
+        r.kind, r.handle, r.n, r.deadline_us = kind, handle.value, int(n), 0
+        r.ptrs = ctypes.cast(ctypes.byref(self.ptrs, base * ctypes.sizeof(ctypes.c_void_p)),
+                             ctypes.POINTER(ctypes.c_void_p))
+        if scalar_bytes:
+            off = k * self.sb
+            ctypes.memmove(ctypes.addressof(self.scal) + off, scalar_bytes, len(scalar_bytes))
+            r.scalars = ctypes.addressof(self.scal) + off
+        else:
+            r.scalars = None
+
+
+def pyc_server_replay(s, table, arrival_ns=None, mode=PYC_REPLAY_SERVER):
+    """Replay a RequestTable; returns the pyc_result array."""
+    import numpy as np
+    res = (pyc_result * table.n)()
+    arr = None
+    if arrival_ns is not None:
+        arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        assert arr.size == table.n
+    _check(load().pyc_server_replay(
+        s, table.n, table.reqs, None if arr is None else arr.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int64)), mode, res))
+    return res
 
 
 # ------------------------------------------------------------------ paper-style front ends

@@ -26,6 +26,7 @@ MAPS = {
                       "z[i] = x[i]*exp(-y[i]*y[i]) + sin(u[i])*w[i]"),
     "scale2_f32": ("float *a", "a[i] *= 2"),
     "add_f32": ("float *tgt, float *op1, float *op2", "tgt[i] = op1[i] + op2[i]"),
+    "copy_f32": ("float *src, float *dst", "dst[i] = src[i]"),
 }
 
 # name: (result dtype, neutral, reduce expression, map expression, argspec, options)

@@ -204,3 +204,17 @@ def test_front_end_params():
     buf = pyc.pack_scalars(k._h, [5, 6])  # Listing 3a passes ints for float params
     import struct
     assert struct.unpack_from("ff", buf, 0) == (5.0, 6.0)
+
+
+@pytest.mark.skipif(_has_gpu(), reason="checks the no-driver error path")
+def test_server_without_driver_is_an_error():
+    with pytest.raises(pyc.PycError) as e:
+        pyc.pyc_server_create(1 << 20)
+    assert e.value.status == pyc.PYC_E_CUDA
+
+
+def test_server_config_validation():
+    for bad in (dict(mem_budget_bytes=0), dict(mem_budget_bytes=1 << 20, num_streams=100)):
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_server_create(**bad)
+        assert e.value.status == pyc.PYC_E_ARG

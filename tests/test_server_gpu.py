@@ -1,0 +1,222 @@
+"""Serving loop on the GPU: continuous batching of map and map-reduce requests
+through the C ABI.  Each result is the same alone and in a mix (bit for bit),
+agrees with the oracle, admission never exceeds the memory budget, and
+deadlines, queue limits and the per-request baseline behave as declared."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from bounds import lin_comb_f32_bound, plain_sum_bound
+from paper_1304_5553_gb300 import inputs, pyc, stock
+
+pytestmark = pytest.mark.gpu
+A, B = 2.5, -0.75
+POOL = 1 << 22
+
+
+@pytest.fixture(scope="module")
+def pools():
+    x = inputs.uniform_f32(31, 0, POOL, -1.0, 1.0)
+    y = inputs.uniform_f32(31, 1, POOL, -1.0, 1.0)
+    xi = inputs.int_uniform_i32(31, 2, POOL)
+    yi = inputs.int_uniform_i32(31, 3, POOL)
+    dev = {"x": torch.from_numpy(x).cuda(), "y": torch.from_numpy(y).cuda(),
+           "xi": torch.from_numpy(xi).cuda(), "yi": torch.from_numpy(yi).cuda()}
+    return {"x": x, "y": y, "xi": xi, "yi": yi}, dev
+
+
+def _req(kind, name, n, off, dev, scal=None):
+    h = stock.create(name)
+    if name.endswith("i32") or name == "dot_i32_i64":
+        a, b = dev["xi"], dev["yi"]
+    else:
+        a, b = dev["x"], dev["y"]
+    es = a.element_size()
+    ptrs = [a.data_ptr() + off * es, b.data_ptr() + off * es]
+    if kind == pyc.PYC_REQ_MAP:
+        ptrs.append(0)  # output allocated by the server
+        scal = pyc.pack_scalars(h, [3, -2] if name.endswith("i32") else [A, B])
+    return pyc.make_request(kind, h, n, ptrs, scal)
+
+
+def _run_one(srv, req):
+    rid = pyc.pyc_server_submit(srv, req)
+    res = pyc.pyc_server_poll(srv, rid, 10_000_000)
+    assert res is not None and res.status == pyc.PYC_OK
+    return rid, res
+
+
+def _map_out(res, n):
+    """Copy a server-owned binary32 map output into a tensor (a copy map)."""
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    pyc.pyc_map_launch(stock.create("copy_f32"), n, [res.d_out, out.data_ptr()], None,
+                       torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out
+
+
+def test_alone_and_in_the_mix_are_identical(pools):
+    host, dev = pools
+    srv = pyc.pyc_server_create(1 << 30, arena_bytes=1 << 28, num_streams=3, max_batch=64,
+                                max_inflight=6)
+    try:
+        probes = [(pyc.PYC_REQ_REDUCE, "dot_f32", 300001, 5),
+                  (pyc.PYC_REQ_REDUCE, "dot_f32", 777, 3),
+                  (pyc.PYC_REQ_REDUCE, "dot_i32_i64", 100003, 11),
+                  (pyc.PYC_REQ_MAP, "lin_comb_f32", 50001, 7)]
+        alone = []
+        for p in probes:
+            req = _req(*p, dev)
+            rid, res = _run_one(srv, req)
+            val = bytes(res.value)
+            out = _map_out(res, p[2]).cpu().numpy().copy() if p[0] == pyc.PYC_REQ_MAP else None
+            pyc.pyc_server_release(srv, rid)
+            alone.append((val, out))
+        # the same probes inside a stream of other requests of all kinds and sizes
+        rng = np.random.default_rng(5)
+        ids, keep = [], []
+        for k in range(300):
+            if k % 50 == 25:
+                req = _req(*probes[(k // 50) % len(probes)], dev)
+                probe = (k // 50) % len(probes)
+            else:
+                kind = pyc.PYC_REQ_REDUCE if rng.random() < 0.6 else pyc.PYC_REQ_MAP
+                name = rng.choice(["dot_f32", "dot_i32_i64"]) if kind else rng.choice(
+                    ["lin_comb_f32", "lin_comb_i32"])
+                n = int(2 ** rng.uniform(0, 20))
+                req = _req(kind, str(name), n, int(rng.integers(0, POOL - n)), dev)
+                probe = -1
+            keep.append(req)
+            ids.append((pyc.pyc_server_submit(srv, req), probe))
+        batched_probe = 0
+        for rid, probe in ids:
+            res = pyc.pyc_server_poll(srv, rid, 20_000_000)
+            assert res is not None and res.status == pyc.PYC_OK
+            if probe >= 0:
+                val, out = alone[probe]
+                assert bytes(res.value) == val
+                if out is not None:
+                    assert np.array_equal(_map_out(res, probes[probe][2]).cpu().numpy(), out)
+                batched_probe = max(batched_probe, res.batch_size)
+            pyc.pyc_server_release(srv, rid)
+        assert batched_probe > 1  # the probes really ran inside batches
+        st = pyc.pyc_server_get_stats(srv)
+        assert st["completed"] == 304 and st["failed"] == 0 and st["admitted_bytes"] == 0
+        assert st["arena_in_use"] == 0
+        # results against the oracle
+        v = np.frombuffer(alone[0][0][:4], np.float32)[0]
+        ref, ab = oracle.dot_f32(host["x"][5:300006], host["y"][5:300006])
+        assert abs(v - ref) <= plain_sum_bound(ab)
+        vi = np.frombuffer(alone[2][0][:8], np.int64)[0]
+        assert vi == oracle.dot_i32_i64(host["xi"][11:100014], host["yi"][11:100014])
+        z = alone[3][1]
+        want = oracle.map_lin_comb_f32ops(A, host["x"][7:50008], B, host["y"][7:50008])
+        assert np.array_equal(z, want)
+    finally:
+        pyc.pyc_server_destroy(srv)
+
+
+def test_admission_respects_budget(pools):
+    _, dev = pools
+    budget = 24 << 20
+    srv = pyc.pyc_server_create(budget, arena_bytes=16 << 20, num_streams=2, max_batch=16,
+                                max_inflight=4)
+    try:
+        reqs, ids = [], []
+        for k in range(200):
+            n = 50000 + 997 * k
+            r = _req(pyc.PYC_REQ_REDUCE, "dot_f32", n, k, dev)
+            reqs.append(r)
+            ids.append(pyc.pyc_server_submit(srv, r))
+        for rid in ids:
+            res = pyc.pyc_server_poll(srv, rid, 20_000_000)
+            assert res is not None and res.status == pyc.PYC_OK
+            pyc.pyc_server_release(srv, rid)
+        st = pyc.pyc_server_get_stats(srv)
+        assert 0 < st["peak_admitted_bytes"] <= budget
+        with pytest.raises(pyc.PycError) as e:  # larger than the whole budget
+            pyc.pyc_server_submit(srv, _req(pyc.PYC_REQ_REDUCE, "dot_f32", 4 << 20, 0, dev))
+        assert e.value.status == pyc.PYC_E_NOMEM
+    finally:
+        pyc.pyc_server_destroy(srv)
+
+
+def test_deadline_queue_limit_and_errors(pools):
+    _, dev = pools
+    n = 1 << 20
+    per = n * 8 + 4  # two binary32 arrays + the result
+    srv = pyc.pyc_server_create(per, num_streams=1, max_batch=4, max_inflight=2, max_queue=3)
+    try:
+        held = _req(pyc.PYC_REQ_REDUCE, "dot_f32", n, 0, dev)
+        rid, _ = _run_one(srv, held)  # finished but not released: the budget is full
+        late = _req(pyc.PYC_REQ_REDUCE, "dot_f32", n, 1, dev)
+        late[0].deadline_us = 2000
+        lid = pyc.pyc_server_submit(srv, late)
+        res = pyc.pyc_server_poll(srv, lid, 5_000_000)
+        assert res is not None and res.status == pyc.PYC_E_TIMEOUT
+        pyc.pyc_server_release(srv, lid)
+        waiting = [_req(pyc.PYC_REQ_REDUCE, "dot_f32", n, 2 + k, dev) for k in range(4)]
+        wids = [pyc.pyc_server_submit(srv, w) for w in waiting[:3]]
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_server_submit(srv, waiting[3])
+        assert e.value.status == pyc.PYC_E_BUSY  # queue full
+        assert pyc.pyc_server_poll(srv, wids[0], 0) is None  # still waiting: budget held
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_server_release(srv, wids[0])
+        assert e.value.status == pyc.PYC_E_BUSY
+        pyc.pyc_server_release(srv, rid)  # frees the budget; the queue drains
+        for w in wids:
+            res = pyc.pyc_server_poll(srv, w, 10_000_000)
+            assert res is not None and res.status == pyc.PYC_OK
+            pyc.pyc_server_release(srv, w)
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_server_poll(srv, 123456789, 0)
+        assert e.value.status == pyc.PYC_E_NOTFOUND
+    finally:
+        pyc.pyc_server_destroy(srv)
+
+
+def test_replay_server_and_direct_agree(pools):
+    host, dev = pools
+    nreq = 3000
+    rng = np.random.default_rng(8)
+    srv = pyc.pyc_server_create(1 << 30, arena_bytes=1 << 28)
+    try:
+        table = pyc.RequestTable(nreq)
+        plan = []
+        for k in range(nreq):
+            kind = pyc.PYC_REQ_REDUCE if rng.random() < 0.6 else pyc.PYC_REQ_MAP
+            ints = rng.random() < 0.5
+            name = ("dot_i32_i64" if ints else "dot_f32") if kind else (
+                "lin_comb_i32" if ints else "lin_comb_f32")
+            n = int(2 ** rng.uniform(4, 19))
+            off = int(rng.integers(0, POOL - n))
+            req, arr, sc = _req(kind, name, n, off, dev)
+            ptrs = [arr[j] for j in range(len(arr))]
+            table.set(k, kind, stock.create(name), n, ptrs, bytes(sc) if sc is not None else b"")
+            plan.append((kind, name, n, off))
+        gaps = rng.exponential(1e9 / 200000.0, nreq).astype(np.int64)
+        arrival = np.cumsum(gaps)
+        rs = pyc.pyc_server_replay(srv, table, arrival, pyc.PYC_REPLAY_SERVER)
+        rd = pyc.pyc_server_replay(srv, table, None, pyc.PYC_REPLAY_DIRECT)
+        assert all(r.status == pyc.PYC_OK for r in rs) and all(r.status == pyc.PYC_OK for r in rd)
+        assert max(r.batch_size for r in rs) > 1 and max(r.batch_size for r in rd) == 1
+        for k, (kind, name, n, off) in enumerate(plan):
+            if kind != pyc.PYC_REQ_REDUCE:
+                continue
+            if name == "dot_i32_i64":
+                want = oracle.dot_i32_i64(host["xi"][off:off + n], host["yi"][off:off + n])
+                assert np.frombuffer(bytes(rs[k].value)[:8], np.int64)[0] == want
+                assert np.frombuffer(bytes(rd[k].value)[:8], np.int64)[0] == want
+            elif k % 7 == 0:
+                ref, ab = oracle.dot_f32(host["x"][off:off + n], host["y"][off:off + n])
+                for r in (rs[k], rd[k]):
+                    assert abs(np.frombuffer(bytes(r.value)[:4], np.float32)[0] - ref) <= \
+                        plain_sum_bound(ab)
+        lat = np.array([r.t_done_ns - r.t_submit_ns for r in rs]) / 1e3
+        print("replay 3000 req at 200k/s: p50 %.1f us p99 %.1f us" % tuple(np.percentile(lat, [50, 99])))
+        st = pyc.pyc_server_get_stats(srv)
+        assert st["admitted_bytes"] == 0 and st["arena_in_use"] == 0
+    finally:
+        pyc.pyc_server_destroy(srv)
