@@ -168,37 +168,33 @@ def time_steps(torch, launchers, names, steps, warmup, barrier):
 
 
 def bench_e2e(torch, pyc, stock, host, dev, steps=3, warmup=1):
-    """Same step through the C ABI with HOST buffers: pinned inputs copied in, the
-    three maps, outputs copied back, all inside the timed region."""
+    """Same step through the C ABI with HOST buffers: pyc_map_launch_host on
+    page-locked host arrays; it copies the inputs in and the output back (chunked,
+    overlapped on three streams) inside the timed region, and returns when the
+    output is in host memory."""
     pinned = {k: [torch.from_numpy(a).to(torch.bfloat16 if k.endswith("bf16") else torch.float32)
                   .pin_memory() for a in arrs] for k, arrs in host.items()}
     outs_h = {k: torch.empty(N_MAP, dtype=pinned[k][0].dtype).pin_memory() for k in pinned}
-    dbufs = {k: [torch.empty(N_MAP, dtype=p[0].dtype, device=dev) for _ in range(len(p) + 1)]
-             for k, p in pinned.items()}
-    stream = torch.cuda.current_stream()
-    launch = map_launchers(torch, pyc, stock, dbufs, stream.cuda_stream)
+    handles = {k: stock.create(k) for k in pinned}
+    scal = {k: pyc.pack_scalars(handles[k], [A, B]) if k.startswith("lin_comb") else None
+            for k in pinned}
+    ptrs = {k: [t.data_ptr() for t in pinned[k]] + [outs_h[k].data_ptr()] for k in pinned}
     h2d = sum(t.numel() * t.element_size() for p in pinned.values() for t in p)
     d2h = sum(t.numel() * t.element_size() for t in outs_h.values())
 
     def step():
         for k in pinned:
-            for src, dst in zip(pinned[k], dbufs[k]):
-                dst.copy_(src, non_blocking=True)
-            launch[k]()
-            outs_h[k].copy_(dbufs[k][-1], non_blocking=True)
+            pyc.pyc_map_launch_host(handles[k], N_MAP, ptrs[k], scal[k])
 
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
+    t0 = time.perf_counter()
     for _ in range(steps):
         step()
-    b.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / steps
+    ms = (time.perf_counter() - t0) * 1e3 / steps
     alg = sum(MAP_BYTES[k] for k in pinned) * N_MAP
-    del dbufs, pinned, outs_h
+    del pinned, outs_h
     return {"value": round(alg / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
             "steps": steps}
@@ -218,20 +214,24 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
              ("max_f32", ln, 4), ("argmin_f32", xa, 4)]
     for name, arr, bpe in cases:
         h = stock.create(name)
+        pyc.pyc_reduce_autotune(h, n, s)
         f = (lambda h=h, arr=arr: pyc.pyc_reduce_launch(h, n, [arr.data_ptr()], None,
                                                          out.data_ptr(), s))
         ms = _time_fn(torch, f, reps)
-        res[name] = {"n": n, "us": round(ms * 1e3, 2), "GB/s": round(bpe * n / (ms * 1e-3) / 1e9, 1)}
+        res[name] = {"n": n, "us": round(ms * 1e3, 2), "GB/s": round(bpe * n / (ms * 1e-3) / 1e9, 1),
+                     "config": "vec%d_u%d_b%d" % pyc.launch_config(h, n, reduce=True)}
     del ln, xi, xa
     # small dot: latency-bound (8 MiB fits in L2: warm timing)
     m = 1 << 20
     x = torch.from_numpy(inputs.uniform_f32(0, 0, m, -1.0, 1.0)).to(dev)
     y = torch.from_numpy(inputs.uniform_f32(0, 1, m, -1.0, 1.0)).to(dev)
     h = stock.create("dot_f32")
+    pyc.pyc_reduce_autotune(h, m, s)
     f = lambda: pyc.pyc_reduce_launch(h, m, [x.data_ptr(), y.data_ptr()], None, out.data_ptr(), s)
     ms = _time_fn(torch, f, 200)
     res["dot_f32_n2^20"] = {"n": m, "us": round(ms * 1e3, 2),
-                            "GB/s": round(8 * m / (ms * 1e-3) / 1e9, 1), "cache": "warm (fits L2)"}
+                            "GB/s": round(8 * m / (ms * 1e-3) / 1e9, 1), "cache": "warm (fits L2)",
+                            "config": "vec%d_u%d_b%d" % pyc.launch_config(h, m, reduce=True)}
     return res
 
 
@@ -376,6 +376,37 @@ def cpu_oracle_maps(n_sample, steps=1):
     return alg / sec / 1e9, sec
 
 
+def profile_reduce(args):
+    """Profiling driver (not a bench line): one stock reduction at n = 2^n_log2,
+    warm-up then `steps` launches, for ncu captures of a single kernel."""
+    import torch
+    from paper_1304_5553_gb300 import inputs, pyc, stock
+    torch.cuda.set_device(0)
+    n = N_MAP
+    name = args.profile_reduce
+    if name.startswith("sum_i32"):
+        arr = [inputs.int_uniform_i32(0, 0, n)]
+    elif name.startswith("argmin"):
+        arr = [inputs.argmin_with_minima(0, n)]
+    elif name.startswith("dot"):
+        arr = [inputs.uniform_f32(0, s, n, -1.0, 1.0) for s in range(2)]
+        if name.endswith("bf16"):
+            arr = [torch.from_numpy(a).to(torch.bfloat16) for a in arr]
+    else:
+        arr = [inputs.lognormal_signed_f32(0, 0, n)]
+    d = [(a if isinstance(a, torch.Tensor) else torch.from_numpy(a)).cuda() for a in arr]
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    h = stock.create(name)
+    s = torch.cuda.current_stream().cuda_stream
+    if args.autotune == "on":
+        pyc.pyc_reduce_autotune(h, n, s)
+    print("config vec%d_u%d_b%d" % pyc.launch_config(h, n, reduce=True), file=sys.stderr)
+    f = lambda: pyc.pyc_reduce_launch(h, n, [t.data_ptr() for t in d], None, out.data_ptr(), s)
+    ms = _time_fn(torch, f, args.steps, warmup=args.warmup)
+    print(json.dumps({"profile_reduce": name, "n": n, "us": round(ms * 1e3, 2),
+                      "note": "profiling driver, not a bench value"}))
+
+
 def run_gpu(args):
     import torch
     from paper_1304_5553_gb300 import pyc, stock
@@ -511,6 +542,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--only", default="", help="comma-separated subset of the maps (profiling)")
     ap.add_argument("--n-log2", type=int, default=28, help="map size (profiling captures only)")
+    ap.add_argument("--profile-reduce", default="",
+                    help="profiling driver: time one stock reduction only (not a bench line)")
     ap.add_argument("--autotune", default="on", choices=["on", "off"],
                     help="off: use the tuning cache / defaults without timing candidates")
     args = ap.parse_args()
@@ -520,6 +553,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_reduce:
+        profile_reduce(args)
     else:
         run_gpu(args)
 

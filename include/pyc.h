@@ -92,9 +92,9 @@ typedef struct {
  * the launch's size bucket, or the built-in default".  A NULL pyc_opts* means
  * all zero. */
 typedef struct {
-  int block;            /* threads per CTA: 0 or a multiple of 32 in [32, 1024] */
+  int block;            /* threads per CTA: 0 or a multiple of 32 in [32, 512] */
   int vec_bytes;        /* bytes per vector access: 0, 16 or 32 */
-  int items_per_thread; /* vector accesses per thread per tile (unroll): 0, 1, 2, 4 or 8 */
+  int items_per_thread; /* vector accesses per thread per tile (unroll): 0, 1, 2 or 4 */
   int compensated;      /* map-reduce only: 1 = compensated FP32 sum (two-sum per element,
                            pairwise (sum, error) combine, binary64 final combine).  Needs
                            result type F32 and reduce expression a+b. */
@@ -159,6 +159,20 @@ pyc_status pyc_map_create(const char* argspec, const char* stmt, const char* nam
 pyc_status pyc_map_launch(pyc_map_t h, int64_t n, void* const* ptrs, const void* scalars,
                           pyc_stream_t stream);
 
+/* Run a map on HOST arrays and return when the results are in host memory.
+ * The arrays are streamed through device staging buffers in chunks of 2^22
+ * elements, overlapping host-to-device copies, kernels and device-to-host
+ * copies on three streams of the library's own.  Arrays the statement reads
+ * are copied in and arrays it writes are copied back (one it may leave
+ * unwritten is also copied in).  Every array must be accessed as name[i] alone
+ * (an elementwise statement), else PYC_E_ARG.  host_ptrs: one host pointer per
+ * array; page-locked memory gives full copy bandwidth.  The staging buffers
+ * (three chunks of every array) are allocated by the first call and kept by the
+ * handle.  Synchronous: returns after the last copy back.  Errors as for
+ * pyc_map_launch. */
+pyc_status pyc_map_launch_host(pyc_map_t h, int64_t n, void* const* host_ptrs,
+                               const void* scalars);
+
 /* Number of declared parameters and their descriptions. */
 int pyc_map_num_params(pyc_map_t h);
 pyc_status pyc_map_param(pyc_map_t h, int idx, pyc_param_info* info);
@@ -171,6 +185,11 @@ const char* pyc_map_source(pyc_map_t h);
  * allocates and frees, remember the fastest for the handle and persist it in the
  * tuning cache.  Synchronises the stream.  (Automated tuning, Sec. 3.3.1.) */
 pyc_status pyc_map_autotune(pyc_map_t h, int64_t n, pyc_stream_t stream);
+
+/* The launch configuration (vector bytes, unroll, block) a launch of n
+ * elements would use now: explicit options, else the tuned value of n's size
+ * bucket, else the default. */
+pyc_status pyc_map_config(pyc_map_t h, int64_t n, int* vec_bytes, int* unroll, int* block);
 
 void pyc_map_destroy(pyc_map_t h);
 
@@ -246,6 +265,7 @@ int pyc_reduce_scalar_bytes(pyc_reduce_t h);
 int pyc_reduce_out_bytes(pyc_reduce_t h);
 const char* pyc_reduce_source(pyc_reduce_t h);
 pyc_status pyc_reduce_autotune(pyc_reduce_t h, int64_t n, pyc_stream_t stream);
+pyc_status pyc_reduce_config(pyc_reduce_t h, int64_t n, int* vec_bytes, int* unroll, int* block);
 void pyc_reduce_destroy(pyc_reduce_t h);
 
 /* ------------------------------------------------------------------ serving */

@@ -282,7 +282,11 @@ PYC_API int pyc_map_scalar_bytes(pyc_map_t h) { return h ? h->spec.scalar_bytes 
 
 PYC_API const char* pyc_map_source(pyc_map_t h) { return h ? h->source.c_str() : ""; }
 
-PYC_API void pyc_map_destroy(pyc_map_t h) { delete h; }
+PYC_API void pyc_map_destroy(pyc_map_t h) {
+  if (!h) return;
+  free_host_pipe(h);
+  delete h;
+}
 
 // ------------------------------------------------------------------ map-reduce
 
@@ -348,7 +352,9 @@ PYC_API pyc_status pyc_reduce_create(pyc_dtype out_dtype, const char* neutral,
     h->tag = kernel_tag(nullptr, 'r',
                         h->spec.canonical + "|" + std::to_string((int)out_dtype) + "|" + neu +
                             "|" + red + "|" + mrw + "|" + std::to_string((int)h->kind));
-    h->gen = generate_reduce(h->spec, out_dtype, h->kind, neu, red, mrw, h->preamble, h->tag);
+    int ordered = (arg && !reduce_expr) ? (out_dtype == PYC_ARGMIN_F32 ? 1 : 2) : 0;
+    h->gen = generate_reduce(h->spec, out_dtype, h->kind, neu, red, mrw, h->preamble, h->tag,
+                             ordered);
     h->source = h->gen.source;
     finish_handle(*h, true);
     *out = h.release();

@@ -311,6 +311,46 @@ std::string group_io(const ArgSpec& spec, bool load) {
   return o.str();
 }
 
+// Double-buffer declarations / loads / name bindings / fold of one tile for
+// the reduction span (lifted arrays only; a map expression never writes them).
+std::string buf_decls(const ArgSpec& spec, const char* prefix, const std::string& count) {
+  std::ostringstream o;
+  for (auto& p : spec.params)
+    if (p.is_ptr && p.lifted)
+      o << "  __align__(32) " << device_type(p.dtype) << " " << prefix << p.name << "[" << count
+        << "];\n";
+  return o.str();
+}
+
+std::string buf_load(const ArgSpec& spec, const char* prefix, const std::string& base) {
+  std::ostringstream o;
+  o << "#pragma unroll\n    for (int pyc_u = 0; pyc_u < U; ++pyc_u) {\n"
+    << "      const pyc_i64 pyc_e0 = (" << base << ") + (pyc_i64)pyc_u * pyc_step;\n";
+  for (auto& p : spec.params)
+    if (p.is_ptr && p.lifted && p.read)
+      o << "      pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&" << prefix << p.name
+        << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
+  o << "    }\n";
+  return o.str();
+}
+
+std::string buf_refs(const ArgSpec& spec, const char* prefix) {
+  std::ostringstream o;
+  for (auto& p : spec.params)
+    if (p.is_ptr && p.lifted)
+      o << "      " << device_type(p.dtype) << " (&pyc_r_" << p.name << ")[T] = " << prefix
+        << p.name << ";\n";
+  return o.str();
+}
+
+std::string fold_tile(const std::string& map_expr, const std::string& base) {
+  std::ostringstream o;
+  o << "#pragma unroll\n      for (int pyc_k = 0; pyc_k < T; ++pyc_k) {\n"
+    << "        const pyc_i64 i = (" << base << ") + (pyc_i64)(pyc_k / E) * pyc_step + (pyc_k % E);\n"
+    << "        pyc_fold_ordered(pyc_acc[pyc_k % A], (" << map_expr << "), i);\n      }\n";
+  return o.str();
+}
+
 std::string scalar_io(const ArgSpec& spec, bool load) {
   std::ostringstream o;
   for (auto& p : spec.params) {
@@ -504,7 +544,7 @@ __device__ __forceinline__ void pyc_map_batched_body(const pyc_mtask* __restrict
 ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind kind,
                           const std::string& neutral, const std::string& reduce_expr,
                           const std::string& map_expr, const std::string& preamble,
-                          const std::string& tag) {
+                          const std::string& tag, int ordered_arg) {
   ReduceGen g;
   const int mins = lifted_min_bytes(spec);
   std::string acc_t, out_t;
@@ -596,6 +636,22 @@ __device__ __forceinline__ pyc_out_t pyc_finalize(const pyc_acc_t a) {
 )PYC";
       break;
   }
+  // Fold used in the vector body.  Each accumulator slot k sees the indices
+  // of its elements in increasing order there, so for the built-in argmin /
+  // argmax rule a strict comparison already keeps the first index; the
+  // neutral element (index LLONG_MAX) is replaced by the first value seen.
+  // Everything else (and the scalar leftovers, which visit the head after the
+  // body) uses the full fold.
+  if (ordered_arg == 1 || ordered_arg == 2) {
+    o << "template <typename V> __device__ __forceinline__ void pyc_fold_ordered(pyc_acc_t& pyc_a, "
+         "const V pyc_v, const pyc_i64 pyc_i) {\n"
+         "  const float pyc_f = (float)(pyc_v);\n"
+         "  if (pyc_f " << (ordered_arg == 1 ? "<" : ">") << " pyc_a.v || pyc_a.i == LLONG_MAX) { "
+         "pyc_a.v = pyc_f; pyc_a.i = pyc_i; }\n}\n";
+  } else {
+    o << "template <typename V> __device__ __forceinline__ void pyc_fold_ordered(pyc_acc_t& pyc_a, "
+         "const V pyc_v, const pyc_i64 pyc_i) { pyc_fold(pyc_a, pyc_v, pyc_i); }\n";
+  }
   o << R"PYC(
 struct pyc_combine_op {
   __device__ __forceinline__ pyc_acc_t operator()(const pyc_acc_t a, const pyc_acc_t b) const { return pyc_combine(a, b); }
@@ -619,27 +675,34 @@ __device__ __forceinline__ pyc_acc_t pyc_reduce_span(const pyc_args& pyc_p, cons
   pyc_acc_t pyc_acc[A];
 #pragma unroll
   for (int k = 0; k < A; ++k) pyc_acc[k] = pyc_neutral();
+  // Tiles are register double-buffered: the loads of tile t+1 are issued
+  // before tile t is folded, so memory traffic overlaps the arithmetic.
   const pyc_i64 pyc_step = (pyc_i64)pyc_nthr * E;
   const pyc_i64 pyc_tile = pyc_step * U;
   const pyc_i64 pyc_nt = pyc_ve > pyc_vs ? (pyc_ve - pyc_vs) / pyc_tile : 0;
-  for (pyc_i64 pyc_t = 0; pyc_t < pyc_nt; ++pyc_t) {
-    const pyc_i64 pyc_b0 = pyc_vs + pyc_t * pyc_tile + (pyc_i64)pyc_tid * E;
-    {
+  const pyc_i64 pyc_tb = pyc_vs + (pyc_i64)pyc_tid * E;
 )PYC";
-  o << reg_decls(spec, "T");
-  o << R"PYC(#pragma unroll
-      for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
-        const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+  // unroll 1-2: double-buffered; unroll 4 (registers already full): single buffer
+  o << "  if constexpr (U <= 2) {\n";
+  o << buf_decls(spec, "pyc_ba_", "T") << buf_decls(spec, "pyc_bb_", "T");
+  o << "  if (pyc_nt > 0) {\n" << buf_load(spec, "pyc_ba_", "pyc_tb") << "  }\n";
+  o << R"PYC(  for (pyc_i64 pyc_t = 0; pyc_t < pyc_nt; pyc_t += 2) {
+    const pyc_i64 pyc_b0 = pyc_tb + pyc_t * pyc_tile;
+    const pyc_i64 pyc_b1 = pyc_b0 + pyc_tile;
+    const bool pyc_has1 = pyc_t + 1 < pyc_nt;
+    if (pyc_has1) {
 )PYC";
-  o << group_io(spec, true);
-  o << R"PYC(      }
-#pragma unroll
-      for (int pyc_k = 0; pyc_k < T; ++pyc_k) {
-        const pyc_i64 i = pyc_b0 + (pyc_i64)(pyc_k / E) * pyc_step + (pyc_k % E);
-        pyc_fold(pyc_acc[pyc_k % A], ()PYC" << map_expr << R"PYC(), i);
-      }
-    }
-  }
+  o << buf_load(spec, "pyc_bb_", "pyc_b1");
+  o << "    }\n    {\n" << buf_refs(spec, "pyc_ba_") << fold_tile(map_expr, "pyc_b0") << "    }\n";
+  o << "    if (pyc_t + 2 < pyc_nt) {\n" << buf_load(spec, "pyc_ba_", "pyc_b1 + pyc_tile") << "    }\n";
+  o << "    if (pyc_has1) {\n" << buf_refs(spec, "pyc_bb_") << fold_tile(map_expr, "pyc_b1")
+    << "    }\n  }\n";
+  o << "  } else {\n";
+  o << "  for (pyc_i64 pyc_t = 0; pyc_t < pyc_nt; ++pyc_t) {\n"
+       "    const pyc_i64 pyc_b0 = pyc_tb + pyc_t * pyc_tile;\n    {\n";
+  o << buf_decls(spec, "pyc_ba_", "T") << buf_load(spec, "pyc_ba_", "pyc_b0");
+  o << buf_refs(spec, "pyc_ba_") << fold_tile(map_expr, "pyc_b0") << "    }\n  }\n  }\n";
+  o << R"PYC(
   const pyc_i64 pyc_r0 = pyc_vs + pyc_nt * pyc_tile;
   const pyc_i64 pyc_ns = pyc_se - pyc_ss;
   const pyc_i64 pyc_nr = (pyc_ve > pyc_r0 ? pyc_ve - pyc_r0 : 0) + pyc_ns;

@@ -51,10 +51,12 @@ struct ReduceGen {
   int task_off_slot0 = 0;
 };
 
+// ordered_arg: 0, or for the built-in argmin (1) / argmax (2) rule a cheaper
+// fold for the vector body, where each accumulator sees increasing indices.
 ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind kind,
                           const std::string& neutral, const std::string& reduce_expr,
                           const std::string& map_rewritten, const std::string& preamble,
-                          const std::string& tag);
+                          const std::string& tag, int ordered_arg = 0);
 
 // Device-side spelling of a dtype (pyc_bf16 for BF16, ...).
 std::string device_type(pyc_dtype t);

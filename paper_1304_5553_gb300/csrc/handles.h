@@ -34,6 +34,7 @@ struct TuneTable {
 };
 
 struct BatchPlan;  // batched reducer plan (batched.cpp)
+struct HostPipe;   // staging for host-array maps (hostpipe.cpp)
 
 struct HandleBase {
   ArgSpec spec;
@@ -61,6 +62,8 @@ std::string kernel_tag(const char* name, char prefix, const std::string& spec_te
 
 struct pyc_map : pyc::HandleBase {
   pyc::MapGen gen;
+  std::mutex pipe_mu;
+  pyc::HostPipe* pipe = nullptr;  // created by the first pyc_map_launch_host
 };
 
 struct pyc_reduce : pyc::HandleBase {
@@ -165,5 +168,6 @@ void write_map_work(const pyc_map* h, const LaunchCfg& cfg, const std::vector<Ma
 void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* offsets, void* const* ptrs,
                     const void* scalars, void* d_out, CUstream stream);
 void free_plans(pyc_reduce* h);
+void free_host_pipe(pyc_map* h);
 
 }  // namespace pyc

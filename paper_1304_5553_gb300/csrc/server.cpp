@@ -221,7 +221,8 @@ SlotLayout layout(int max_batch, int64_t task_bytes, int64_t item_bytes, int64_t
   return L;
 }
 
-// Builds and enqueues one batch; marks its requests launched.
+// Builds and enqueues one batch (without the server lock: it reads only the
+// batch's immutable request fields and its own slot).
 void launch_batch(pyc_server* s, Batch& b) {
   const Driver& d = drv();
   Slot& sl = s->slots[b.slot];
@@ -270,7 +271,6 @@ void launch_batch(pyc_server* s, Batch& b) {
     nitems = (int)items.size();
     f = h->mod->function(h->kname("pyc_mbatch", cfg.v));
   }
-  const int64_t t_launch = now_ns();
   if (nitems > 0) {
     PYC_CU(d.cuMemcpyHtoDAsync(sl.dev + L.tasks, sl.host, (size_t)(L.task_bytes + L.item_bytes), st));
     int grid = std::max(1, std::min(resident_ctas(f, cfg.block), nitems));
@@ -289,11 +289,6 @@ void launch_batch(pyc_server* s, Batch& b) {
   if (reduce && L.res_bytes > 0)
     PYC_CU(d.cuMemcpyDtoHAsync(sl.host + L.host_res, sl.dev + L.res, (size_t)L.res_bytes, st));
   PYC_CU(d.cuEventRecord(sl.ev, st));
-  for (SReq* r : b.reqs) {
-    r->state = kLaunched;
-    r->res.t_launch_ns = t_launch;
-    r->res.batch_size = (int32_t)b.reqs.size();
-  }
 }
 
 // Retire the batch (results to the requests, slot freed).  Caller holds mu.
@@ -380,7 +375,10 @@ void scheduler(pyc_server* s) {
       s->admitted.push_back(r);
     }
     notify();
-    // 3. batches: group admitted requests by handle, in arrival order
+    // 3. batches: group admitted requests by handle, in arrival order.  While
+    //    num_streams batches are already running, admitted requests wait and
+    //    accumulate into larger batches, unless a full batch is ready.
+    std::vector<Batch> to_launch;
     while (!s->admitted.empty()) {
       int free_slot = -1;
       for (size_t k = 0; k < s->slots.size(); ++k)
@@ -389,31 +387,58 @@ void scheduler(pyc_server* s) {
           break;
         }
       if (free_slot < 0) break;
-      Batch b;
-      b.h = s->admitted.front()->handle();
-      b.kind = s->admitted.front()->kind;
+      if ((int)(s->inflight.size() + to_launch.size()) >= s->cfg.num_streams &&
+          (int)s->admitted.size() < s->cfg.max_batch)
+        break;
+      Batch bt;
+      bt.h = s->admitted.front()->handle();
+      bt.kind = s->admitted.front()->kind;
       std::vector<SReq*> rest;
       int64_t chunks = 0;
       for (SReq* r : s->admitted) {
         int64_t rc = r->n / kChunkElems + 2;
-        if (r->handle() == b.h && (int)b.reqs.size() < s->cfg.max_batch &&
-            (b.reqs.empty() || chunks + rc <= (int64_t)1 << 15)) {
-          b.reqs.push_back(r);
+        if (r->handle() == bt.h && (int)bt.reqs.size() < s->cfg.max_batch &&
+            (bt.reqs.empty() || chunks + rc <= (int64_t)1 << 15)) {
+          bt.reqs.push_back(r);
           chunks += rc;
         } else {
           rest.push_back(r);
         }
       }
       s->admitted.swap(rest);
-      b.slot = free_slot;
+      bt.slot = free_slot;
       s->slots[free_slot].busy = true;
-      try {
-        launch_batch(s, b);
-        s->inflight.push_back(std::move(b));
-      } catch (const std::exception& e) {
-        if (s->fatal.empty()) s->fatal = e.what();
-        s->slots[free_slot].busy = false;
-        for (SReq* r : b.reqs) finish_req(s, r, PYC_E_CUDA, now_ns());
+      to_launch.push_back(std::move(bt));
+    }
+    if (!to_launch.empty()) {
+      // build and enqueue outside the lock: submitters and pollers go on
+      std::vector<int> ok(to_launch.size(), 0);
+      std::vector<std::string> err(to_launch.size());
+      lk.unlock();
+      for (size_t k = 0; k < to_launch.size(); ++k) {
+        try {
+          launch_batch(s, to_launch[k]);
+          ok[k] = 1;
+        } catch (const std::exception& e) {
+          err[k] = e.what();
+        }
+      }
+      lk.lock();
+      const int64_t tl = now_ns();
+      for (size_t k = 0; k < to_launch.size(); ++k) {
+        Batch& bt = to_launch[k];
+        if (ok[k]) {
+          for (SReq* r : bt.reqs) {
+            r->state = kLaunched;
+            r->res.t_launch_ns = tl;
+            r->res.batch_size = (int32_t)bt.reqs.size();
+          }
+          s->inflight.push_back(std::move(bt));
+        } else {
+          if (s->fatal.empty()) s->fatal = err[k];
+          s->slots[bt.slot].busy = false;
+          for (SReq* r : bt.reqs) finish_req(s, r, PYC_E_CUDA, tl);
+        }
       }
     }
     notify();
@@ -687,18 +712,24 @@ void replay_server(pyc_server* s, int64_t nreq, const pyc_request* reqs, const i
         s->finished.pop_front();
       }
     }
-    for (uint64_t id : fin) {
-      auto it = index.find(id);
-      if (it == index.end()) continue;
-      int64_t k = it->second;
-      pyc_result r;
-      if (pyc_server_poll(s, id, &r, 0) == PYC_OK) {
-        r.t_submit_ns = arr ? t0 + arr[k] : t0;  // latency is measured from the arrival
-        results[k] = r;
-        pyc_server_release(s, id);
+    if (!fin.empty()) {
+      // copy results and release, all under one lock
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (uint64_t id : fin) {
+        auto it = index.find(id);
+        auto rq = s->reqs.find(id);
+        if (it == index.end() || rq == s->reqs.end()) continue;
+        int64_t k = it->second;
+        SReq* r = rq->second.get();
+        results[k] = r->res;
+        results[k].t_submit_ns = arr ? t0 + arr[k] : t0;  // latency from the arrival
+        for (int64_t off : r->out_offs) s->arena.release(off);
+        if (r->counted) s->admitted_bytes -= r->bytes;
+        s->reqs.erase(rq);
+        index.erase(it);
         ++done;
       }
-      index.erase(it);
+      ++s->nevents;
     }
   }
   std::lock_guard<std::mutex> lk(s->mu);

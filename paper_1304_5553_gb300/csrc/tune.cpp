@@ -5,6 +5,7 @@
 // Keys: (digest of the generated source, map / reduce, size bucket).
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <fstream>
 #include <sstream>
 
@@ -110,6 +111,10 @@ void autotune(H* h, int64_t n, CUstream stream, bool reduce, Launch&& launch_one
       c.v = v;
       c.block = b;
       double us = time_us([&] { launch_one(c, nt, ptrs.data(), scal.data(), out); }, stream, 5);
+      if (std::getenv("PYC_TUNE_LOG"))
+        std::fprintf(stderr, "pyc tune %s %s n=%lld vec=%d unroll=%d block=%d %.2f us\n",
+                     reduce ? "reduce" : "map", h->tag.c_str(), (long long)nt, v.vec_bytes,
+                     v.unroll, b, us);
       if (us < best_us) {
         best_us = us;
         best = c;
@@ -177,6 +182,28 @@ void tune_cache_store(const HandleBase& h, bool reduce, int bucket, const Launch
 }  // namespace pyc
 
 using namespace pyc;
+
+PYC_API pyc_status pyc_map_config(pyc_map_t h, int64_t n, int* vec_bytes, int* unroll,
+                                  int* block) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    LaunchCfg c = choose_cfg(*h, n, false);
+    if (vec_bytes) *vec_bytes = c.v.vec_bytes;
+    if (unroll) *unroll = c.v.unroll;
+    if (block) *block = c.block;
+  });
+}
+
+PYC_API pyc_status pyc_reduce_config(pyc_reduce_t h, int64_t n, int* vec_bytes, int* unroll,
+                                     int* block) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    LaunchCfg c = choose_cfg(*h, n, true);
+    if (vec_bytes) *vec_bytes = c.v.vec_bytes;
+    if (unroll) *unroll = c.v.unroll;
+    if (block) *block = c.block;
+  });
+}
 
 PYC_API pyc_status pyc_map_autotune(pyc_map_t h, int64_t n, pyc_stream_t stream) {
   return guarded([&] {

@@ -95,7 +95,8 @@ EXPORTED = [
     "pyc_reduce_param", "pyc_reduce_scalar_bytes", "pyc_reduce_out_bytes", "pyc_reduce_source",
     "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats", "pyc_reduce_launch_static",
     "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
-    "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay",
+    "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay", "pyc_map_launch_host",
+    "pyc_map_config", "pyc_reduce_config",
 ]
 
 _lib = None
@@ -124,6 +125,9 @@ def load(build_if_missing=True):
         "pyc_version": (cp, []),
         "pyc_map_create": (st, [cp, cp, cp, ctypes.POINTER(pyc_opts), ctypes.POINTER(vp)]),
         "pyc_map_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp]),
+        "pyc_map_launch_host": (st, [vp, i64, ctypes.POINTER(vp), vp]),
+        "pyc_map_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
+        "pyc_reduce_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_map_num_params": (i32, [vp]),
         "pyc_map_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
         "pyc_map_scalar_bytes": (i32, [vp]),
@@ -215,6 +219,11 @@ def pyc_map_launch(h, n, ptrs, scalars=None, stream=None):
     _check(load().pyc_map_launch(h, int(n), _ptr_array(ptrs), scalars, _stream(stream)))
 
 
+def pyc_map_launch_host(h, n, host_ptrs, scalars=None):
+    """Map over host arrays (addresses of page-locked or pageable host memory)."""
+    _check(load().pyc_map_launch_host(h, int(n), _ptr_array(host_ptrs), scalars))
+
+
 def pyc_map_destroy(h):
     load().pyc_map_destroy(h)
 
@@ -269,6 +278,14 @@ def pyc_reduce_out_bytes(h) -> int:
 
 def pyc_reduce_autotune(h, n, stream=None):
     _check(load().pyc_reduce_autotune(h, int(n), _stream(stream)))
+
+
+def launch_config(h, n, reduce=False):
+    """(vec_bytes, unroll, block) a launch of n elements would use."""
+    v, u, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    fn = load().pyc_reduce_config if reduce else load().pyc_map_config
+    _check(fn(h, int(n), ctypes.byref(v), ctypes.byref(u), ctypes.byref(b)))
+    return v.value, u.value, b.value
 
 
 def pyc_cache_stats():

@@ -228,3 +228,29 @@ def test_launch_argument_errors():
         pyc.pyc_map_launch(h, -1, [d.data_ptr()] * 3, sc, _stream())
     assert e.value.status == pyc.PYC_E_ARG
     pyc.pyc_map_launch(h, 0, [0, 0, 0], sc, _stream())  # n == 0: no-op, pointers unused
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_host_array_launch(bf16):
+    """pyc_map_launch_host on page-locked host arrays: several chunks plus a
+    ragged tail, bit-exact against binary32 source order; in-place too."""
+    n = 3 * (1 << 22) + 12345
+    x = inputs.uniform_f32(40, 0, n, -2.0, 2.0)
+    y = inputs.uniform_f32(40, 1, n, -2.0, 2.0)
+    dt = BF if bf16 else torch.float32
+    if bf16:
+        x, y = inputs.to_bf16_values(x), inputs.to_bf16_values(y)
+    hx = torch.from_numpy(x).to(dt).pin_memory()
+    hy = torch.from_numpy(y).to(dt).pin_memory()
+    hz = torch.full((n,), -4096.0, dtype=dt).pin_memory()
+    h = stock.create("lin_comb_bf16" if bf16 else "lin_comb_f32")
+    pyc.pyc_map_launch_host(h, n, [hx.data_ptr(), hy.data_ptr(), hz.data_ptr()],
+                            pyc.pack_scalars(h, [A, B]))
+    assert np.array_equal(hz.float().numpy(), oracle.map_lin_comb_f32ops(A, x, B, y, out_bf16=bf16))
+    a = torch.from_numpy(x.astype(np.float32)).pin_memory()
+    pyc.pyc_map_launch_host(stock.create("scale2_f32"), n, [a.data_ptr()])
+    assert np.array_equal(a.numpy(), oracle.map_scale(2, x)[0])
+    with pytest.raises(pyc.PycError) as e:  # not elementwise: rejected
+        k = pyc.pyc_map_create("float *x, float *z", "z[i] = i + 1 < n ? x[i + 1] : 0.0f")
+        pyc.pyc_map_launch_host(k, 10, [hx.data_ptr(), hz.data_ptr()])
+    assert e.value.status == pyc.PYC_E_ARG

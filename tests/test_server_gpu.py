@@ -57,8 +57,15 @@ def _map_out(res, n):
 
 
 def test_alone_and_in_the_mix_are_identical(pools):
+    """Each probe request gives the same bits alone and inside batches of other
+    requests.  To make the batching deterministic, a blocker request holds the
+    whole memory budget while the mix queues up; releasing it admits the queue
+    at once, so the scheduler forms large batches."""
     host, dev = pools
-    srv = pyc.pyc_server_create(1 << 30, arena_bytes=1 << 28, num_streams=3, max_batch=64,
+    nb = 1 << 24
+    zeros = torch.zeros(2 * nb, device="cuda")
+    budget = 8 * nb + 12  # the blocker's bytes (two binary32 arrays + result) + 8
+    srv = pyc.pyc_server_create(budget, arena_bytes=1 << 27, num_streams=3, max_batch=64,
                                 max_inflight=6)
     try:
         probes = [(pyc.PYC_REQ_REDUCE, "dot_f32", 300001, 5),
@@ -73,22 +80,26 @@ def test_alone_and_in_the_mix_are_identical(pools):
             out = _map_out(res, p[2]).cpu().numpy().copy() if p[0] == pyc.PYC_REQ_MAP else None
             pyc.pyc_server_release(srv, rid)
             alone.append((val, out))
-        # the same probes inside a stream of other requests of all kinds and sizes
+        blocker = pyc.make_request(pyc.PYC_REQ_REDUCE, stock.create("dot_f32"), nb,
+                                   [zeros.data_ptr(), zeros.data_ptr() + 4 * nb])
+        bid, _ = _run_one(srv, blocker)  # finished, not released: the budget is held
         rng = np.random.default_rng(5)
         ids, keep = [], []
         for k in range(300):
             if k % 50 == 25:
-                req = _req(*probes[(k // 50) % len(probes)], dev)
                 probe = (k // 50) % len(probes)
+                req = _req(*probes[probe], dev)
             else:
                 kind = pyc.PYC_REQ_REDUCE if rng.random() < 0.6 else pyc.PYC_REQ_MAP
                 name = rng.choice(["dot_f32", "dot_i32_i64"]) if kind else rng.choice(
                     ["lin_comb_f32", "lin_comb_i32"])
-                n = int(2 ** rng.uniform(0, 20))
+                n = int(2 ** rng.uniform(0, 17))
                 req = _req(kind, str(name), n, int(rng.integers(0, POOL - n)), dev)
                 probe = -1
             keep.append(req)
             ids.append((pyc.pyc_server_submit(srv, req), probe))
+        assert pyc.pyc_server_get_stats(srv)["queued"] == 300
+        pyc.pyc_server_release(srv, bid)
         batched_probe = 0
         for rid, probe in ids:
             res = pyc.pyc_server_poll(srv, rid, 20_000_000)
@@ -102,7 +113,7 @@ def test_alone_and_in_the_mix_are_identical(pools):
             pyc.pyc_server_release(srv, rid)
         assert batched_probe > 1  # the probes really ran inside batches
         st = pyc.pyc_server_get_stats(srv)
-        assert st["completed"] == 304 and st["failed"] == 0 and st["admitted_bytes"] == 0
+        assert st["completed"] == 305 and st["failed"] == 0 and st["admitted_bytes"] == 0
         assert st["arena_in_use"] == 0
         # results against the oracle
         v = np.frombuffer(alone[0][0][:4], np.float32)[0]
