@@ -263,6 +263,7 @@ def bench_batched(torch, pyc, stock, dev, reps=5):
         out = torch.zeros(lens.size, dtype=torch.float32, device=dev)
         h = stock.create(name)
         ptrs = [x.data_ptr(), y.data_ptr()]
+        pyc.pyc_reduce_batched_autotune(h, lens.size, off, ptrs, None, out.data_ptr(), s)
         fb = lambda: pyc.pyc_reduce_batched(h, lens.size, off, ptrs, None, out.data_ptr(), s)
         ms_b = _time_fn(torch, fb, reps)
 
@@ -376,6 +377,29 @@ def cpu_oracle_maps(n_sample, steps=1):
     return alg / sec / 1e9, sec
 
 
+def kernel_name(pyc, stock, name):
+    h = stock.create(name)
+    v, u, b = pyc.launch_config(h, N_MAP)
+    return "pyc_map_%s_v%d_u%d" % (name, v, u)
+
+
+def measured_traffic(pyc, stock, name, n):
+    """DRAM bytes (read + write) per launch of this kernel from the committed ncu
+    summary profiles/dram_traffic.txt, scaled to n elements; None when no
+    capture exists for the kernel as currently generated (source digest)."""
+    import hashlib
+    kname = kernel_name(pyc, stock, name)
+    digest = hashlib.sha256(pyc.pyc_map_source(stock.create(name)).encode()).hexdigest()[:16]
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "dram_traffic.txt")):
+            f = line.split("#")[0].split()
+            if len(f) >= 3 and f[0] == kname and f[1] == digest:
+                return round(float(f[2]) * n)
+    except OSError:
+        pass
+    return None
+
+
 def profile_reduce(args):
     """Profiling driver (not a bench line): one stock reduction at n = 2^n_log2,
     warm-up then `steps` launches, for ncu captures of a single kernel."""
@@ -485,8 +509,10 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "n": N_MAP, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(ach / peak, 4), "traffic": None,
-                         "kernel": "pyc_map (%s)" % dom, "peak_kind": peak_kind},
+                         "frac": round(ach / peak, 4),
+                         "traffic": measured_traffic(pyc, stock, dom, N_MAP),
+                         "kernel": "%s (%s)" % (kernel_name(pyc, stock, dom), dom),
+                         "peak_kind": peak_kind},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(names) * args.steps,
             "clocks": clocks, "details": details,
         }

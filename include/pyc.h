@@ -258,6 +258,16 @@ pyc_status pyc_reduce_batched(pyc_reduce_t h, int64_t nseg, const int64_t* seg_o
 pyc_status pyc_reduce_launch_static(pyc_reduce_t h, int64_t n, void* const* ptrs,
                                     const void* scalars, void* d_out, pyc_stream_t stream);
 
+/* Tune the batched launch (automated tuning, Sec. 3.3.1): time every vector
+ * width x unroll x block candidate of the segmented reducer on this segment
+ * table (same arguments as pyc_reduce_batched; d_out receives results), keep the
+ * fastest for the handle's batched launches -- pyc_reduce_batched and the
+ * server's map-reduce batches -- and persist it in the tuning cache.
+ * Synchronises the stream. */
+pyc_status pyc_reduce_batched_autotune(pyc_reduce_t h, int64_t nseg, const int64_t* seg_offsets,
+                                       void* const* ptrs, const void* scalars, void* d_out,
+                                       pyc_stream_t stream);
+
 int pyc_reduce_num_params(pyc_reduce_t h);
 pyc_status pyc_reduce_param(pyc_reduce_t h, int idx, pyc_param_info* info);
 int pyc_reduce_scalar_bytes(pyc_reduce_t h);

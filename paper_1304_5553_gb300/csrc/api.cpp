@@ -379,6 +379,17 @@ PYC_API pyc_status pyc_reduce_batched(pyc_reduce_t h, int64_t nseg, const int64_
   });
 }
 
+PYC_API pyc_status pyc_reduce_batched_autotune(pyc_reduce_t h, int64_t nseg,
+                                               const int64_t* seg_offsets, void* const* ptrs,
+                                               const void* scalars, void* d_out,
+                                               pyc_stream_t stream) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    reduce_batched_autotune(h, nseg, seg_offsets, ptrs, scalars, d_out,
+                            reinterpret_cast<CUstream>(stream));
+  });
+}
+
 PYC_API int pyc_reduce_num_params(pyc_reduce_t h) { return h ? (int)h->spec.params.size() : -1; }
 
 PYC_API pyc_status pyc_reduce_param(pyc_reduce_t h, int idx, pyc_param_info* info) {

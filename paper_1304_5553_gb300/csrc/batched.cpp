@@ -10,6 +10,8 @@
 // the caller's stream; while the caller's stream is itself being captured the
 // kernel is launched directly so it becomes part of the caller's graph.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -128,11 +130,12 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
 
 }  // namespace
 
-void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const* ptrs,
-                    const void* scalars, void* d_out, CUstream stream) {
+namespace {
+
+void check_batched_args(pyc_reduce* h, int64_t nseg, const int64_t* off, void* d_out) {
   if (nseg < 0) fail(PYC_E_ARG, "nseg must be >= 0");
-  if (nseg == 0) return;
   if (nseg > (int64_t)INT32_MAX / 2) fail(PYC_E_ARG, "too many segments");
+  if (nseg == 0) return;
   if (!off) fail(PYC_E_ARG, "seg_offsets is NULL");
   if (!d_out) fail(PYC_E_ARG, "d_out is NULL");
   if (reinterpret_cast<uintptr_t>(d_out) % (uintptr_t)std::min(h->gen.out_bytes, 8))
@@ -140,9 +143,40 @@ void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const
   if (off[0] < 0) fail(PYC_E_ARG, "seg_offsets[0] must be >= 0");
   for (int64_t s = 0; s < nseg; ++s)
     if (off[s + 1] < off[s]) fail(PYC_E_ARG, "seg_offsets must be non-decreasing");
-  LaunchCfg cfg = choose_cfg(*h, kSmallTask, true);
-  if (!h->opts.items_per_thread) cfg.v.unroll = 1;
-  if (!h->opts.block) cfg.block = 256;
+}
+
+}  // namespace
+
+LaunchCfg batched_cfg(HandleBase& h, bool reduce) {
+  LaunchCfg c;
+  bool tuned = false;
+  {
+    std::lock_guard<std::mutex> lk(h.tune.mu);
+    auto it = h.tune.by_bucket.find(kBatchedBucket);
+    if (it != h.tune.by_bucket.end()) {
+      c = it->second;
+      tuned = true;
+    }
+  }
+  if (!tuned) {
+    if (reduce) {
+      c.v = Variant{16, 1};  // short segments are one warp each: small tiles
+      c.block = 256;
+    } else {
+      c = choose_cfg(h, (int64_t)1 << 26, false);
+    }
+  }
+  if (h.opts.block) c.block = h.opts.block;
+  if (h.opts.vec_bytes) c.v.vec_bytes = h.opts.vec_bytes;
+  if (h.opts.items_per_thread) c.v.unroll = h.opts.items_per_thread;
+  return c;
+}
+
+void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const* ptrs,
+                    const void* scalars, void* d_out, CUstream stream) {
+  check_batched_args(h, nseg, off, d_out);
+  if (nseg == 0) return;
+  LaunchCfg cfg = batched_cfg(*h, true);
 
   // key: everything the plan bakes in
   std::string k;
@@ -192,6 +226,69 @@ pyc_reduce::pyc_reduce() = default;
 pyc_reduce::~pyc_reduce() = default;
 
 namespace pyc {
+
+// Times every (variant, block) candidate on the caller's segment table (one
+// plan and graph each, three replays, best kept) and keeps the fastest as the
+// handle's batched configuration (also persisted in the tuning cache).
+void reduce_batched_autotune(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const* ptrs,
+                             const void* scalars, void* d_out, CUstream stream) {
+  check_batched_args(h, nseg, off, d_out);
+  if (nseg == 0) fail(PYC_E_ARG, "autotune needs nseg > 0");
+  const Driver& d = drv();
+  CUevent e0, e1;
+  PYC_CU(d.cuEventCreate(&e0, CU_EVENT_DEFAULT));
+  PYC_CU(d.cuEventCreate(&e1, CU_EVENT_DEFAULT));
+  LaunchCfg best;
+  double best_us = 1e30;
+  try {
+    for (const Variant& v : all_variants()) {
+      if (h->opts.vec_bytes && v.vec_bytes != h->opts.vec_bytes) continue;
+      if (h->opts.items_per_thread && v.unroll != h->opts.items_per_thread) continue;
+      for (int b : {128, 256, 512}) {
+        if (h->opts.block && b != h->opts.block) continue;
+        LaunchCfg c;
+        c.v = v;
+        c.block = b;
+        std::unique_ptr<BatchPlan> plan = build_plan(h, nseg, off, ptrs, scalars, d_out, c);
+        double us = 1e30;
+        try {
+          PYC_CU(d.cuGraphLaunch(plan->exec, stream));
+          for (int r = 0; r < 3; ++r) {
+            PYC_CU(d.cuEventRecord(e0, stream));
+            PYC_CU(d.cuGraphLaunch(plan->exec, stream));
+            PYC_CU(d.cuEventRecord(e1, stream));
+            PYC_CU(d.cuEventSynchronize(e1));
+            float ms = 0;
+            PYC_CU(d.cuEventElapsedTime(&ms, e0, e1));
+            us = std::min(us, (double)ms * 1000.0);
+          }
+        } catch (...) {
+          plan->release();
+          throw;
+        }
+        plan->release();
+        if (std::getenv("PYC_TUNE_LOG"))
+          std::fprintf(stderr, "pyc tune batched %s nseg=%lld vec=%d unroll=%d block=%d %.2f us\n",
+                       h->tag.c_str(), (long long)nseg, v.vec_bytes, v.unroll, b, us);
+        if (us < best_us) {
+          best_us = us;
+          best = c;
+        }
+      }
+    }
+  } catch (...) {
+    d.cuEventDestroy(e0);
+    d.cuEventDestroy(e1);
+    throw;
+  }
+  d.cuEventDestroy(e0);
+  d.cuEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(h->tune.mu);
+    h->tune.by_bucket[kBatchedBucket] = best;
+  }
+  tune_cache_store(*h, true, kBatchedBucket, best, best_us);
+}
 
 void free_plans(pyc_reduce* h) {
   std::lock_guard<std::mutex> lk(h->plan_mu);

@@ -164,9 +164,16 @@ struct MapItem {
 void write_map_work(const pyc_map* h, const LaunchCfg& cfg, const std::vector<MapTaskIn>& in,
                     std::vector<unsigned char>& tasks, std::vector<MapItem>& items);
 
-// Batched reducer (batched.cpp).
+// Batched reducer (batched.cpp).  The configuration of batched launches (the
+// segmented reducer and the server's batches) is tuned separately from single
+// launches and kept under this pseudo size bucket.
+constexpr int kBatchedBucket = -1;
+LaunchCfg batched_cfg(HandleBase& h, bool reduce);
 void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* offsets, void* const* ptrs,
                     const void* scalars, void* d_out, CUstream stream);
+void reduce_batched_autotune(pyc_reduce* h, int64_t nseg, const int64_t* offsets,
+                             void* const* ptrs, const void* scalars, void* d_out,
+                             CUstream stream);
 void free_plans(pyc_reduce* h);
 void free_host_pipe(pyc_map* h);
 

@@ -140,14 +140,7 @@ struct Batch {
 
 // Launch configuration the server uses for a handle's batches: fixed per
 // handle so that a request's result never depends on its batch.
-LaunchCfg batch_cfg(HandleBase& h, bool reduce) {
-  LaunchCfg c = choose_cfg(h, reduce ? kSmallTask : ((int64_t)1 << 26), reduce);
-  if (reduce) {
-    if (!h.opts.items_per_thread) c.v.unroll = 1;
-    if (!h.opts.block) c.block = 256;
-  }
-  return c;
-}
+LaunchCfg batch_cfg(HandleBase& h, bool reduce) { return batched_cfg(h, reduce); }
 
 }  // namespace
 

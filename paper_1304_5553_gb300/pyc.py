@@ -96,7 +96,7 @@ EXPORTED = [
     "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats", "pyc_reduce_launch_static",
     "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
     "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay", "pyc_map_launch_host",
-    "pyc_map_config", "pyc_reduce_config",
+    "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
 ]
 
 _lib = None
@@ -140,6 +140,8 @@ def load(build_if_missing=True):
         "pyc_reduce_batched": (st, [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(vp), vp, vp,
                                     vp]),
         "pyc_reduce_launch_static": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, vp]),
+        "pyc_reduce_batched_autotune": (st, [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(vp), vp,
+                                             vp, vp]),
         "pyc_reduce_num_params": (i32, [vp]),
         "pyc_reduce_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
         "pyc_reduce_scalar_bytes": (i32, [vp]),
@@ -262,6 +264,16 @@ def pyc_reduce_batched(h, nseg, seg_offsets, ptrs, scalars, d_out, stream=None):
     _check(load().pyc_reduce_batched(h, int(nseg),
                                      off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                      _ptr_array(ptrs), scalars, d_out, _stream(stream)))
+
+
+def pyc_reduce_batched_autotune(h, nseg, seg_offsets, ptrs, scalars, d_out, stream=None):
+    import numpy as np
+    off = np.ascontiguousarray(seg_offsets, dtype=np.int64)
+    if off.size != int(nseg) + 1:
+        raise ValueError("seg_offsets must hold nseg + 1 entries")
+    _check(load().pyc_reduce_batched_autotune(h, int(nseg),
+                                              off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                              _ptr_array(ptrs), scalars, d_out, _stream(stream)))
 
 
 def pyc_reduce_destroy(h):

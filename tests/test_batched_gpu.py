@@ -151,3 +151,23 @@ def test_capture_into_caller_graph():
         g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, want)
+
+
+def test_batched_autotune_keeps_results_within_bound():
+    lens = inputs.segment_lengths(nseg=2000, seed=16, max_log2=18)
+    off = _offsets(lens)
+    x = inputs.uniform_f32(16, 0, int(off[-1]), -1.0, 1.0)
+    y = inputs.uniform_f32(16, 1, int(off[-1]), -1.0, 1.0)
+    dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    h = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i]", "float *x, float *y")
+    try:
+        out = torch.zeros(len(lens), device="cuda")
+        ptrs = [dx.data_ptr(), dy.data_ptr()]
+        pyc.pyc_reduce_batched_autotune(h, len(lens), off, ptrs, None, out.data_ptr(), _s())
+        out.zero_()
+        pyc.pyc_reduce_batched(h, len(lens), off, ptrs, None, out.data_ptr(), _s())
+        torch.cuda.synchronize()
+        ref, ab = oracle.dot_segments_f32(off, x, y)
+        assert np.all(np.abs(out.cpu().numpy() - ref) <= plain_sum_bound(ab))
+    finally:
+        pyc.pyc_reduce_destroy(h)
