@@ -377,6 +377,22 @@ def cpu_oracle_maps(n_sample, steps=1):
     return alg / sec / 1e9, sec
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """The largest value over all ranks (the slowest replica's step time); the
+    value itself without a process group."""
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(step_bytes_per_rank, world, ms_step):
+    """Whole-job throughput: every rank's bytes over the slowest rank's step time."""
+    return world * step_bytes_per_rank / (ms_step * 1e-3) / 1e9
+
+
 def kernel_name(pyc, stock, name):
     h = stock.create(name)
     v, u, b = pyc.launch_config(h, N_MAP)
@@ -471,15 +487,11 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         total_ms, per = time_steps(torch, launch, names, args.steps, args.warmup, barrier)
     clocks = clk.summary()
-    ms_step = total_ms / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(total_ms / args.steps, dist, dev)
     step_bytes = sum(MAP_BYTES[k] for k in names) * N_MAP
     if args.n_log2 != 28 or args.only:
         print("note: reduced profiling configuration, not a bench value", file=sys.stderr)
-    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    value = whole_job_gbs(step_bytes, world, ms_step)
     peak, peak_kind = peaks()
     avg = {k: statistics.mean(v) for k, v in per.items()}
     dom = max(avg, key=lambda k: avg[k])

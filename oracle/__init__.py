@@ -45,8 +45,13 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(LIB_PATH)
+        # ORACLE_LIB: load another build of oracle.c instead (the mutation test
+        # uses it to check that the pins catch planted mistakes)
+        path = os.environ.get("ORACLE_LIB")
+        if not path:
+            build()
+            path = LIB_PATH
+        lib = ctypes.CDLL(path)
         i64, f64, vp = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
         sig = {
             "orc_round_bf16": (f64, [f64]),
