@@ -235,6 +235,36 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
     return res
 
 
+def bench_scans(torch, pyc, stock, dev, reps=10):
+    """n = 2^28 prefix scans (Sec. 3.2.6): two launches per scan.  GB/s counts the
+    algorithmic bytes (input read once, output written once); the two-pass
+    design reads the input twice, so its traffic is (2 in + 1 out) per element."""
+    from paper_1304_5553_gb300 import inputs
+    n = N_MAP
+    res = {}
+    s = torch.cuda.current_stream().cuda_stream
+    xf = torch.from_numpy(inputs.uniform_f32(0, 0, n, -1.0, 1.0)).to(dev)
+    xi = torch.from_numpy(inputs.int_uniform_i32(0, 0, n)).to(dev)
+    yf = torch.empty(n, dtype=torch.float32, device=dev)
+    yi = torch.empty(n, dtype=torch.int64, device=dev)
+    cases = [("cumsum_f32", xf, yf, 8, 12), ("cummax_f32", xf, yf, 8, 12),
+             ("cumsum_excl_i32_i64", xi, yi, 12, 16)]
+    peak, kind = peaks()
+    for name, x, y, bpe, traffic in cases:
+        h = stock.create(name)
+        pyc.pyc_scan_autotune(h, n, s)
+        f = (lambda h=h, x=x, y=y: pyc.pyc_scan_launch(h, n, [x.data_ptr(), y.data_ptr()], None, s))
+        ms = _time_fn(torch, f, reps)
+        gbs = bpe * n / (ms * 1e-3) / 1e9
+        res[name] = {"n": n, "us": round(ms * 1e3, 2), "GB/s": round(gbs, 1),
+                     "frac_of_%s_peak" % kind: round(gbs / peak, 4),
+                     "two_pass_bytes_per_elem": traffic,
+                     "config": "vec%d_u%d_b%d" % pyc.launch_config(h, n, reduce="scan")}
+    del xf, xi, yf, yi
+    torch.cuda.empty_cache()
+    return res
+
+
 def _time_fn(torch, f, reps, warmup=3):
     for _ in range(warmup):
         f()
@@ -505,6 +535,7 @@ def run_gpu(args):
     e2e = None
     if rank == 0 and not args.quick:
         details["reductions"] = bench_reductions(torch, pyc, stock, dev)
+        details["scans"] = bench_scans(torch, pyc, stock, dev)
         details["batched"] = bench_batched(torch, pyc, stock, dev)
         details["serving"] = bench_serving(torch, pyc, stock, dev)
     if not args.quick:

@@ -278,6 +278,39 @@ pyc_status pyc_reduce_autotune(pyc_reduce_t h, int64_t n, pyc_stream_t stream);
 pyc_status pyc_reduce_config(pyc_reduce_t h, int64_t n, int* vec_bytes, int* unroll, int* block);
 void pyc_reduce_destroy(pyc_reduce_t h);
 
+/* ------------------------------------------------------------------ scan */
+
+/* Parallel prefix scan (Sec. 3.2.6: the packages' parallel prefix sums), in the
+ * spec style of the map-reduce.
+ *   dtype        value type: F32, F64, I32, I64, U32 or U64.
+ *   neutral      C expression of the neutral element of scan_expr.
+ *   scan_expr    associative C expression in a and b (a earlier, b later), e.g. "a+b".
+ *   input_expr   value of element i, e.g. "x[i]".
+ *   output_stmt  statement run for each i with `item` = the inclusive prefix
+ *                scan_expr(input(0), ..., input(i)) and `prev_item` = the exclusive
+ *                prefix (neutral for i = 0), e.g. "y[i] = item" or "y[i] = prev_item".
+ *   argspec      C parameter list; "item" and "prev_item" are reserved names.
+ * Floating-point association follows a fixed tree that depends on (n, tuning).
+ * Errors as for pyc_reduce_create. */
+typedef struct pyc_scan* pyc_scan_t;
+pyc_status pyc_scan_create(pyc_dtype dtype, const char* neutral, const char* scan_expr,
+                           const char* input_expr, const char* output_stmt, const char* argspec,
+                           const pyc_opts* opts, pyc_scan_t* out);
+
+/* Scan over i in [0, n): two launches on `stream` (chunk totals and carries,
+ * then the chunk scans with the output statement); no host round trip.  The
+ * handle keeps one workspace per (context, stream).  n == 0 is a no-op. */
+pyc_status pyc_scan_launch(pyc_scan_t h, int64_t n, void* const* ptrs, const void* scalars,
+                           pyc_stream_t stream);
+int pyc_scan_num_params(pyc_scan_t h);
+pyc_status pyc_scan_param(pyc_scan_t h, int idx, pyc_param_info* info);
+int pyc_scan_scalar_bytes(pyc_scan_t h);
+const char* pyc_scan_source(pyc_scan_t h);
+pyc_status pyc_scan_autotune(pyc_scan_t h, int64_t n, pyc_stream_t stream);
+/* (vec_bytes, unroll, block) a launch of n elements would use (as pyc_map_config). */
+pyc_status pyc_scan_config(pyc_scan_t h, int64_t n, int* vec_bytes, int* unroll, int* block);
+void pyc_scan_destroy(pyc_scan_t h);
+
 /* ------------------------------------------------------------------ serving */
 
 /* A request-serving loop over map and map-reduce handles (continuous

@@ -72,6 +72,9 @@ def _load():
             "orc_min_f32": (ctypes.c_float, [i64, vp]),
             "orc_argmin_f32": (None, [i64, vp, vp, vp]),
             "orc_argmax_f32": (None, [i64, vp, vp, vp]),
+            "orc_scan_sum_f32": (None, [i64, vp, vp, vp]),
+            "orc_scan_sum_i32_i64": (None, [i64, vp, ctypes.c_int, vp]),
+            "orc_scan_max_f32": (None, [i64, vp, vp]),
             "orc_exact_sum_f64": (f64, [i64, vp]),
             "orc_exact_dot_f32": (f64, [i64, vp, vp]),
             "orc_exact_sum_f32": (f64, [i64, vp]),
@@ -231,6 +234,30 @@ def argmax_f32(x):
     v, i = ctypes.c_float(), ctypes.c_int64()
     _load().orc_argmax_f32(x.size, _ptr(x), ctypes.addressof(v), ctypes.addressof(i))
     return float(v.value), int(i.value)
+
+
+# ------------------------------------------------------------------ scans
+
+def scan_sum_f32(x):
+    """Inclusive prefix sums in binary64 (compensated) and prefix sums of |x|."""
+    x = _f32(x)
+    incl, ab = np.empty(x.size, np.float64), np.empty(x.size, np.float64)
+    _load().orc_scan_sum_f32(x.size, _ptr(x), _ptr(incl), _ptr(ab))
+    return incl, ab
+
+
+def scan_sum_i32_i64(x, exclusive=False):
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    out = np.empty(x.size, np.int64)
+    _load().orc_scan_sum_i32_i64(x.size, _ptr(x), int(exclusive), _ptr(out))
+    return out
+
+
+def scan_max_f32(x):
+    x = _f32(x)
+    out = np.empty_like(x)
+    _load().orc_scan_max_f32(x.size, _ptr(x), _ptr(out))
+    return out
 
 
 def exact_sum_f64(t):

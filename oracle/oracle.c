@@ -237,6 +237,42 @@ void orc_argmax_f32(int64_t n, const float* x, float* v, int64_t* idx) {
   *idx = bi;
 }
 
+/* ------------------------------------------------------------ scans */
+
+/* Parallel prefix sums (Sec. 3.2.6) with scan expression a+b over binary32
+ * values: incl[i] = x[0] + ... + x[i] accumulated in binary64 (compensated,
+ * as orc_sum_f32), abs_prefix[i] = |x[0]| + ... + |x[i]| for error bounds. */
+void orc_scan_sum_f32(int64_t n, const float* x, double* incl, double* abs_prefix) {
+  double s = 0.0, c = 0.0, as = 0.0, ac = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    neumaier_add(&s, &c, (double)x[i]);
+    neumaier_add(&as, &ac, fabs((double)x[i]));
+    incl[i] = s + c;
+    if (abs_prefix) abs_prefix[i] = as + ac;
+  }
+}
+
+/* Prefix sums of int32 values into int64 with two's-complement wrap-around:
+ * inclusive (out[i] = x[0] + ... + x[i]) or exclusive (out[i] = x[0] + ... +
+ * x[i-1], out[0] = 0, the neutral element). */
+void orc_scan_sum_i32_i64(int64_t n, const int32_t* x, int exclusive, int64_t* out) {
+  uint64_t s = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (exclusive) out[i] = (int64_t)s;
+    s += (uint64_t)(int64_t)x[i];
+    if (!exclusive) out[i] = (int64_t)s;
+  }
+}
+
+/* Running maximum from the neutral element -inf (scan expression a > b ? a : b). */
+void orc_scan_max_f32(int64_t n, const float* x, float* out) {
+  float m = -INFINITY;
+  for (int64_t i = 0; i < n; ++i) {
+    if (x[i] > m) m = x[i];
+    out[i] = m;
+  }
+}
+
 /* ------------------------------------------------------- superaccumulator */
 
 /* Exact sum of binary64 values.  The accumulator is a signed fixed-point

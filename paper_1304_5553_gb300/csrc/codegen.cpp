@@ -544,7 +544,7 @@ __device__ __forceinline__ void pyc_map_batched_body(const pyc_mtask* __restrict
 ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind kind,
                           const std::string& neutral, const std::string& reduce_expr,
                           const std::string& map_expr, const std::string& preamble,
-                          const std::string& tag, int ordered_arg) {
+                          const std::string& tag, int ordered_arg, bool emit_kernels) {
   ReduceGen g;
   const int mins = lifted_min_bytes(spec);
   std::string acc_t, out_t;
@@ -876,6 +876,7 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
 
 )PYC";
   for (auto& v : all_variants()) {
+    if (!emit_kernels) break;
     std::string sfx = variant_suffix(v);
     o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_reduce_" << tag << "_" << sfx
       << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
@@ -887,6 +888,214 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
          "unsigned* tickets, unsigned* ctl) {\n"
       << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll
       << ">(tasks, items, nitems, part, tickets, ctl);\n}\n";
+  }
+  g.source = o.str();
+  return g;
+}
+
+ScanGen generate_scan(const ArgSpec& spec, pyc_dtype dtype, const std::string& neutral,
+                      const std::string& scan_expr, const std::string& input_expr,
+                      const std::string& output_stmt, const std::string& preamble,
+                      const std::string& tag) {
+  ReduceGen core = generate_reduce(spec, dtype, ReduceKind::Plain, neutral, scan_expr, input_expr,
+                                   preamble, tag, 0, false);
+  ScanGen g;
+  g.acc_bytes = core.acc_bytes;
+  std::ostringstream o;
+  o << core.source;
+  o << R"PYC(
+// ------------------------------------------------------------------ scan
+template <typename T>
+__device__ __forceinline__ T pyc_shfl_up(const T v, int d) {
+  pyc_words<T> u;
+  u.t = v;
+#pragma unroll
+  for (int j = 0; j < (int)(sizeof(T) / 4); ++j) u.w[j] = __shfl_up_sync(0xffffffffu, u.w[j], d);
+  return u.t;
+}
+// Inclusive scan across a warp in lane order (the earlier operand on the left).
+__device__ __forceinline__ pyc_acc_t pyc_warp_incl_scan(pyc_acc_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const pyc_acc_t o = pyc_shfl_up(v, d);
+    if (lane >= d) v = pyc_combine(o, v);
+  }
+  return v;
+}
+// Exclusive scan across the block in thread order; *total = the block's total.
+__device__ __forceinline__ pyc_acc_t pyc_block_excl_scan(const pyc_acc_t v, pyc_acc_t* total) {
+  __shared__ pyc_acc_t pyc_ws[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const pyc_acc_t incl = pyc_warp_incl_scan(v);
+  __syncthreads();  // pyc_ws may still be read from the previous call
+  if (lane == 31) pyc_ws[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    pyc_acc_t s = lane < nw ? pyc_ws[lane] : pyc_neutral();
+    s = pyc_warp_incl_scan(s);
+    pyc_ws[lane] = s;
+  }
+  __syncthreads();
+  pyc_acc_t ex = pyc_shfl_up(incl, 1);
+  if (lane == 0) ex = pyc_neutral();
+  *total = pyc_ws[nw - 1];
+  return w > 0 ? pyc_combine(pyc_ws[w - 1], ex) : ex;
+}
+
+// Pass 1: chunk totals (the reduction core), then the last CTA to finish
+// replaces them by exclusive carries: carry[c] = total[0] + ... + total[c-1].
+template <int VB, int U>
+__device__ __forceinline__ void pyc_scan_pass1(const pyc_args& pyc_p, const pyc_i64 n,
+    const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 nchunks,
+    pyc_acc_t* __restrict__ part, unsigned* __restrict__ ticket) {
+  __shared__ unsigned pyc_last;
+  for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    pyc_acc_t v = pyc_chunk<VB, U>(pyc_p, n, head, chunk, c, threadIdx.x, blockDim.x);
+    v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
+    if (threadIdx.x == 0) part[c] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) pyc_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!pyc_last) return;
+  __threadfence();
+  // each thread owns a contiguous run of totals
+  const int cnt = (int)nchunks;
+  const int per = (cnt + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int lo = (int)threadIdx.x * per;
+  const int hi = lo + per < cnt ? lo + per : cnt;
+  pyc_acc_t mine = pyc_neutral();
+  for (int j = lo; j < hi; ++j) mine = pyc_combine(mine, pyc_ld_cg(part + j));
+  pyc_acc_t tot;
+  pyc_acc_t run = pyc_block_excl_scan(mine, &tot);
+  for (int j = lo; j < hi; ++j) {
+    const pyc_acc_t t = pyc_ld_cg(part + j);
+    part[j] = run;
+    run = pyc_combine(run, t);
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// Pass 2: chunk c in index order -- the scalar head (chunk 0 only), the full
+// tiles, the scalar tail -- with a running carry that starts at carry[c].
+template <int VB, int U>
+__device__ __forceinline__ void pyc_scan_chunk(const pyc_args& pyc_p, const pyc_i64 n,
+    const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 c, pyc_acc_t pyc_carry) {
+  constexpr int E = VB / PYC_MIN_BYTES;
+  constexpr int T = E * U;
+)PYC";
+  o << aliases(spec, "pyc_p");
+  o << R"PYC(  (void)n;
+  const pyc_i64 pyc_step = (pyc_i64)blockDim.x * E;
+  const pyc_i64 pyc_tile = pyc_step * U;
+  pyc_i64 pyc_vs = 0, pyc_ve = 0, pyc_ss, pyc_se;
+  if (head >= 0) {
+    pyc_vs = head + c * chunk;
+    pyc_ve = pyc_vs + chunk < n ? pyc_vs + chunk : n;
+    pyc_ss = 0;
+    pyc_se = c == 0 ? head : 0;
+  } else {
+    pyc_ss = c * chunk;
+    pyc_se = pyc_ss + chunk < n ? pyc_ss + chunk : n;
+  }
+  const pyc_i64 pyc_nt = pyc_ve > pyc_vs ? (pyc_ve - pyc_vs) / pyc_tile : 0;
+  const pyc_i64 pyc_r0 = pyc_vs + pyc_nt * pyc_tile;
+  for (int pyc_part = 0; pyc_part < 3; ++pyc_part) {
+    if (pyc_part == 1) {
+      for (pyc_i64 pyc_t = 0; pyc_t < pyc_nt; ++pyc_t) {
+        const pyc_i64 pyc_b0 = pyc_vs + pyc_t * pyc_tile + (pyc_i64)threadIdx.x * E;
+)PYC";
+  o << reg_decls(spec, "T");
+  o << R"PYC(#pragma unroll
+        for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
+          const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+)PYC";
+  o << group_io(spec, true);
+  o << R"PYC(        }
+#pragma unroll
+        for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
+          pyc_acc_t pyc_l[E];
+#pragma unroll
+          for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
+            const int pyc_k = pyc_u * E + pyc_e;
+            const pyc_i64 i = pyc_b0 + (pyc_i64)pyc_u * pyc_step + pyc_e;
+            (void)i;
+            (void)pyc_k;
+            const pyc_acc_t pyc_v = (pyc_acc_t)()PYC" << input_expr << R"PYC();
+            pyc_l[pyc_e] = pyc_e == 0 ? pyc_v : pyc_combine(pyc_l[pyc_e - 1], pyc_v);
+          }
+          pyc_acc_t pyc_rowtot;
+          const pyc_acc_t pyc_ex = pyc_block_excl_scan(pyc_l[E - 1], &pyc_rowtot);
+          const pyc_acc_t pyc_pre = pyc_combine(pyc_carry, pyc_ex);
+#pragma unroll
+          for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
+            const int pyc_k = pyc_u * E + pyc_e;
+            const pyc_i64 i = pyc_b0 + (pyc_i64)pyc_u * pyc_step + pyc_e;
+            (void)i;
+            (void)pyc_k;
+            const pyc_acc_t item = pyc_combine(pyc_pre, pyc_l[pyc_e]);
+            const pyc_acc_t prev_item = pyc_e == 0 ? pyc_pre : pyc_combine(pyc_pre, pyc_l[pyc_e - 1]);
+            (void)item;
+            (void)prev_item;
+            { )PYC" << output_stmt << R"PYC( ; }
+          }
+          pyc_carry = pyc_combine(pyc_carry, pyc_rowtot);
+        }
+#pragma unroll
+        for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
+          const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+)PYC";
+  o << group_io(spec, false);
+  o << R"PYC(        }
+      }
+      continue;
+    }
+    // scalar ranges: the head before the tiles, the tail after them, in rounds
+    // of blockDim.x consecutive elements
+    const pyc_i64 pyc_rs = pyc_part == 0 ? pyc_ss : pyc_r0;
+    const pyc_i64 pyc_re = pyc_part == 0 ? pyc_se : (pyc_ve > pyc_r0 ? pyc_ve : pyc_r0);
+    for (pyc_i64 pyc_base = pyc_rs; pyc_base < pyc_re; pyc_base += blockDim.x) {
+      const pyc_i64 i = pyc_base + threadIdx.x;
+      const bool pyc_valid = i < pyc_re;
+)PYC";
+  o << reg_decls(spec, "1");
+  o << "      if (pyc_valid) {\n" << scalar_io(spec, true) << "      }\n";
+  o << R"PYC(      const int pyc_k = 0;
+      (void)pyc_k;
+      pyc_acc_t pyc_v = pyc_neutral();
+      if (pyc_valid) pyc_v = (pyc_acc_t)()PYC" << input_expr << R"PYC();
+      pyc_acc_t pyc_tot;
+      const pyc_acc_t pyc_ex = pyc_block_excl_scan(pyc_v, &pyc_tot);
+      if (pyc_valid) {
+        const pyc_acc_t prev_item = pyc_combine(pyc_carry, pyc_ex);
+        const pyc_acc_t item = pyc_combine(prev_item, pyc_v);
+        (void)item;
+        (void)prev_item;
+        { )PYC" << output_stmt << R"PYC( ; }
+)PYC";
+  o << scalar_io(spec, false);
+  o << R"PYC(      }
+      pyc_carry = pyc_combine(pyc_carry, pyc_tot);
+    }
+  }
+}
+
+)PYC";
+  for (auto& v : all_variants()) {
+    std::string sfx = variant_suffix(v);
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_scan1_" << tag << "_" << sfx
+      << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
+         "const pyc_i64 nchunks, pyc_acc_t* part, unsigned* ticket) {\n"
+      << "  pyc_scan_pass1<" << v.vec_bytes << ", " << v.unroll
+      << ">(pyc_p, n, head, chunk, nchunks, part, ticket);\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_scan2_" << tag << "_" << sfx
+      << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
+         "const pyc_i64 nchunks, const pyc_acc_t* carry) {\n"
+      << "  for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x)\n"
+      << "    pyc_scan_chunk<" << v.vec_bytes << ", " << v.unroll
+      << ">(pyc_p, n, head, chunk, c, carry[c]);\n}\n";
   }
   g.source = o.str();
   return g;

@@ -53,10 +53,24 @@ struct ReduceGen {
 
 // ordered_arg: 0, or for the built-in argmin (1) / argmax (2) rule a cheaper
 // fold for the vector body, where each accumulator sees increasing indices.
+// emit_kernels = false leaves out the entry points (the scan reuses the core).
 ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind kind,
                           const std::string& neutral, const std::string& reduce_expr,
                           const std::string& map_rewritten, const std::string& preamble,
-                          const std::string& tag, int ordered_arg = 0);
+                          const std::string& tag, int ordered_arg = 0, bool emit_kernels = true);
+
+// Parallel prefix scan (Sec. 3.2.6): the reduction core for pass 1 (chunk
+// totals; the last CTA turns them into exclusive carries) plus pass 2 (each
+// chunk scanned from its carry, the output statement run per element with
+// `item` = inclusive and `prev_item` = exclusive prefix).
+struct ScanGen {
+  std::string source;
+  int acc_bytes = 0;
+};
+ScanGen generate_scan(const ArgSpec& spec, pyc_dtype dtype, const std::string& neutral,
+                      const std::string& scan_expr, const std::string& input_rewritten,
+                      const std::string& output_rewritten, const std::string& preamble,
+                      const std::string& tag);
 
 // Device-side spelling of a dtype (pyc_bf16 for BF16, ...).
 std::string device_type(pyc_dtype t);

@@ -5,6 +5,7 @@
 
 #include <cuda.h>
 
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -126,6 +127,13 @@ void launch_reduce(pyc_reduce* h, const LaunchCfg& cfg, int64_t n, void* const* 
 // Enqueue one map.
 void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
                 const void* scalars, CUstream stream);
+
+// Times every (variant, block) candidate of a handle with `launch_one` on
+// scratch buffers for n's size bucket and keeps the fastest (tune.cpp).
+using TuneLaunch = std::function<void(const LaunchCfg&, int64_t, void* const*, const void*,
+                                      CUdeviceptr)>;
+void autotune_generic(HandleBase& h, int64_t n, CUstream stream, bool reduce,
+                      const TuneLaunch& launch_one);
 
 // Persistent tuning cache (JSON lines in the kernel cache directory).
 void tune_cache_load(HandleBase& h, bool reduce);

@@ -293,38 +293,42 @@ ArgSpec parse_argspec(const std::string& text) {
   return spec;
 }
 
-std::string analyze_and_rewrite(ArgSpec& spec, const std::string& code, bool expression) {
+namespace {
+
+bool is_member_at(const std::vector<Token>& t, size_t j) {
+  return j > 0 && t[j - 1].kind == Token::Punct &&
+         (t[j - 1].text == "." || t[j - 1].text == "->" || t[j - 1].text == "::");
+}
+
+bool is_index_i_at(const std::vector<Token>& t, size_t j) {
+  return j + 3 < t.size() && t[j + 1].text == "[" && t[j + 2].text == "i" &&
+         t[j + 2].kind == Token::Ident && t[j + 3].text == "]";
+}
+
+Param* find_array(ArgSpec& spec, const std::string& name) {
+  for (auto& p : spec.params)
+    if (p.is_ptr && p.name == name) return &p;
+  return nullptr;
+}
+
+}  // namespace
+
+void analyze_code(ArgSpec& spec, const std::string& code, bool expression) {
   const char* what = expression ? "map expression" : "statement";
   std::vector<Token> t = tokenize(code);
   check_balanced(t, what);
   check_forbidden(t, what);
-  auto find_param = [&](const std::string& name) -> Param* {
-    for (auto& p : spec.params)
-      if (p.is_ptr && p.name == name) return &p;
-    return nullptr;
-  };
-  auto is_member = [&](size_t j) {
-    return j > 0 && t[j - 1].kind == Token::Punct &&
-           (t[j - 1].text == "." || t[j - 1].text == "->" || t[j - 1].text == "::");
-  };
-  auto is_index_i = [&](size_t j) {
-    return j + 3 < t.size() && t[j + 1].text == "[" && t[j + 2].text == "i" &&
-           t[j + 2].kind == Token::Ident && t[j + 3].text == "]";
-  };
-  // Pass 1: which arrays can be lifted, and how they are used.
-  std::vector<bool> raw(spec.params.size(), false), fully_written(spec.params.size(), false);
   int depth = 0;
   for (size_t j = 0; j < t.size(); ++j) {
     const Token& k = t[j];
     if (k.kind == Token::Punct && (k.text == "(" || k.text == "[" || k.text == "{")) ++depth;
     if (k.kind == Token::Punct && (k.text == ")" || k.text == "]" || k.text == "}")) --depth;
-    if (k.kind != Token::Ident || is_member(j)) continue;
-    Param* p = find_param(k.text);
+    if (k.kind != Token::Ident || is_member_at(t, j)) continue;
+    Param* p = find_array(spec, k.text);
     if (!p) continue;
-    size_t idx = p - spec.params.data();
     p->used = true;
-    if (!is_index_i(j)) {
-      raw[idx] = true;
+    if (!is_index_i_at(t, j)) {
+      p->raw = true;
       p->read = true;
       if (!expression) p->written = true;  // unknown use: assume both
       continue;
@@ -340,7 +344,7 @@ std::string analyze_and_rewrite(ArgSpec& spec, const std::string& code, bool exp
         unary = !operand;
       }
       if (unary) {
-        raw[idx] = true;
+        p->raw = true;
         p->read = true;
         if (!expression) p->written = true;
         continue;
@@ -351,7 +355,7 @@ std::string analyze_and_rewrite(ArgSpec& spec, const std::string& code, bool exp
     bool incdec = next == "++" || next == "--" || prev == "++" || prev == "--";
     if (is_assign_op(next) || incdec) {
       if (expression) {
-        raw[idx] = true;  // side effects in a map expression: leave it to the compiler
+        p->raw = true;  // side effects in a map expression: leave it to the compiler
         p->read = p->written = true;
         continue;
       }
@@ -360,25 +364,27 @@ std::string analyze_and_rewrite(ArgSpec& spec, const std::string& code, bool exp
       // a plain assignment that starts a top-level statement writes every element
       bool top = depth == 0 && next == "=" && !incdec &&
                  (j == 0 || t[j - 1].text == ";" || t[j - 1].text == "}");
-      if (top) fully_written[idx] = true;
+      if (top) p->fully_written = true;
     } else {
       p->read = true;
     }
   }
-  for (size_t idx = 0; idx < spec.params.size(); ++idx) {
-    Param& p = spec.params[idx];
+  for (auto& p : spec.params) {
     if (!p.is_ptr || !p.used) continue;
-    p.lifted = !raw[idx];
+    p.lifted = !p.raw;
     // an element the code may leave unwritten must be stored back unchanged
-    if (p.lifted && p.written && !fully_written[idx]) p.read = true;
+    if (p.lifted && p.written && !p.fully_written) p.read = true;
   }
-  // Pass 2: rewrite lifted accesses.
+}
+
+std::string rewrite_lifted(ArgSpec& spec, const std::string& code) {
+  std::vector<Token> t = tokenize(code);
   std::vector<Token> o;
   for (size_t j = 0; j < t.size(); ++j) {
     const Token& k = t[j];
-    if (k.kind == Token::Ident && !is_member(j)) {
-      Param* p = find_param(k.text);
-      if (p && p->lifted && is_index_i(j)) {
+    if (k.kind == Token::Ident && !is_member_at(t, j)) {
+      Param* p = find_array(spec, k.text);
+      if (p && p->lifted && is_index_i_at(t, j)) {
         o.push_back({Token::Ident, "pyc_r_" + p->name});
         o.push_back({Token::Punct, "["});
         o.push_back({Token::Ident, "pyc_k"});
@@ -390,6 +396,11 @@ std::string analyze_and_rewrite(ArgSpec& spec, const std::string& code, bool exp
     o.push_back(k);
   }
   return join_tokens(o);
+}
+
+std::string analyze_and_rewrite(ArgSpec& spec, const std::string& code, bool expression) {
+  analyze_code(spec, code, expression);
+  return rewrite_lifted(spec, code);
 }
 
 std::string check_expression(const std::string& code, const char* what) {

@@ -33,6 +33,8 @@ struct Param {
   bool read = false;
   bool written = false;
   bool lifted = false;
+  bool raw = false;            // used other than as name[i] somewhere
+  bool fully_written = false;  // some top-level statement assigns name[i] unconditionally
 };
 
 struct ArgSpec {
@@ -62,6 +64,11 @@ std::vector<Token> tokenize(const std::string& code);
 // a map-reduce map expression (writes make an array raw).  Throws
 // Error(PYC_E_PARSE) on unbalanced brackets or forbidden constructs.
 std::string analyze_and_rewrite(ArgSpec& spec, const std::string& code, bool expression);
+
+// The two halves of analyze_and_rewrite, for specs with several pieces of code
+// (analyse every piece first, then rewrite each with the final flags).
+void analyze_code(ArgSpec& spec, const std::string& code, bool expression);
+std::string rewrite_lifted(ArgSpec& spec, const std::string& code);
 
 // Checks an expression that may only use the given formal names (a, b for
 // reduce expressions); returns it re-joined from tokens.

@@ -131,6 +131,11 @@ void autotune(H* h, int64_t n, CUstream stream, bool reduce, Launch&& launch_one
 
 }  // namespace
 
+void autotune_generic(HandleBase& h, int64_t n, CUstream stream, bool reduce,
+                      const TuneLaunch& launch_one) {
+  autotune(&h, n, stream, reduce, launch_one);
+}
+
 void tune_cache_load(HandleBase& h, bool reduce) {
   std::string path = tune_path();
   if (path.empty()) return;

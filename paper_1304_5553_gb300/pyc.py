@@ -97,6 +97,8 @@ EXPORTED = [
     "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
     "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay", "pyc_map_launch_host",
     "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
+    "pyc_scan_create", "pyc_scan_launch", "pyc_scan_num_params", "pyc_scan_param",
+    "pyc_scan_scalar_bytes", "pyc_scan_source", "pyc_scan_autotune", "pyc_scan_config", "pyc_scan_destroy",
 ]
 
 _lib = None
@@ -128,6 +130,7 @@ def load(build_if_missing=True):
         "pyc_map_launch_host": (st, [vp, i64, ctypes.POINTER(vp), vp]),
         "pyc_map_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_reduce_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
+        "pyc_scan_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_map_num_params": (i32, [vp]),
         "pyc_map_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
         "pyc_map_scalar_bytes": (i32, [vp]),
@@ -140,6 +143,15 @@ def load(build_if_missing=True):
         "pyc_reduce_batched": (st, [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(vp), vp, vp,
                                     vp]),
         "pyc_reduce_launch_static": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, vp]),
+        "pyc_scan_create": (st, [i32, cp, cp, cp, cp, cp, ctypes.POINTER(pyc_opts),
+                                 ctypes.POINTER(vp)]),
+        "pyc_scan_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp]),
+        "pyc_scan_num_params": (i32, [vp]),
+        "pyc_scan_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
+        "pyc_scan_scalar_bytes": (i32, [vp]),
+        "pyc_scan_source": (cp, [vp]),
+        "pyc_scan_autotune": (st, [vp, i64, vp]),
+        "pyc_scan_destroy": (None, [vp]),
         "pyc_reduce_batched_autotune": (st, [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(vp), vp,
                                              vp, vp]),
         "pyc_reduce_num_params": (i32, [vp]),
@@ -266,6 +278,29 @@ def pyc_reduce_batched(h, nseg, seg_offsets, ptrs, scalars, d_out, stream=None):
                                      _ptr_array(ptrs), scalars, d_out, _stream(stream)))
 
 
+def pyc_scan_create(dtype, neutral, scan_expr, input_expr, output_stmt, argspec, opts=None):
+    h = ctypes.c_void_p()
+    _check(load().pyc_scan_create(int(dtype), _enc(neutral), _enc(scan_expr), _enc(input_expr),
+                                  _enc(output_stmt), _enc(argspec), _opts(opts), ctypes.byref(h)))
+    return h
+
+
+def pyc_scan_launch(h, n, ptrs, scalars=None, stream=None):
+    _check(load().pyc_scan_launch(h, int(n), _ptr_array(ptrs), scalars, _stream(stream)))
+
+
+def pyc_scan_autotune(h, n, stream=None):
+    _check(load().pyc_scan_autotune(h, int(n), _stream(stream)))
+
+
+def pyc_scan_source(h) -> str:
+    return load().pyc_scan_source(h).decode()
+
+
+def pyc_scan_destroy(h):
+    load().pyc_scan_destroy(h)
+
+
 def pyc_reduce_batched_autotune(h, nseg, seg_offsets, ptrs, scalars, d_out, stream=None):
     import numpy as np
     off = np.ascontiguousarray(seg_offsets, dtype=np.int64)
@@ -295,7 +330,7 @@ def pyc_reduce_autotune(h, n, stream=None):
 def launch_config(h, n, reduce=False):
     """(vec_bytes, unroll, block) a launch of n elements would use."""
     v, u, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    fn = load().pyc_reduce_config if reduce else load().pyc_map_config
+    fn = getattr(load(), "pyc_%s_config" % _kind(reduce))
     _check(fn(h, int(n), ctypes.byref(v), ctypes.byref(u), ctypes.byref(b)))
     return v.value, u.value, b.value
 
@@ -306,11 +341,18 @@ def pyc_cache_stats():
     return {"compiled": a.value, "disk_hits": b.value, "mem_hits": c.value}
 
 
+def _kind(reduce):
+    """'map', 'reduce' or 'scan' from the `reduce` argument (False, True or 'scan')."""
+    return "scan" if reduce == "scan" else ("reduce" if reduce else "map")
+
+
 def params(h, reduce=False):
-    """Declared parameters as dicts (name, is_pointer, dtype, ... )."""
+    """Declared parameters as dicts (name, is_pointer, dtype, ... ); reduce is
+    False (map), True (map-reduce) or 'scan'."""
     lib = load()
-    num = (lib.pyc_reduce_num_params if reduce else lib.pyc_map_num_params)(h)
-    get = lib.pyc_reduce_param if reduce else lib.pyc_map_param
+    k = _kind(reduce)
+    num = getattr(lib, "pyc_%s_num_params" % k)(h)
+    get = getattr(lib, "pyc_%s_param" % k)
     out = []
     for k in range(num):
         info = pyc_param_info()
@@ -324,7 +366,7 @@ def pack_scalars(h, values, reduce=False):
     """Pack scalar values in declaration order into the layout the handle expects
     (Python ints/floats are converted to the declared C type, as in Listing 3a)."""
     lib = load()
-    size = (lib.pyc_reduce_scalar_bytes if reduce else lib.pyc_map_scalar_bytes)(h)
+    size = getattr(lib, "pyc_%s_scalar_bytes" % _kind(reduce))(h)
     buf = ctypes.create_string_buffer(max(size, 1))
     scal = [p for p in params(h, reduce) if not p["is_pointer"]]
     if len(scal) != len(values):

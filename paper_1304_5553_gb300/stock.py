@@ -42,6 +42,15 @@ REDUCES = {
     "argmax_f32": (pyc.PYC_ARGMAX_F32, None, None, "x[i]", "float *x", {}),
 }
 
+# name: (value dtype, neutral, scan expression, input expression, output statement, argspec)
+SCANS = {
+    "cumsum_f32": (pyc.PYC_F32, "0", "a+b", "x[i]", "y[i] = item", "float *x, float *y"),
+    "cumsum_excl_i32_i64": (pyc.PYC_I64, "0", "a+b", "(long long)x[i]", "y[i] = prev_item",
+                            "int *x, long long *y"),
+    "cummax_f32": (pyc.PYC_F32, "-INFINITY", "a > b ? a : b", "x[i]", "y[i] = item",
+                   "float *x, float *y"),
+}
+
 _handles = {}
 _lock = threading.Lock()
 
@@ -55,6 +64,9 @@ def create(name, **opts):
     if name in MAPS:
         spec, stmt = MAPS[name]
         h = pyc.pyc_map_create(spec, stmt, name, opts or None)
+    elif name in SCANS:
+        dt, neu, red, inp, out, spec = SCANS[name]
+        h = pyc.pyc_scan_create(dt, neu, red, inp, out, spec, opts or None)
     else:
         dt, neu, red, mexpr, spec, o = REDUCES[name]
         o = dict(o, **opts)
@@ -67,7 +79,7 @@ def create(name, **opts):
 def compile_all(names=None, threads=8):
     """Create (and so compile or load from cache) the stock specs in parallel:
     NVRTC runs outside the GIL, one program per thread."""
-    names = list(names or (list(MAPS) + list(REDUCES)))
+    names = list(names or (list(MAPS) + list(REDUCES) + list(SCANS)))
     with ThreadPoolExecutor(max_workers=threads) as ex:
         list(ex.map(create, names))
     return names

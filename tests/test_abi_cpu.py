@@ -218,3 +218,22 @@ def test_server_config_validation():
         with pytest.raises(pyc.PycError) as e:
             pyc.pyc_server_create(**bad)
         assert e.value.status == pyc.PYC_E_ARG
+
+
+def test_scan_create_validation():
+    h = pyc.pyc_scan_create(pyc.PYC_F32, "0", "a+b", "x[i]", "y[i] = item", "float *x, float *y")
+    p = {q["name"]: q for q in pyc.params(h, "scan")}
+    assert p["x"]["lifted"] and p["x"]["read"] and not p["x"]["written"]
+    assert p["y"]["lifted"] and p["y"]["written"] and not p["y"]["read"]
+    src = pyc.pyc_scan_source(h)
+    assert "pyc_scan1_s" in src and "pyc_scan2_s" in src
+    pyc.pyc_scan_destroy(h)
+    bad = [
+        (pyc.PYC_BF16, "0", "a+b", "x[i]", "y[i] = item", "float *x, float *y"),
+        (pyc.PYC_F32, "0", "a+b", "x[i]", "y[i] = item", "float *x, float *item"),
+        (pyc.PYC_F32, "0", "a+b; }", "x[i]", "y[i] = item", "float *x, float *y"),
+    ]
+    for args in bad:
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_scan_create(*args)
+        assert e.value.status in (pyc.PYC_E_ARG, pyc.PYC_E_PARSE)

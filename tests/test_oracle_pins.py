@@ -329,3 +329,44 @@ def test_argmin_recipe_first_chosen_index():
     pos = inputs.index_sample(15, 1, n // 100, n)
     v, i = oracle.argmin_f32(x)
     assert v == np.float32(-2.5) and i == int(pos.min())
+
+
+# ----------------------------------------------------------------- scans (Sec. 3.2.6)
+
+def test_scan_sum_against_library_and_exact():
+    rng = np.random.default_rng(20)
+    xi = rng.integers(-1000, 1000, 5000).astype(np.float32)  # exact in binary64
+    incl, ab = oracle.scan_sum_f32(xi)
+    assert np.array_equal(incl, np.cumsum(xi.astype(np.int64)).astype(np.float64))
+    assert np.array_equal(ab, np.cumsum(np.abs(xi.astype(np.int64))).astype(np.float64))
+    x = (rng.standard_normal(600) * np.exp(3 * rng.standard_normal(600))).astype(np.float32)
+    incl, ab = oracle.scan_sum_f32(x)
+    run = Fraction(0)
+    for i in range(x.size):
+        run += Fraction(float(x[i]))
+        assert abs(Fraction(incl[i]) - run) <= Fraction(abs(float(run))) / 2 ** 52 + \
+            (i + 1) * Fraction(ab[i]) / 2 ** 100
+    # the last prefix is the reduction
+    assert incl[-1] == oracle.sum_f32(x)[0]
+    # a prefix that cancels a term 2^100 times larger: exact only with the compensation
+    incl, ab = oracle.scan_sum_f32(np.array([2.0 ** 100, 1.0, -2.0 ** 100, 0.5], np.float32))
+    assert list(incl) == [2.0 ** 100, 2.0 ** 100, 1.0, 1.5]
+    assert list(ab) == [2.0 ** 100, 2.0 ** 100, 2.0 ** 101, 2.0 ** 101]
+    assert oracle.scan_sum_f32(np.zeros(0, np.float32))[0].size == 0
+
+
+def test_scan_int_inclusive_exclusive():
+    x = inputs.int_uniform_i32(21, 0, 10000)
+    inc = oracle.scan_sum_i32_i64(x)
+    exc = oracle.scan_sum_i32_i64(x, exclusive=True)
+    assert np.array_equal(inc, np.cumsum(x.astype(np.int64)))
+    assert exc[0] == 0 and np.array_equal(exc[1:], inc[:-1])
+    n = 3000
+    assert np.array_equal(oracle.scan_sum_i32_i64(np.arange(n, dtype=np.int32)),
+                          np.arange(n, dtype=np.int64) * (np.arange(n) + 1) // 2)
+
+
+def test_scan_max_against_library():
+    x = np.random.default_rng(22).standard_normal(4000).astype(np.float32)
+    assert np.array_equal(oracle.scan_max_f32(x), np.maximum.accumulate(x))
+    assert oracle.scan_max_f32(np.array([np.float32(-np.inf)]))[0] == -np.inf
