@@ -297,11 +297,32 @@ pyc_status pyc_scan_create(pyc_dtype dtype, const char* neutral, const char* sca
                            const char* input_expr, const char* output_stmt, const char* argspec,
                            const pyc_opts* opts, pyc_scan_t* out);
 
-/* Scan over i in [0, n): two launches on `stream` (chunk totals and carries,
- * then the chunk scans with the output statement); no host round trip.  The
- * handle keeps one workspace per (context, stream).  n == 0 is a no-op. */
+/* Scan over i in [0, n): one launch on `stream`, no host round trip.  Tiles
+ * of the index range are handed to CTAs in order; each tile finds its
+ * exclusive prefix by looking back at the descriptors that earlier tiles
+ * publish in the handle's workspace (one per (context, stream), grown on
+ * demand; growing it synchronizes `stream`).  Each of those waits is bounded
+ * (about a second of polling); if one runs out the launch still completes,
+ * its output is not valid, and pyc_scan_sync reports PYC_E_TIMEOUT.  Aliasing
+ * as for maps: output_stmt may write the array input_expr reads at the same
+ * index (an in-place scan).  n == 0 is a no-op. */
 pyc_status pyc_scan_launch(pyc_scan_t h, int64_t n, void* const* ptrs, const void* scalars,
                            pyc_stream_t stream);
+/* Debugging aid: with the environment variable PYC_CHECK_BOUNDS=1 set when a
+ * scan is created, its kernel checks every array and descriptor index and
+ * records the first out-of-range one instead of accessing it; pyc_scan_sync
+ * then fails with PYC_E_INTERNAL naming the index, tile and thread. */
+/* Synchronizes `stream` and reports whether any scan launch of this handle on
+ * it gave up a wait since the last call: PYC_OK, or PYC_E_TIMEOUT (the error
+ * is then cleared and the workspace made ready for the next launch; launches
+ * between the failing one and this call may have produced invalid output). */
+pyc_status pyc_scan_sync(pyc_scan_t h, pyc_stream_t stream);
+/* Test hook (the paper has no counterpart): pyc_scan_launch in which tile
+ * `stall_tile` publishes no descriptor and every wait gives up after
+ * `spin_limit` polls, so that the error path can be exercised without a fault.
+ * stall_tile = -1 and spin_limit = 1 << 20 is pyc_scan_launch. */
+pyc_status pyc_scan_launch_test(pyc_scan_t h, int64_t n, void* const* ptrs, const void* scalars,
+                                pyc_stream_t stream, int64_t stall_tile, int64_t spin_limit);
 int pyc_scan_num_params(pyc_scan_t h);
 pyc_status pyc_scan_param(pyc_scan_t h, int idx, pyc_param_info* info);
 int pyc_scan_scalar_bytes(pyc_scan_t h);

@@ -75,6 +75,7 @@ def _load():
             "orc_scan_sum_f32": (None, [i64, vp, vp, vp]),
             "orc_scan_sum_i32_i64": (None, [i64, vp, ctypes.c_int, vp]),
             "orc_scan_max_f32": (None, [i64, vp, vp]),
+            "orc_scan_affine_u32": (None, [i64, vp, vp, vp]),
             "orc_exact_sum_f64": (f64, [i64, vp]),
             "orc_exact_dot_f32": (f64, [i64, vp, vp]),
             "orc_exact_sum_f32": (f64, [i64, vp]),
@@ -257,6 +258,16 @@ def scan_max_f32(x):
     x = _f32(x)
     out = np.empty_like(x)
     _load().orc_scan_max_f32(x.size, _ptr(x), _ptr(out))
+    return out
+
+
+def scan_affine_u32(a, b):
+    """Prefix compositions of v -> a[k] v + b[k] mod 2^32, packed A << 32 | B."""
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    b = np.ascontiguousarray(b, dtype=np.uint32)
+    assert a.size == b.size
+    out = np.empty(a.size, np.uint64)
+    _load().orc_scan_affine_u32(a.size, _ptr(a), _ptr(b), _ptr(out))
     return out
 
 

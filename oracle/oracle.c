@@ -273,6 +273,19 @@ void orc_scan_max_f32(int64_t n, const float* x, float* out) {
   }
 }
 
+/* A scan whose operator does not commute: composition of the affine maps
+ * f_k(v) = a[k] v + b[k] (mod 2^32), applied in index order.  The prefix up to
+ * i is the map v -> A_i v + B_i with A_i = A_{i-1} a[i], B_i = a[i] B_{i-1} +
+ * b[i] (A_{-1} = 1, B_{-1} = 0: the identity map), stored as A_i << 32 | B_i. */
+void orc_scan_affine_u32(int64_t n, const uint32_t* a, const uint32_t* b, uint64_t* out) {
+  uint32_t A = 1u, B = 0u;
+  for (int64_t i = 0; i < n; ++i) {
+    A = A * a[i];
+    B = a[i] * B + b[i];
+    out[i] = ((uint64_t)A << 32) | B;
+  }
+}
+
 /* ------------------------------------------------------- superaccumulator */
 
 /* Exact sum of binary64 values.  The accumulator is a signed fixed-point

@@ -2,6 +2,9 @@
 #include <algorithm>
 #include <cctype>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "cudrv.h"
 #include "handles.h"
@@ -84,20 +87,21 @@ int64_t vector_head(const ArgSpec& spec, void* const* ptrs, int vec_bytes, int m
   return -1;
 }
 
-int resident_ctas(CUfunction f, int block) {
+int resident_ctas(CUfunction f, int block, int dyn_smem) {
   static std::mutex mu;
-  static std::map<std::pair<CUfunction, int>, int> cache;
+  static std::map<std::tuple<CUfunction, int, int>, int> cache;
+  const auto key = std::make_tuple(f, block, dyn_smem);
   {
     std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find({f, block});
+    auto it = cache.find(key);
     if (it != cache.end()) return it->second;
   }
   int nb = 0;
-  PYC_CU(drv().cuOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, 0));
+  PYC_CU(drv().cuOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, (size_t)dyn_smem));
   if (nb < 1) fail(PYC_E_ARG, "block size " + std::to_string(block) + " cannot be resident");
   int r = nb * current_device_props().sm_count;
   std::lock_guard<std::mutex> lk(mu);
-  cache[{f, block}] = r;
+  cache[key] = r;
   return r;
 }
 

@@ -351,6 +351,51 @@ std::string fold_tile(const std::string& map_expr, const std::string& base) {
   return o.str();
 }
 
+// Bytes of the lifted arrays read per element (what one pass over a tile loads).
+int stage_elem_bytes(const ArgSpec& spec) {
+  int b = 0;
+  for (auto& p : spec.params)
+    if (p.is_ptr && p.lifted && p.read) b += type_info(p.dtype).bytes;
+  return b;
+}
+
+// Vector loads of group u for the lifted arrays that `code` (already
+// rewritten to register slots) reads.
+std::string group_loads_used(const ArgSpec& spec, const std::string& code) {
+  std::ostringstream o;
+  for (auto& p : spec.params) {
+    if (!(p.is_ptr && p.lifted && p.read)) continue;
+    if (code.find("pyc_r_" + p.name + " ") == std::string::npos &&
+        code.find("pyc_r_" + p.name + "[") == std::string::npos)
+      continue;
+    o << "        pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&pyc_r_" << p.name
+      << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
+  }
+  return o.str();
+}
+
+// Element-wise loads into register slot pyc_k at index i of the lifted arrays
+// read (by `code` only, if it is not empty), and stores of those written.
+std::string scalar_loads_k(const ArgSpec& spec, const std::string& code) {
+  std::ostringstream o;
+  for (auto& p : spec.params) {
+    if (!(p.is_ptr && p.lifted && p.read)) continue;
+    if (!code.empty() && code.find("pyc_r_" + p.name + " ") == std::string::npos &&
+        code.find("pyc_r_" + p.name + "[") == std::string::npos)
+      continue;
+    o << "          pyc_r_" << p.name << "[pyc_k] = " << p.name << "[i];\n";
+  }
+  return o.str();
+}
+
+std::string scalar_stores_k(const ArgSpec& spec) {
+  std::ostringstream o;
+  for (auto& p : spec.params)
+    if (p.is_ptr && p.lifted && p.written)
+      o << "            " << p.name << "[i] = pyc_r_" << p.name << "[pyc_k];\n";
+  return o.str();
+}
+
 std::string scalar_io(const ArgSpec& spec, bool load) {
   std::ostringstream o;
   for (auto& p : spec.params) {
@@ -901,6 +946,7 @@ ScanGen generate_scan(const ArgSpec& spec, pyc_dtype dtype, const std::string& n
                                    preamble, tag, 0, false);
   ScanGen g;
   g.acc_bytes = core.acc_bytes;
+  g.stage_elem_bytes = stage_elem_bytes(spec);
   std::ostringstream o;
   o << core.source;
   o << R"PYC(
@@ -923,161 +969,474 @@ __device__ __forceinline__ pyc_acc_t pyc_warp_incl_scan(pyc_acc_t v) {
   }
   return v;
 }
-// Exclusive scan across the block in thread order; *total = the block's total.
-__device__ __forceinline__ pyc_acc_t pyc_block_excl_scan(const pyc_acc_t v, pyc_acc_t* total) {
-  __shared__ pyc_acc_t pyc_ws[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const pyc_acc_t incl = pyc_warp_incl_scan(v);
-  __syncthreads();  // pyc_ws may still be read from the previous call
-  if (lane == 31) pyc_ws[w] = incl;
-  __syncthreads();
-  if (w == 0) {
-    pyc_acc_t s = lane < nw ? pyc_ws[lane] : pyc_neutral();
-    s = pyc_warp_incl_scan(s);
-    pyc_ws[lane] = s;
-  }
-  __syncthreads();
-  pyc_acc_t ex = pyc_shfl_up(incl, 1);
-  if (lane == 0) ex = pyc_neutral();
-  *total = pyc_ws[nw - 1];
-  return w > 0 ? pyc_combine(pyc_ws[w - 1], ex) : ex;
+template <typename T>
+__device__ __forceinline__ T pyc_shfl_idx(const T v, int src) {
+  pyc_words<T> u;
+  u.t = v;
+#pragma unroll
+  for (int j = 0; j < (int)(sizeof(T) / 4); ++j) u.w[j] = __shfl_sync(0xffffffffu, u.w[j], src);
+  return u.t;
+}
+__device__ __forceinline__ unsigned pyc_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void pyc_st_release(unsigned* p, const unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Pass 1: chunk totals (the reduction core), then the last CTA to finish
-// replaces them by exclusive carries: carry[c] = total[0] + ... + total[c-1].
-template <int VB, int U>
-__device__ __forceinline__ void pyc_scan_pass1(const pyc_args& pyc_p, const pyc_i64 n,
-    const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 nchunks,
-    pyc_acc_t* __restrict__ part, unsigned* __restrict__ ticket) {
-  __shared__ unsigned pyc_last;
-  for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    pyc_acc_t v = pyc_chunk<VB, U>(pyc_p, n, head, chunk, c, threadIdx.x, blockDim.x);
-    v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
-    if (threadIdx.x == 0) part[c] = v;
+// Launch parameters of the single-pass scan.  Tile t publishes a descriptor:
+// flag[t] = epoch << 2 | state, state 1 = its aggregate is in agg[t], state 2 =
+// its inclusive prefix is in inc[t].  ctl[0] hands out tile indices in order,
+// ctl[1] counts CTAs that have finished (the last one resets both), ctl[2] is
+// the error word (non-zero after a wait gave up; cleared by the host) and
+// ctl[3] the epoch of the last launch in which a wait gave up.
+struct pyc_scan_params {
+  unsigned* flag;
+  pyc_acc_t* agg;
+  pyc_acc_t* inc;
+  unsigned long long* ctl;
+  pyc_i64 n;
+  pyc_i64 head;         // < 0: every tile is ragged; else [0, head) is tile 0 if head > 0
+  pyc_i64 nfull;        // vector tiles of `groups` row groups per warp after the head
+  pyc_i64 ntiles;
+  pyc_i64 spin_limit;   // polls of one descriptor window before giving up
+  pyc_i64 stall_tile;   // test hook: this tile publishes nothing (-1: none)
+  unsigned epoch;
+  unsigned groups;      // row groups per warp in a vector tile
+  unsigned tail_groups; // row groups of the vector tile after them (0: none)
+  unsigned pad;
+};
+static_assert(sizeof(pyc_scan_params) == 96, "scan params layout");
+
+// Bounds-checked build (PYC_CHECK defined): every access of the scan checks
+// [idx, idx + cnt) against [0, bound); the first violation is recorded in
+// ctl[4..7] (code, index, tile, block << 16 | thread) and the access skipped.
+#ifdef PYC_CHECK
+__device__ __noinline__ bool pyc_check_fail(const pyc_scan_params& S, const pyc_i64 idx,
+                                            const int code, const pyc_i64 t) {
+  if (atomicCAS(S.ctl + 4, 0ull, (unsigned long long)code) == 0ull) {
+    S.ctl[5] = (unsigned long long)idx;
+    S.ctl[6] = (unsigned long long)t;
+    S.ctl[7] = ((unsigned long long)blockIdx.x << 16) | threadIdx.x;
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) pyc_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
-  __syncthreads();
-  if (!pyc_last) return;
-  __threadfence();
-  // each thread owns a contiguous run of totals
-  const int cnt = (int)nchunks;
-  const int per = (cnt + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int lo = (int)threadIdx.x * per;
-  const int hi = lo + per < cnt ? lo + per : cnt;
-  pyc_acc_t mine = pyc_neutral();
-  for (int j = lo; j < hi; ++j) mine = pyc_combine(mine, pyc_ld_cg(part + j));
-  pyc_acc_t tot;
-  pyc_acc_t run = pyc_block_excl_scan(mine, &tot);
-  for (int j = lo; j < hi; ++j) {
-    const pyc_acc_t t = pyc_ld_cg(part + j);
-    part[j] = run;
-    run = pyc_combine(run, t);
-  }
-  if (threadIdx.x == 0) *ticket = 0u;
+  return false;
+}
+#define PYC_OK(S, idx, cnt, bound, code, t)                                        \
+  (((pyc_i64)(idx) >= 0 && (pyc_i64)(idx) + (pyc_i64)(cnt) <= (pyc_i64)(bound)) || \
+   pyc_check_fail(S, (pyc_i64)(idx), code, t))
+#else
+#define PYC_OK(S, idx, cnt, bound, code, t) true
+#endif
+
+__device__ __forceinline__ void pyc_publish(const pyc_scan_params& S, const pyc_i64 t,
+                                            const unsigned state, const pyc_acc_t v) {
+  if (t == S.stall_tile) return;
+  if (!PYC_OK(S, t, 1, S.ntiles, 31, t)) return;
+  if (state == 1u) S.agg[t] = v;
+  else S.inc[t] = v;
+  pyc_st_release(S.flag + t, (S.epoch << 2) | state);
 }
 
-// Pass 2: chunk c in index order -- the scalar head (chunk 0 only), the full
-// tiles, the scalar tail -- with a running carry that starts at carry[c].
-template <int VB, int U>
-__device__ __forceinline__ void pyc_scan_chunk(const pyc_args& pyc_p, const pyc_i64 n,
-    const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 c, pyc_acc_t pyc_carry) {
+// Exclusive prefix of tile t > 0 by warp 0: look back over the descriptors of
+// tiles t-1, t-2, ... 32 at a time (lane l reads tile j-l) until a window holds
+// an inclusive prefix; the aggregates after it are combined in tile order.
+// Every tile below t was handed out before t, so its CTA is running and
+// publishes without waiting on this one.  The wait is bounded: after
+// spin_limit polls (or once another CTA of the same launch has given up) the
+// error word is set and the neutral element is returned.
+__device__ pyc_acc_t pyc_lookback(const pyc_scan_params& S, const pyc_i64 t) {
+  const int lane = threadIdx.x & 31;
+  const unsigned want = S.epoch;
+  pyc_acc_t run = pyc_neutral();
+  pyc_i64 j = t - 1;
+  pyc_i64 polls = 0;
+  for (;;) {
+    const pyc_i64 q = j - lane;
+    unsigned st;
+    for (;;) {
+      st = 2u;  // below tile 0: treated as an inclusive prefix never selected
+      if (q >= 0 && PYC_OK(S, q, 1, S.ntiles, 32, t)) {
+        const unsigned f = pyc_ld_acquire(S.flag + q);
+        st = (f >> 2) == want ? (f & 3u) : 0u;
+      }
+      // done once every tile after the nearest inclusive prefix has published
+      // (or all 32 have): tiles further back are not needed
+      const unsigned xm = __ballot_sync(0xffffffffu, st == 0u);
+      const unsigned pm0 = __ballot_sync(0xffffffffu, st == 2u);
+      if (xm == 0u || (pm0 != 0u && (xm & ((2u << (__ffs(pm0) - 1)) - 1u)) == 0u)) break;
+      ++polls;
+      bool give_up = polls > S.spin_limit;
+      if ((polls & 63) == 0)
+        give_up |= *(volatile const unsigned long long*)(S.ctl + 3) == (unsigned long long)want;
+      if (__any_sync(0xffffffffu, give_up)) {
+        if (lane == 0) {
+          atomicOr(S.ctl + 2, polls > S.spin_limit ? 1ull : 2ull);
+          atomicExch(S.ctl + 3, (unsigned long long)want);
+        }
+        return pyc_neutral();
+      }
+      __nanosleep(32);
+    }
+    const unsigned pm = __ballot_sync(0xffffffffu, st == 2u);
+    const int p = pm ? __ffs(pm) - 1 : 31;
+    pyc_acc_t v = pyc_neutral();
+    if (q >= 0 && lane <= p && PYC_OK(S, q, 1, S.ntiles, 33, t))
+      v = st == 2u ? pyc_ld_cg(S.inc + q) : pyc_ld_cg(S.agg + q);
+    // ordered fold: lane p (earliest tile) first, lane 0 (tile j) last
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const pyc_acc_t o = pyc_shfl_down(v, d);
+      if (lane + d < 32) v = pyc_combine(o, v);
+    }
+    run = pyc_combine(pyc_shfl_idx(v, 0), run);
+    if (pm) return run;
+    j -= 32;
+  }
+}
+
+// Intra-CTA hand-offs: mbarriers, waited on with a bounded loop.
+__device__ __forceinline__ unsigned pyc_saddr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void pyc_mbar_init(unsigned long long* bar, const unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(pyc_saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void pyc_mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(pyc_saddr(bar)) : "memory");
+}
+__device__ __forceinline__ bool pyc_mbar_try_wait(unsigned long long* bar, const unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(pyc_saddr(bar)), "r"(parity) : "memory");
+  return ok != 0u;
+}
+// Waits for the phase of `bar` with the given parity to complete; false (and
+// bit 8 set in the error word) if it has not after about 2^25 polls, a bound
+// well above the look-back's own.
+__device__ __forceinline__ bool pyc_mbar_wait(unsigned long long* bar, const unsigned parity,
+                                              unsigned long long* err) {
+  for (unsigned it = 0; !pyc_mbar_try_wait(bar, parity); ++it) {
+    if (it > (1u << 25)) {
+      atomicOr(err, 8ull);
+      return false;
+    }
+    if (it > 64u) __nanosleep(128);
+  }
+  return true;
+}
+
+// Rows of a tile: warp w (of nw compute warps) owns rows [w*G*U, (w+1)*G*U),
+// each of 32*E consecutive elements, lane l holding E consecutive elements of
+// a row.  A vector tile is aligned and full: U rows at a time, one coalesced
+// vector per array and row.  A ragged tile [ts, te) takes one row at a time
+// with element-wise accesses where i < te.
+
+// Sweep 1: the warp's aggregate in element order (valid in lane 0).
+template <int VB, int U, bool RAG>
+__device__ __forceinline__ pyc_acc_t pyc_sweep1(const pyc_args& pyc_p, const pyc_scan_params& S,
+    const pyc_i64 t, const pyc_i64 ts, const pyc_i64 te, const int G, const int w,
+    const int lane) {
   constexpr int E = VB / PYC_MIN_BYTES;
-  constexpr int T = E * U;
+  constexpr int RU = RAG ? 1 : U;  // rows per step
+  constexpr int T = E * RU;
 )PYC";
   o << aliases(spec, "pyc_p");
-  o << R"PYC(  (void)n;
-  const pyc_i64 pyc_step = (pyc_i64)blockDim.x * E;
-  const pyc_i64 pyc_tile = pyc_step * U;
-  pyc_i64 pyc_vs = 0, pyc_ve = 0, pyc_ss, pyc_se;
-  if (head >= 0) {
-    pyc_vs = head + c * chunk;
-    pyc_ve = pyc_vs + chunk < n ? pyc_vs + chunk : n;
-    pyc_ss = 0;
-    pyc_se = c == 0 ? head : 0;
-  } else {
-    pyc_ss = c * chunk;
-    pyc_se = pyc_ss + chunk < n ? pyc_ss + chunk : n;
-  }
-  const pyc_i64 pyc_nt = pyc_ve > pyc_vs ? (pyc_ve - pyc_vs) / pyc_tile : 0;
-  const pyc_i64 pyc_r0 = pyc_vs + pyc_nt * pyc_tile;
-  for (int pyc_part = 0; pyc_part < 3; ++pyc_part) {
-    if (pyc_part == 1) {
-      for (pyc_i64 pyc_t = 0; pyc_t < pyc_nt; ++pyc_t) {
-        const pyc_i64 pyc_b0 = pyc_vs + pyc_t * pyc_tile + (pyc_i64)threadIdx.x * E;
+  o << R"PYC(  (void)te;
+  const pyc_i64 pyc_wb = ts + (pyc_i64)w * G * (U * 32 * E) + (pyc_i64)lane * E;
+  pyc_acc_t pyc_wagg = pyc_neutral();
+  const int pyc_steps = G * (U / RU);
+  for (int pyc_g = 0; pyc_g < pyc_steps; ++pyc_g) {
+    const pyc_i64 pyc_gb = pyc_wb + (pyc_i64)pyc_g * (RU * 32 * E);
 )PYC";
   o << reg_decls(spec, "T");
-  o << R"PYC(#pragma unroll
-        for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
-          const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
+  o << R"PYC(    if constexpr (RAG) {
+#pragma unroll
+      for (int pyc_k = 0; pyc_k < T; ++pyc_k) {
+        const pyc_i64 i = pyc_gb + pyc_k;
+        if (i < te) {
 )PYC";
-  o << group_io(spec, true);
-  o << R"PYC(        }
-#pragma unroll
-        for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
-          pyc_acc_t pyc_l[E];
-#pragma unroll
-          for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
-            const int pyc_k = pyc_u * E + pyc_e;
-            const pyc_i64 i = pyc_b0 + (pyc_i64)pyc_u * pyc_step + pyc_e;
-            (void)i;
-            (void)pyc_k;
-            const pyc_acc_t pyc_v = (pyc_acc_t)()PYC" << input_expr << R"PYC();
-            pyc_l[pyc_e] = pyc_e == 0 ? pyc_v : pyc_combine(pyc_l[pyc_e - 1], pyc_v);
-          }
-          pyc_acc_t pyc_rowtot;
-          const pyc_acc_t pyc_ex = pyc_block_excl_scan(pyc_l[E - 1], &pyc_rowtot);
-          const pyc_acc_t pyc_pre = pyc_combine(pyc_carry, pyc_ex);
-#pragma unroll
-          for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
-            const int pyc_k = pyc_u * E + pyc_e;
-            const pyc_i64 i = pyc_b0 + (pyc_i64)pyc_u * pyc_step + pyc_e;
-            (void)i;
-            (void)pyc_k;
-            const pyc_acc_t item = pyc_combine(pyc_pre, pyc_l[pyc_e]);
-            const pyc_acc_t prev_item = pyc_e == 0 ? pyc_pre : pyc_combine(pyc_pre, pyc_l[pyc_e - 1]);
-            (void)item;
-            (void)prev_item;
-            { )PYC" << output_stmt << R"PYC( ; }
-          }
-          pyc_carry = pyc_combine(pyc_carry, pyc_rowtot);
-        }
-#pragma unroll
-        for (int pyc_u = 0; pyc_u < U; ++pyc_u) {
-          const pyc_i64 pyc_e0 = pyc_b0 + (pyc_i64)pyc_u * pyc_step;
-)PYC";
-  o << group_io(spec, false);
+  o << "          if (PYC_OK(S, i, 1, S.n, 12, t)) {\n" << scalar_loads_k(spec, input_expr)
+    << "          }\n";
   o << R"PYC(        }
       }
-      continue;
-    }
-    // scalar ranges: the head before the tiles, the tail after them, in rounds
-    // of blockDim.x consecutive elements
-    const pyc_i64 pyc_rs = pyc_part == 0 ? pyc_ss : pyc_r0;
-    const pyc_i64 pyc_re = pyc_part == 0 ? pyc_se : (pyc_ve > pyc_r0 ? pyc_ve : pyc_r0);
-    for (pyc_i64 pyc_base = pyc_rs; pyc_base < pyc_re; pyc_base += blockDim.x) {
-      const pyc_i64 i = pyc_base + threadIdx.x;
-      const bool pyc_valid = i < pyc_re;
+    } else {
+#pragma unroll
+      for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_gb + (pyc_i64)pyc_u * (32 * E);
 )PYC";
-  o << reg_decls(spec, "1");
-  o << "      if (pyc_valid) {\n" << scalar_io(spec, true) << "      }\n";
-  o << R"PYC(      const int pyc_k = 0;
-      (void)pyc_k;
+  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 11, t)) {\n" << group_loads_used(spec, input_expr)
+    << "        }\n";
+  o << R"PYC(      }
+    }
+#pragma unroll
+    for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
       pyc_acc_t pyc_v = pyc_neutral();
-      if (pyc_valid) pyc_v = (pyc_acc_t)()PYC" << input_expr << R"PYC();
-      pyc_acc_t pyc_tot;
-      const pyc_acc_t pyc_ex = pyc_block_excl_scan(pyc_v, &pyc_tot);
-      if (pyc_valid) {
-        const pyc_acc_t prev_item = pyc_combine(pyc_carry, pyc_ex);
-        const pyc_acc_t item = pyc_combine(prev_item, pyc_v);
+#pragma unroll
+      for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
+        const int pyc_k = pyc_u * E + pyc_e;
+        const pyc_i64 i = pyc_gb + (pyc_i64)pyc_u * (32 * E) + pyc_e;
+        (void)i;
+        pyc_acc_t pyc_x = pyc_neutral();
+        if (!RAG || i < te) pyc_x = (pyc_acc_t)()PYC" << input_expr << R"PYC();
+        pyc_v = pyc_e == 0 ? pyc_x : pyc_combine(pyc_v, pyc_x);
+      }
+      // ordered fold across the row: lane 0 ends with lanes 0..31 in order
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const pyc_acc_t o = pyc_shfl_down(pyc_v, d);
+        if (lane + d < 32) pyc_v = pyc_combine(pyc_v, o);
+      }
+      pyc_wagg = pyc_combine(pyc_wagg, pyc_v);
+    }
+  }
+  return pyc_wagg;
+}
+
+// Sweep 2: the warp's rows again (from L2), scanned from `run` (everything
+// before the warp's first element), with the output statement.
+template <int VB, int U, bool RAG>
+__device__ __forceinline__ void pyc_sweep2(const pyc_args& pyc_p, const pyc_scan_params& S,
+    const pyc_i64 t, const pyc_i64 ts, const pyc_i64 te, const int G, const int w,
+    const int lane, pyc_acc_t pyc_run) {
+  constexpr int E = VB / PYC_MIN_BYTES;
+  constexpr int RU = RAG ? 1 : U;
+  constexpr int T = E * RU;
+)PYC";
+  o << aliases(spec, "pyc_p");
+  o << R"PYC(  (void)te;
+  const pyc_i64 pyc_wb = ts + (pyc_i64)w * G * (U * 32 * E) + (pyc_i64)lane * E;
+  const int pyc_steps = G * (U / RU);
+  for (int pyc_g = 0; pyc_g < pyc_steps; ++pyc_g) {
+    const pyc_i64 pyc_gb = pyc_wb + (pyc_i64)pyc_g * (RU * 32 * E);
+)PYC";
+  o << reg_decls(spec, "T");
+  o << R"PYC(    if constexpr (RAG) {
+#pragma unroll
+      for (int pyc_k = 0; pyc_k < T; ++pyc_k) {
+        const pyc_i64 i = pyc_gb + pyc_k;
+        if (i < te) {
+)PYC";
+  o << "          if (PYC_OK(S, i, 1, S.n, 21, t)) {\n" << scalar_loads_k(spec, "")
+    << "          }\n";
+  o << R"PYC(        }
+      }
+    } else {
+#pragma unroll
+      for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_gb + (pyc_i64)pyc_u * (32 * E);
+)PYC";
+  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 22, t)) {\n" << group_io(spec, true) << "        }\n";
+  o << R"PYC(      }
+    }
+#pragma unroll
+    for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
+      pyc_acc_t pyc_l[E];
+#pragma unroll
+      for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
+        const int pyc_k = pyc_u * E + pyc_e;
+        const pyc_i64 i = pyc_gb + (pyc_i64)pyc_u * (32 * E) + pyc_e;
+        (void)i;
+        pyc_acc_t pyc_x = pyc_neutral();
+        if (!RAG || i < te) pyc_x = (pyc_acc_t)()PYC" << input_expr << R"PYC();
+        pyc_l[pyc_e] = pyc_e == 0 ? pyc_x : pyc_combine(pyc_l[pyc_e - 1], pyc_x);
+      }
+      const pyc_acc_t pyc_in = pyc_warp_incl_scan(pyc_l[E - 1]);
+      pyc_acc_t pyc_ex = pyc_shfl_up(pyc_in, 1);
+      if (lane == 0) pyc_ex = pyc_neutral();
+      const pyc_acc_t pyc_p0 = pyc_combine(pyc_run, pyc_ex);
+#pragma unroll
+      for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
+        const int pyc_k = pyc_u * E + pyc_e;
+        const pyc_i64 i = pyc_gb + (pyc_i64)pyc_u * (32 * E) + pyc_e;
+        (void)i;
+        const pyc_acc_t item = pyc_combine(pyc_p0, pyc_l[pyc_e]);
+        const pyc_acc_t prev_item = pyc_e == 0 ? pyc_p0 : pyc_combine(pyc_p0, pyc_l[pyc_e - 1]);
         (void)item;
         (void)prev_item;
-        { )PYC" << output_stmt << R"PYC( ; }
+        if (!RAG || i < te) {
+          { )PYC" << output_stmt << R"PYC( ; }
+          if constexpr (RAG) {
+            if (PYC_OK(S, i, 1, S.n, 23, t)) {
 )PYC";
-  o << scalar_io(spec, false);
+  o << scalar_stores_k(spec);
+  o << R"PYC(            }
+          }
+        }
+      }
+      pyc_run = pyc_combine(pyc_run, pyc_shfl_idx(pyc_in, 31));
+    }
+    if constexpr (!RAG) {
+#pragma unroll
+      for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_gb + (pyc_i64)pyc_u * (32 * E);
+)PYC";
+  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 24, t)) {\n" << group_io(spec, false) << "        }\n";
   o << R"PYC(      }
-      pyc_carry = pyc_combine(pyc_carry, pyc_tot);
+    }
+  }
+}
+
+// Tile t: [ts, te), row groups per warp, and whether it is ragged.  Order: the
+// scalar head (if head > 0), nfull vector tiles of `groups` row groups, one of
+// `tail_groups` (if any), the ragged rest; with head < 0 every tile is ragged.
+struct pyc_tinfo {
+  pyc_i64 ts, te;
+  int g;
+  bool rag;
+};
+__device__ __forceinline__ pyc_tinfo pyc_tile_info(const pyc_scan_params& S, const pyc_i64 t,
+                                                   const pyc_i64 base) {
+  const pyc_i64 tile = base * S.groups;
+  const pyc_i64 htile = S.head > 0 ? 1 : 0;
+  pyc_tinfo r;
+  if (S.head < 0) {
+    r.ts = t * tile;
+    r.te = r.ts + tile < S.n ? r.ts + tile : S.n;
+    r.g = (int)S.groups;
+    r.rag = true;
+  } else if (t < htile) {
+    r.ts = 0;
+    r.te = S.head;
+    r.g = 1;
+    r.rag = true;
+  } else if (t < htile + S.nfull) {
+    r.ts = S.head + (t - htile) * tile;
+    r.te = r.ts + tile;
+    r.g = (int)S.groups;
+    r.rag = false;
+  } else if (t == htile + S.nfull && S.tail_groups > 0) {
+    r.ts = S.head + S.nfull * tile;
+    r.te = r.ts + base * S.tail_groups;
+    r.g = (int)S.tail_groups;
+    r.rag = false;
+  } else {
+    r.ts = S.head + S.nfull * tile + base * S.tail_groups;
+    r.te = S.n;
+    r.g = 1;
+    r.rag = true;
+  }
+  return r;
+}
+
+// Persistent single-pass scan with a look-back warp.  The CTA has nw compute
+// warps and one look-back warp (the last).  Iteration k of the compute warps:
+// take tile k, sweep 1 over it, publish its aggregate and hand the warp
+// aggregates to the look-back warp, then (once its prefix is known) sweep 2
+// over tile k-1.  The look-back warp finds tile k's exclusive prefix, publishes
+// its inclusive prefix and hands back the prefix of every compute warp's rows,
+// so the look-back of one tile runs while the compute warps scan the previous
+// tile and fold the next.  Slots alternate with the parity of k:
+//   m_tile[s]  compute warp 0 has posted the tile index (1 arrival),
+//   m_agg[s]   every compute warp has stored its aggregate (nw arrivals),
+//   m_pre[s]   the look-back warp has stored the warp prefixes (1 arrival);
+// a slot is reused two iterations later, after both sides have passed the
+// hand-off of the iteration between, so no wait can miss its phase.  The last
+// compute warp to store its aggregate (a shared counter) publishes the tile's.
+// A wait that runs out sets the error word and ends the CTA.
+template <int VB, int U>
+__device__ __forceinline__ void pyc_scan_body(const pyc_args& pyc_p, const pyc_scan_params& S) {
+  constexpr int R = 32 * (VB / PYC_MIN_BYTES) * U;  // elements of one row group of a warp
+  __shared__ pyc_acc_t pyc_tot[2][32];
+  __shared__ pyc_acc_t pyc_off[2][32];
+  __shared__ pyc_i64 pyc_tq[2];
+  __shared__ unsigned pyc_cnt[2];
+  __shared__ __align__(8) unsigned long long pyc_mt[2], pyc_ma[2], pyc_mp[2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5) - 1;
+  const pyc_i64 base = (pyc_i64)nw * R;
+  unsigned long long* const err = S.ctl + 2;
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < 2; ++j) {
+      pyc_mbar_init(&pyc_mt[j], 1u);
+      pyc_mbar_init(&pyc_ma[j], (unsigned)nw);
+      pyc_mbar_init(&pyc_mp[j], 1u);
+      pyc_cnt[j] = 0u;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (w == nw) {
+    for (int k = 0;; ++k) {
+      const int sl = k & 1;
+      const unsigned ph = (unsigned)(k >> 1) & 1u;
+      if (!pyc_mbar_wait(&pyc_ma[sl], ph, err)) return;
+      const pyc_i64 t = pyc_tq[sl];
+      if (t >= S.ntiles || !PYC_OK(S, t, 0, S.ntiles, 41, t)) break;
+      pyc_acc_t s = lane < nw ? pyc_tot[sl][lane] : pyc_neutral();
+      s = pyc_warp_incl_scan(s);
+      const pyc_acc_t agg = pyc_shfl_idx(s, nw - 1);  // (all lanes: a warp-wide shuffle)
+      pyc_acc_t ex = pyc_neutral();
+      if (t > 0) {
+        ex = pyc_lookback(S, t);
+        if (lane == 0) pyc_publish(S, t, 2u, pyc_combine(ex, agg));
+      }
+      pyc_acc_t o = pyc_shfl_up(s, 1);
+      if (lane == 0) o = pyc_neutral();
+      if (lane < nw) pyc_off[sl][lane] = pyc_combine(ex, o);
+      __syncwarp();
+      if (lane == 0) pyc_mbar_arrive(&pyc_mp[sl]);
+    }
+  } else {
+    pyc_i64 tprev = -1;
+    for (int k = 0;; ++k) {
+      const int sl = k & 1;
+      const unsigned ph = (unsigned)(k >> 1) & 1u;
+      if (threadIdx.x == 0) {
+        pyc_tq[sl] = (pyc_i64)atomicAdd(S.ctl, 1ull);
+        pyc_mbar_arrive(&pyc_mt[sl]);
+      }
+      if (!pyc_mbar_wait(&pyc_mt[sl], ph, err)) return;
+      const pyc_i64 t = pyc_tq[sl];
+      if (t < S.ntiles && PYC_OK(S, t, 0, S.ntiles, 42, t)) {
+        const pyc_tinfo I = pyc_tile_info(S, t, base);
+        if (!PYC_OK(S, I.ts, I.te - I.ts, S.n, 43, t)) return;
+        const pyc_acc_t a =
+            I.rag ? pyc_sweep1<VB, U, true>(pyc_p, S, t, I.ts, I.te, I.g, w, lane)
+                  : pyc_sweep1<VB, U, false>(pyc_p, S, t, I.ts, I.te, I.g, w, lane);
+        unsigned last = 0u;
+        if (lane == 0) {
+          pyc_tot[sl][w] = a;
+          __threadfence_block();
+          last = atomicAdd(&pyc_cnt[sl], 1u) == (unsigned)nw - 1u ? 1u : 0u;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+          // every aggregate of the tile is stored: publish the tile's at once
+          // (its inclusive prefix for tile 0), so that later tiles need not wait
+          // for this CTA's look-back warp
+          __threadfence_block();
+          pyc_acc_t s = lane < nw ? pyc_tot[sl][lane] : pyc_neutral();
+          s = pyc_warp_incl_scan(s);
+          const pyc_acc_t agg = pyc_shfl_idx(s, nw - 1);
+          if (lane == 0) {
+            pyc_publish(S, t, t == 0 ? 2u : 1u, agg);
+            pyc_cnt[sl] = 0u;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) pyc_mbar_arrive(&pyc_ma[sl]);
+      if (tprev >= 0) {
+        const int sp = (k - 1) & 1;
+        if (!pyc_mbar_wait(&pyc_mp[sp], (unsigned)((k - 1) >> 1) & 1u, err)) return;
+        const pyc_tinfo I = pyc_tile_info(S, tprev, base);
+        const pyc_acc_t run = pyc_off[sp][w];
+        if (I.rag) pyc_sweep2<VB, U, true>(pyc_p, S, tprev, I.ts, I.te, I.g, w, lane, run);
+        else pyc_sweep2<VB, U, false>(pyc_p, S, tprev, I.ts, I.te, I.g, w, lane, run);
+      }
+      if (t >= S.ntiles) break;
+      tprev = t;
+    }
+  }
+  // the last CTA to leave resets the tile counter for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(S.ctl + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+      S.ctl[0] = 0ull;
+      S.ctl[1] = 0ull;
+      __threadfence();
     }
   }
 }
@@ -1085,17 +1444,9 @@ __device__ __forceinline__ void pyc_scan_chunk(const pyc_args& pyc_p, const pyc_
 )PYC";
   for (auto& v : all_variants()) {
     std::string sfx = variant_suffix(v);
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_scan1_" << tag << "_" << sfx
-      << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
-         "const pyc_i64 nchunks, pyc_acc_t* part, unsigned* ticket) {\n"
-      << "  pyc_scan_pass1<" << v.vec_bytes << ", " << v.unroll
-      << ">(pyc_p, n, head, chunk, nchunks, part, ticket);\n}\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_scan2_" << tag << "_" << sfx
-      << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
-         "const pyc_i64 nchunks, const pyc_acc_t* carry) {\n"
-      << "  for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x)\n"
-      << "    pyc_scan_chunk<" << v.vec_bytes << ", " << v.unroll
-      << ">(pyc_p, n, head, chunk, c, carry[c]);\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(544) pyc_scan_" << tag << "_" << sfx
+      << "(const pyc_args pyc_p, const pyc_scan_params S) {\n"
+      << "  pyc_scan_body<" << v.vec_bytes << ", " << v.unroll << ">(pyc_p, S);\n}\n";
   }
   g.source = o.str();
   return g;

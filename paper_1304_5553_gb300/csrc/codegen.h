@@ -66,6 +66,7 @@ ReduceGen generate_reduce(const ArgSpec& spec, pyc_dtype out_dtype, ReduceKind k
 struct ScanGen {
   std::string source;
   int acc_bytes = 0;
+  int stage_elem_bytes = 0;  // bytes per tile element staged in shared memory
 };
 ScanGen generate_scan(const ArgSpec& spec, pyc_dtype dtype, const std::string& neutral,
                       const std::string& scan_expr, const std::string& input_rewritten,

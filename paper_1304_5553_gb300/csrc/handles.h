@@ -110,7 +110,8 @@ int64_t vector_head(const ArgSpec& spec, void* const* ptrs, int vec_bytes, int m
                     int64_t n);
 
 // Resident CTAs of `f` at `block` threads on the current device.
-int resident_ctas(CUfunction f, int block);
+// CTAs of f that fit on the device at once (dyn_smem: dynamic shared bytes per CTA).
+int resident_ctas(CUfunction f, int block, int dyn_smem = 0);
 
 // Chunking of a single reduction of n elements (head from vector_head).
 struct ChunkPlan {

@@ -1,13 +1,14 @@
 // Parallel prefix scan (Sec. 3.2.6): C ABI and launches (see include/pyc.h).
 //
-// Two launches on the caller's stream, with no waiting between CTAs:
-//  pass 1 folds every chunk of the input expression (the map-reduce core) and
-//         the last CTA to finish turns the chunk totals into exclusive carries;
-//  pass 2 scans every chunk from its carry in index order (block scans of one
-//         row of vector groups at a time) and runs the output statement with
-//         `item` (inclusive prefix) and `prev_item` (exclusive prefix).
-// Both passes use one chunk plan, a fixed function of (n, tuning).
+// One launch on the caller's stream.  Persistent CTAs take tiles in index order
+// from a counter.  The compute warps fold each tile (sweep 1) and hand its
+// aggregate to the CTA's look-back warp, which publishes it, looks back over
+// the descriptors of the tiles before it for the exclusive prefix and
+// publishes the inclusive prefix; meanwhile the compute warps scan the
+// previous tile (sweep 2, re-reading it from L2) and write its output.  HBM
+// sees the input read once and the output written once.
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
@@ -18,7 +19,9 @@ struct pyc_scan : pyc::HandleBase {
   pyc_dtype dtype = PYC_F32;
   pyc::ScanGen gen;
   struct Workspace {
-    CUdeviceptr base = 0, part = 0, ticket = 0;
+    CUdeviceptr base = 0;
+    int64_t cap = 0;     // tile descriptors
+    uint32_t epoch = 0;  // of the last launch
   };
   std::mutex ws_mu;
   std::map<std::pair<CUcontext, CUstream>, Workspace> ws;
@@ -28,41 +31,110 @@ namespace pyc {
 
 namespace {
 
-pyc_scan::Workspace& scan_workspace(pyc_scan* h, CUstream stream) {
+// Mirrors pyc_scan_params in the generated source.
+struct ScanParams {
+  CUdeviceptr flag, agg, inc, ctl;
+  int64_t n, head, nfull, ntiles, spin_limit, stall_tile;
+  uint32_t epoch, groups, tail_groups, pad;
+};
+static_assert(sizeof(ScanParams) == 96, "scan params layout");
+
+constexpr int64_t kCtlBytes = 256;               // ctl[0..3] at the start of the workspace
+constexpr uint32_t kEpochLimit = 1u << 30;       // flags hold epoch << 2 | state
+constexpr int64_t kDefaultSpinLimit = 1 << 20;   // about a second of polling
+
+int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
+
+// Row groups per warp in a vector tile.  A tile is read twice (fold, then
+// scan), the second time from L2, so the tiles in flight (one per resident
+// CTA) should fit in about 3/8 of L2; within that, tiles are made as large as
+// possible (fewer look-backs) while leaving at least four tiles per CTA.
+int scan_groups(int64_t n, int64_t base, int resident, int elem_bytes, int64_t l2_bytes) {
+  int64_t want = n / (4 * (int64_t)resident);
+  if (elem_bytes > 0) want = std::min<int64_t>(want, l2_bytes * 3 / 8 / resident / elem_bytes);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(64, want / base));
+}
+
+// Workspace of (context, stream) with room for `ntiles` descriptors, and the
+// parameters of the next launch (a fresh epoch).
+ScanParams scan_workspace(pyc_scan* h, CUstream stream, int64_t ntiles) {
   CUcontext ctx = ensure_context();
   std::lock_guard<std::mutex> lk(h->ws_mu);
-  auto key = std::make_pair(ctx, stream);
-  auto it = h->ws.find(key);
-  if (it != h->ws.end()) return it->second;
-  pyc_scan::Workspace w;
-  size_t part_bytes = (size_t)kMaxChunks * h->gen.acc_bytes;
-  PYC_CU(drv().cuMemAlloc(&w.base, part_bytes + 256));
-  w.part = w.base;
-  w.ticket = w.base + part_bytes;
-  PYC_CU(drv().cuMemsetD8Async(w.ticket, 0, 256, stream));
-  return h->ws.emplace(key, w).first->second;
+  pyc_scan::Workspace& w = h->ws[std::make_pair(ctx, stream)];
+  const int64_t acc = h->gen.acc_bytes;
+  auto flag_bytes = [](int64_t cap) { return align256(cap * 4); };
+  if (ntiles > w.cap) {
+    if (w.base) {
+      // a launch in flight on this stream may still use the old descriptors
+      PYC_CU(drv().cuStreamSynchronize(stream));
+      drv().cuMemFree(w.base);
+      w.base = 0;
+      w.cap = 0;
+    }
+    int64_t cap = std::max<int64_t>(4096, ntiles);
+    int64_t bytes = kCtlBytes + flag_bytes(cap) + 2 * align256(cap * acc);
+    PYC_CU(drv().cuMemAlloc(&w.base, (size_t)bytes));
+    PYC_CU(drv().cuMemsetD8Async(w.base, 0, (size_t)(kCtlBytes + flag_bytes(cap)), stream));
+    w.cap = cap;
+    w.epoch = 0;
+  }
+  if (++w.epoch >= kEpochLimit) {
+    // flags and ctl[3] may hold old epochs that are about to be reused
+    PYC_CU(drv().cuMemsetD8Async(w.base + kCtlBytes, 0, (size_t)flag_bytes(w.cap), stream));
+    PYC_CU(drv().cuMemsetD8Async(w.base + 24, 0, 8, stream));
+    w.epoch = 1;
+  }
+  ScanParams p{};
+  p.ctl = w.base;
+  p.flag = w.base + kCtlBytes;
+  p.agg = p.flag + flag_bytes(w.cap);
+  p.inc = p.agg + align256(w.cap * acc);
+  p.epoch = w.epoch;
+  return p;
 }
 
 void launch_scan(pyc_scan* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
-                 const void* scalars, CUstream stream) {
+                 const void* scalars, CUstream stream, int64_t stall_tile = -1,
+                 int64_t spin_limit = kDefaultSpinLimit) {
   if (cfg.block < 32 || cfg.block > 512 || cfg.block % 32)
     fail(PYC_E_ARG, "block must be a multiple of 32 in [32, 512]");
   if (n < 0) fail(PYC_E_ARG, "n must be >= 0");
+  if (spin_limit < 1) fail(PYC_E_ARG, "spin_limit must be >= 1");
   std::vector<unsigned char> args = pack_args(h->spec, ptrs, scalars);
   int64_t head = vector_head(h->spec, ptrs, cfg.v.vec_bytes, h->min_bytes, n);
   if (n == 0) return;
-  CUfunction f1 = h->mod->function(h->kname("pyc_scan1", cfg.v));
-  CUfunction f2 = h->mod->function(h->kname("pyc_scan2", cfg.v));
-  int r1 = resident_ctas(f1, cfg.block), r2 = resident_ctas(f2, cfg.block);
-  int64_t tile = (int64_t)cfg.block * (cfg.v.vec_bytes / h->min_bytes) * cfg.v.unroll;
-  ChunkPlan cp = plan_chunks(n, head, tile, std::min(r1, r2));
-  pyc_scan::Workspace& w = scan_workspace(h, stream);
-  void* p1[] = {args.data(), &n, &cp.head, &cp.chunk, &cp.nchunks, &w.part, &w.ticket};
-  PYC_CU(drv().cuLaunchKernel(f1, (unsigned)cp.grid, 1, 1, (unsigned)cfg.block, 1, 1, 0, stream,
-                              p1, nullptr));
-  unsigned grid2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(r2, cp.nchunks));
-  void* p2[] = {args.data(), &n, &cp.head, &cp.chunk, &cp.nchunks, &w.part};
-  PYC_CU(drv().cuLaunchKernel(f2, grid2, 1, 1, (unsigned)cfg.block, 1, 1, 0, stream, p2, nullptr));
+  CUfunction f = h->mod->function(h->kname("pyc_scan", cfg.v));
+  // cfg.block compute threads and one look-back warp
+  const int threads = cfg.block + 32;
+  const int resident = resident_ctas(f, threads);
+  // one row group per compute warp: 32 lanes x one vector of E elements x unroll rows
+  const int64_t base = (int64_t)cfg.block * (cfg.v.vec_bytes / h->min_bytes) * cfg.v.unroll;
+  const int groups = scan_groups(n, base, resident, h->gen.stage_elem_bytes,
+                                 current_device_props().l2_bytes);
+  const int64_t tile = base * groups;
+  int64_t nfull = 0, tail_groups = 0, ntiles;
+  if (head < 0) {
+    ntiles = (n + tile - 1) / tile;
+  } else {
+    nfull = (n - head) / tile;
+    const int64_t rest = (n - head) - nfull * tile;
+    tail_groups = rest / base;
+    ntiles = (head > 0 ? 1 : 0) + nfull + (tail_groups > 0 ? 1 : 0) +
+             (rest - tail_groups * base > 0 ? 1 : 0);
+  }
+  ScanParams S = scan_workspace(h, stream, ntiles);
+  S.n = n;
+  S.head = head;
+  S.nfull = nfull;
+  S.ntiles = ntiles;
+  S.spin_limit = spin_limit;
+  S.stall_tile = stall_tile;
+  S.groups = (uint32_t)groups;
+  S.tail_groups = (uint32_t)tail_groups;
+  unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, ntiles));
+  void* params[] = {args.data(), &S};
+  PYC_CU(drv().cuLaunchKernel(f, grid, 1, 1, (unsigned)threads, 1, 1, 0, stream, params,
+                              nullptr));
 }
 
 }  // namespace
@@ -97,6 +169,9 @@ PYC_API pyc_status pyc_scan_create(pyc_dtype dtype, const char* neutral, const c
       fail(PYC_E_ARG, "opts.items_per_thread must be 0, 1, 2 or 4");
     h->preamble = h->opts.preamble ? h->opts.preamble : "";
     h->opts.preamble = nullptr;
+    // PYC_CHECK_BOUNDS=1: build the bounds-checked kernel (debugging aid)
+    if (const char* c = std::getenv("PYC_CHECK_BOUNDS"))
+      if (c[0] == '1') h->preamble = "#define PYC_CHECK 1\n" + h->preamble;
     h->dtype = dtype;
     h->name = "scan";
     h->spec = parse_argspec(argspec);
@@ -164,6 +239,52 @@ PYC_API pyc_status pyc_scan_autotune(pyc_scan_t h, int64_t n, pyc_stream_t strea
     autotune_generic(*h, n, s, true,
                      [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc,
                          CUdeviceptr) { launch_scan(h, c, nt, p, sc, s); });
+  });
+}
+
+PYC_API pyc_status pyc_scan_launch_test(pyc_scan_t h, int64_t n, void* const* ptrs,
+                                        const void* scalars, pyc_stream_t stream,
+                                        int64_t stall_tile, int64_t spin_limit) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    LaunchCfg cfg = choose_cfg(*h, n, true);
+    launch_scan(h, cfg, n, ptrs, scalars, reinterpret_cast<CUstream>(stream), stall_tile,
+                spin_limit);
+  });
+}
+
+PYC_API pyc_status pyc_scan_sync(pyc_scan_t h, pyc_stream_t stream) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    CUstream s = reinterpret_cast<CUstream>(stream);
+    CUcontext ctx = ensure_context();
+    CUdeviceptr base = 0;
+    {
+      std::lock_guard<std::mutex> lk(h->ws_mu);
+      auto it = h->ws.find(std::make_pair(ctx, s));
+      if (it != h->ws.end()) base = it->second.base;
+    }
+    PYC_CU(drv().cuStreamSynchronize(s));
+    if (!base) return;
+    unsigned long long ctl[8] = {};
+    PYC_CU(drv().cuMemcpyDtoH(ctl, base, sizeof(ctl)));
+    if (ctl[4]) {
+      const unsigned long long zero[4] = {0, 0, 0, 0};
+      PYC_CU(drv().cuMemcpyHtoD(base + 32, zero, sizeof(zero)));
+      fail(PYC_E_INTERNAL, "scan bounds check " + std::to_string(ctl[4]) + " failed: index " +
+                               std::to_string((long long)ctl[5]) + ", tile " +
+                               std::to_string((long long)ctl[6]) + ", block " +
+                               std::to_string(ctl[7] >> 16) + ", thread " +
+                               std::to_string(ctl[7] & 0xffff));
+    }
+    const unsigned long long err = ctl[2];
+    if (err) {
+      // a CTA that gave up left without its share of the tile-counter reset
+      const unsigned long long zero[4] = {0, 0, 0, 0};
+      PYC_CU(drv().cuMemcpyHtoD(base, zero, sizeof(zero)));
+      fail(PYC_E_TIMEOUT, "a scan launch on this stream gave up waiting for a tile descriptor; "
+                          "its output is not valid");
+    }
   });
 }
 

@@ -99,6 +99,7 @@ EXPORTED = [
     "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
     "pyc_scan_create", "pyc_scan_launch", "pyc_scan_num_params", "pyc_scan_param",
     "pyc_scan_scalar_bytes", "pyc_scan_source", "pyc_scan_autotune", "pyc_scan_config", "pyc_scan_destroy",
+    "pyc_scan_sync", "pyc_scan_launch_test",
 ]
 
 _lib = None
@@ -146,6 +147,8 @@ def load(build_if_missing=True):
         "pyc_scan_create": (st, [i32, cp, cp, cp, cp, cp, ctypes.POINTER(pyc_opts),
                                  ctypes.POINTER(vp)]),
         "pyc_scan_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp]),
+        "pyc_scan_sync": (st, [vp, vp]),
+        "pyc_scan_launch_test": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, i64, i64]),
         "pyc_scan_num_params": (i32, [vp]),
         "pyc_scan_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
         "pyc_scan_scalar_bytes": (i32, [vp]),
@@ -287,6 +290,17 @@ def pyc_scan_create(dtype, neutral, scan_expr, input_expr, output_stmt, argspec,
 
 def pyc_scan_launch(h, n, ptrs, scalars=None, stream=None):
     _check(load().pyc_scan_launch(h, int(n), _ptr_array(ptrs), scalars, _stream(stream)))
+
+
+def pyc_scan_sync(h, stream=None):
+    """Synchronize `stream`; PycError(PYC_E_TIMEOUT) if a scan launch gave up a wait."""
+    _check(load().pyc_scan_sync(h, _stream(stream)))
+
+
+def pyc_scan_launch_test(h, n, ptrs, scalars=None, stream=None, stall_tile=-1,
+                         spin_limit=1 << 20):
+    _check(load().pyc_scan_launch_test(h, int(n), _ptr_array(ptrs), scalars, _stream(stream),
+                                       int(stall_tile), int(spin_limit)))
 
 
 def pyc_scan_autotune(h, n, stream=None):

@@ -49,6 +49,12 @@ SCANS = {
                             "int *x, long long *y"),
     "cummax_f32": (pyc.PYC_F32, "-INFINITY", "a > b ? a : b", "x[i]", "y[i] = item",
                    "float *x, float *y"),
+    # composition of v -> ca[i] v + cb[i] (mod 2^32), packed A << 32 | B: not commutative
+    "affine_u32": (pyc.PYC_U64, "1ull << 32",
+                   "((unsigned long long)((unsigned)(a >> 32) * (unsigned)(b >> 32)) << 32)"
+                   " | (unsigned)((unsigned)(b >> 32) * (unsigned)a + (unsigned)b)",
+                   "((unsigned long long)ca[i] << 32) | cb[i]", "y[i] = item",
+                   "unsigned *ca, unsigned *cb, unsigned long long *y"),
 }
 
 _handles = {}

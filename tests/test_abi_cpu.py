@@ -226,7 +226,7 @@ def test_scan_create_validation():
     assert p["x"]["lifted"] and p["x"]["read"] and not p["x"]["written"]
     assert p["y"]["lifted"] and p["y"]["written"] and not p["y"]["read"]
     src = pyc.pyc_scan_source(h)
-    assert "pyc_scan1_s" in src and "pyc_scan2_s" in src
+    assert "pyc_scan_s" in src and "pyc_lookback" in src
     pyc.pyc_scan_destroy(h)
     bad = [
         (pyc.PYC_BF16, "0", "a+b", "x[i]", "y[i] = item", "float *x, float *y"),

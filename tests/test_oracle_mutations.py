@@ -47,6 +47,7 @@ MUTATIONS = [
      "    s += (uint64_t)(int64_t)x[i];\n    if (exclusive) out[i] = (int64_t)s;"),
     ("scan records before adding", "    neumaier_add(&s, &c, (double)x[i]);\n    neumaier_add(&as, &ac, fabs((double)x[i]));\n    incl[i] = s + c;",
      "    incl[i] = s + c;\n    neumaier_add(&s, &c, (double)x[i]);\n    neumaier_add(&as, &ac, fabs((double)x[i]));"),
+    ("affine composed in the wrong order", "    B = a[i] * B + b[i];", "    B = B + A * b[i];"),
     ("scan drops compensation", "    incl[i] = s + c;\n    if (abs_prefix)", "    incl[i] = s;\n    if (abs_prefix)"),
     ("running max keeps the first", "    if (x[i] > m) m = x[i];\n    out[i] = m;",
      "    if (m == -INFINITY) m = x[i];\n    out[i] = m;"),

@@ -370,3 +370,36 @@ def test_scan_max_against_library():
     x = np.random.default_rng(22).standard_normal(4000).astype(np.float32)
     assert np.array_equal(oracle.scan_max_f32(x), np.maximum.accumulate(x))
     assert oracle.scan_max_f32(np.array([np.float32(-np.inf)]))[0] == -np.inf
+
+
+def test_scan_affine_composition():
+    """Prefix compositions of v -> a v + b (mod 2^32): the composed map applied
+    to a point equals iterating the maps one by one; a = 1 reduces to prefix
+    sums of b and b = 0 to prefix products of a."""
+    rng = np.random.default_rng(23)
+    n = 3000
+    a = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    b = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    out = oracle.scan_affine_u32(a, b)
+    A, B = (out >> np.uint64(32)).astype(np.uint64), (out & np.uint64(0xFFFFFFFF)).astype(np.uint64)
+    for v0 in (0, 1, 0x9E3779B9, 2 ** 32 - 1):
+        v = v0
+        for i in range(n):
+            v = (int(a[i]) * v + int(b[i])) % 2 ** 32
+            assert (int(A[i]) * v0 + int(B[i])) % 2 ** 32 == v
+    ones = np.ones(n, np.uint32)
+    out = oracle.scan_affine_u32(ones, b)
+    assert np.all(out >> np.uint64(32) == 1)
+    assert np.array_equal(out & np.uint64(0xFFFFFFFF), np.cumsum(b.astype(np.uint64)) % 2 ** 32)
+    out = oracle.scan_affine_u32(a, np.zeros(n, np.uint32))
+    assert np.all(out & np.uint64(0xFFFFFFFF) == 0)
+    assert np.array_equal(out >> np.uint64(32), np.array(_cumprod_mod32(a), np.uint64))
+
+
+def _cumprod_mod32(a):
+    r, p = [], 1
+    for v in a:
+        p = p * int(v) % 2 ** 32
+        r.append(p)
+    return r
+

@@ -102,3 +102,83 @@ def test_full_size_scan_sampled():
     yi = _scan("cumsum_excl_i32_i64", xi, out_dtype=torch.int64)
     assert np.array_equal(yi, oracle.scan_sum_i32_i64(xi, exclusive=True))
     torch.cuda.empty_cache()
+
+
+def _affine_inputs(seed, n):
+    rng = np.random.default_rng(seed)
+    a = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    b = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    return a, b
+
+
+def _u32_dev(a):
+    return torch.from_numpy(a.view(np.int32)).cuda()
+
+
+@pytest.mark.parametrize("vec,unroll,block", [(None, None, None), (16, 1, 32), (32, 4, 512),
+                                              (16, 2, 160), (32, 1, 64)])
+def test_noncommutative_scan_order(vec, unroll, block):
+    """Composition of affine maps: any operand swapped in the warp scans, the
+    block step or the look-back fold changes the result."""
+    o = {} if vec is None else dict(vec_bytes=vec, items_per_thread=unroll, block=block)
+    h = stock.create("affine_u32", **o)
+    for n in (1, 2, 33, 4097, 200003, 3 * (1 << 20) + 5):
+        a, b = _affine_inputs(n, n)
+        da, db = _u32_dev(a), _u32_dev(b)
+        dy = torch.zeros(n, dtype=torch.int64, device="cuda")
+        pyc.pyc_scan_launch(h, n, [da.data_ptr(), db.data_ptr(), dy.data_ptr()], None, _s())
+        pyc.pyc_scan_sync(h, _s())
+        assert np.array_equal(dy.cpu().numpy().view(np.uint64), oracle.scan_affine_u32(a, b)), n
+
+
+def test_noncommutative_scan_misaligned():
+    """Arrays that share no vector alignment: every tile takes the ragged path."""
+    h = stock.create("affine_u32")
+    n = 100000
+    a, b = _affine_inputs(7, n + 8)
+    da, db = _u32_dev(a), _u32_dev(b)
+    for oa, ob in ((1, 0), (0, 3), (2, 2), (3, 1)):
+        dy = torch.zeros(n, dtype=torch.int64, device="cuda")
+        pyc.pyc_scan_launch(h, n, [da.data_ptr() + 4 * oa, db.data_ptr() + 4 * ob, dy.data_ptr()],
+                            None, _s())
+        pyc.pyc_scan_sync(h, _s())
+        want = oracle.scan_affine_u32(a[oa:oa + n], b[ob:ob + n])
+        assert np.array_equal(dy.cpu().numpy().view(np.uint64), want), (oa, ob)
+
+
+def test_repeated_launches_and_growth():
+    """Back-to-back launches reuse the descriptors (a new epoch each); a larger
+    n grows the workspace."""
+    h = stock.create("cumsum_excl_i32_i64")
+    for n in (5000, 5000, 1 << 22, 777, 1 << 24, 1 << 24):
+        x = inputs.int_uniform_i32(40, n % 7, n)
+        dx = torch.from_numpy(x).cuda()
+        dy = torch.empty(n, dtype=torch.int64, device="cuda")
+        pyc.pyc_scan_launch(h, n, [dx.data_ptr(), dy.data_ptr()], None, _s())
+        pyc.pyc_scan_sync(h, _s())
+        assert np.array_equal(dy.cpu().numpy(), oracle.scan_sum_i32_i64(x, exclusive=True)), n
+
+
+def test_wait_gives_up_and_reports():
+    """A tile that publishes nothing: the next tile's wait runs out after
+    spin_limit polls, the launch completes, pyc_scan_sync reports
+    PYC_E_TIMEOUT, and the next launch on the stream is correct."""
+    h = pyc.pyc_scan_create(pyc.PYC_I64, "0", "a+b", "(long long)x[i]", "y[i] = item",
+                            "int *x, long long *y", {"vec_bytes": 16, "items_per_thread": 1,
+                                                     "block": 128})
+    try:
+        n = 1 << 20
+        x = inputs.int_uniform_i32(41, 0, n)
+        dx = torch.from_numpy(x).cuda()
+        dy = torch.empty(n, dtype=torch.int64, device="cuda")
+        ptrs = [dx.data_ptr(), dy.data_ptr()]
+        pyc.pyc_scan_launch_test(h, n, ptrs, None, _s(), stall_tile=1, spin_limit=1 << 12)
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_scan_sync(h, _s())
+        assert e.value.status == pyc.PYC_E_TIMEOUT
+        pyc.pyc_scan_sync(h, _s())  # the error was cleared
+        pyc.pyc_scan_launch(h, n, ptrs, None, _s())
+        pyc.pyc_scan_sync(h, _s())
+        assert np.array_equal(dy.cpu().numpy(), oracle.scan_sum_i32_i64(x))
+    finally:
+        pyc.pyc_scan_destroy(h)
