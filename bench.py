@@ -477,6 +477,36 @@ def profile_reduce(args):
                       "note": "profiling driver, not a bench value"}))
 
 
+def profile_scan(args):
+    """Profiling driver (not a bench line): one stock scan at n = 2^n_log2,
+    warm-up then `steps` launches, for ncu captures of a single kernel."""
+    import torch
+    from paper_1304_5553_gb300 import inputs, pyc, stock
+    torch.cuda.set_device(0)
+    n = N_MAP
+    name = args.profile_scan
+    if "i32" in name:
+        x = torch.from_numpy(inputs.int_uniform_i32(0, 0, n)).cuda()
+        y = torch.empty(n, dtype=torch.int64, device="cuda")
+    else:
+        x = torch.from_numpy(inputs.uniform_f32(0, 0, n, -1.0, 1.0)).cuda()
+        y = torch.empty(n, dtype=torch.float32, device="cuda")
+    opts = {}
+    if args.config:  # vecV_uU_bB: a fixed launch configuration (no tuning launches)
+        v, u, b = (int(q[1:] if q[0] in "ub" else q[3:]) for q in args.config.split("_"))
+        opts = dict(vec_bytes=v, items_per_thread=u, block=b)
+    h = stock.create(name, **opts)
+    s = torch.cuda.current_stream().cuda_stream
+    if args.autotune == "on" and not opts:
+        pyc.pyc_scan_autotune(h, n, s)
+    print("config vec%d_u%d_b%d" % pyc.launch_config(h, n, reduce="scan"), file=sys.stderr)
+    f = lambda: pyc.pyc_scan_launch(h, n, [x.data_ptr(), y.data_ptr()], None, s)
+    ms = _time_fn(torch, f, args.steps, warmup=args.warmup)
+    pyc.pyc_scan_sync(h, s)
+    print(json.dumps({"profile_scan": name, "n": n, "us": round(ms * 1e3, 2),
+                      "note": "profiling driver, not a bench value"}))
+
+
 def run_gpu(args):
     import torch
     from paper_1304_5553_gb300 import pyc, stock
@@ -613,6 +643,10 @@ def main():
     ap.add_argument("--n-log2", type=int, default=28, help="map size (profiling captures only)")
     ap.add_argument("--profile-reduce", default="",
                     help="profiling driver: time one stock reduction only (not a bench line)")
+    ap.add_argument("--profile-scan", default="",
+                    help="profiling driver: time one stock scan only (not a bench line)")
+    ap.add_argument("--config", default="",
+                    help="with --profile-scan: fixed launch configuration, e.g. vec32_u4_b512")
     ap.add_argument("--autotune", default="on", choices=["on", "off"],
                     help="off: use the tuning cache / defaults without timing candidates")
     args = ap.parse_args()
@@ -624,6 +658,8 @@ def main():
         run_reference(args)
     elif args.profile_reduce:
         profile_reduce(args)
+    elif args.profile_scan:
+        profile_scan(args)
     else:
         run_gpu(args)
 

@@ -164,6 +164,57 @@ __device__ __forceinline__ void pyc_stg(void* d, const void* s) {
     pyc_vio<P>::st(reinterpret_cast<char*>(d) + j * P, reinterpret_cast<const char*>(s) + j * P);
 }
 
+// Accesses with an L2 cache policy (createpolicy): 16- and 32-byte pieces.
+template <int B> struct pyc_vioh;
+template <> struct pyc_vioh<16> {
+  static __device__ __forceinline__ void ld(void* d, const void* s, unsigned long long pol) {
+    unsigned* r = reinterpret_cast<unsigned*>(d);
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "l"(s), "l"(pol));
+  }
+  static __device__ __forceinline__ void st(void* d, const void* s, unsigned long long pol) {
+    const unsigned* r = reinterpret_cast<const unsigned*>(s);
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;"
+                 :: "l"(d), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "l"(pol) : "memory");
+  }
+};
+template <> struct pyc_vioh<32> {
+  static __device__ __forceinline__ void ld(void* d, const void* s, unsigned long long pol) {
+    unsigned* r = reinterpret_cast<unsigned*>(d);
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]),
+                   "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "l"(s), "l"(pol));
+  }
+  static __device__ __forceinline__ void st(void* d, const void* s, unsigned long long pol) {
+    const unsigned* r = reinterpret_cast<const unsigned*>(s);
+    asm volatile("st.global.L2::cache_hint.v8.u32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8}, %9;"
+                 :: "l"(d), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]),
+                    "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "l"(pol) : "memory");
+  }
+};
+template <int G, int P>
+__device__ __forceinline__ void pyc_ldgh(void* d, const void* s, unsigned long long pol) {
+#pragma unroll
+  for (int j = 0; j < G / P; ++j)
+    pyc_vioh<P>::ld(reinterpret_cast<char*>(d) + j * P, reinterpret_cast<const char*>(s) + j * P, pol);
+}
+template <int G, int P>
+__device__ __forceinline__ void pyc_stgh(void* d, const void* s, unsigned long long pol) {
+#pragma unroll
+  for (int j = 0; j < G / P; ++j)
+    pyc_vioh<P>::st(reinterpret_cast<char*>(d) + j * P, reinterpret_cast<const char*>(s) + j * P, pol);
+}
+__device__ __forceinline__ unsigned long long pyc_policy_keep() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long pyc_policy_drop() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 // Word-wise shuffle / L2 load of any trivially copyable 4-byte-multiple type.
 template <typename T>
 union pyc_words {
@@ -334,6 +385,49 @@ std::string buf_load(const ArgSpec& spec, const char* prefix, const std::string&
   return o.str();
 }
 
+// buf_load for the lifted arrays `code` reads (rewritten form).
+std::string buf_load_used(const ArgSpec& spec, const char* prefix, const std::string& base,
+                          const std::string& code) {
+  std::ostringstream o;
+  o << "#pragma unroll\n    for (int pyc_u = 0; pyc_u < U; ++pyc_u) {\n"
+    << "      const pyc_i64 pyc_e0 = (" << base << ") + (pyc_i64)pyc_u * pyc_step;\n";
+  for (auto& p : spec.params) {
+    if (!(p.is_ptr && p.lifted && p.read)) continue;
+    if (code.find("pyc_r_" + p.name + " ") == std::string::npos &&
+        code.find("pyc_r_" + p.name + "[") == std::string::npos)
+      continue;
+    o << "      pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&" << prefix << p.name
+      << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
+  }
+  o << "    }\n";
+  return o.str();
+}
+
+// Scan sweep 1: fold the rows of one step (RU rows from `base`) into pyc_wagg
+// in element order; `rag` guards every element with i < te.
+std::string fold_rows(const std::string& input_expr, const std::string& base, bool rag) {
+  std::ostringstream o;
+  o << "#pragma unroll\n      for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {\n"
+    << "        pyc_acc_t pyc_v = pyc_neutral();\n"
+    << "#pragma unroll\n        for (int pyc_e = 0; pyc_e < E; ++pyc_e) {\n"
+    << "          const int pyc_k = pyc_u * E + pyc_e;\n"
+    << "          const pyc_i64 i = (" << base << ") + (pyc_i64)pyc_u * (32 * E) + pyc_e;\n"
+    << "          (void)i;\n"
+    << "          pyc_acc_t pyc_x = pyc_neutral();\n"
+    << "          " << (rag ? "if (i < te) " : "") << "pyc_x = (pyc_acc_t)(" << input_expr
+    << ");\n"
+    << "          pyc_v = pyc_e == 0 ? pyc_x : pyc_combine(pyc_v, pyc_x);\n"
+    << "        }\n"
+    << "        // ordered fold across the row: lane 0 ends with lanes 0..31 in order\n"
+    << "#pragma unroll\n        for (int d = 1; d < 32; d <<= 1) {\n"
+    << "          const pyc_acc_t o = pyc_shfl_down(pyc_v, d);\n"
+    << "          if (lane + d < 32) pyc_v = pyc_combine(pyc_v, o);\n"
+    << "        }\n"
+    << "        pyc_wagg = pyc_combine(pyc_wagg, pyc_v);\n"
+    << "      }\n";
+  return o.str();
+}
+
 std::string buf_refs(const ArgSpec& spec, const char* prefix) {
   std::ostringstream o;
   for (auto& p : spec.params)
@@ -394,6 +488,23 @@ std::string scalar_stores_k(const ArgSpec& spec) {
     if (p.is_ptr && p.lifted && p.written)
       o << "            " << p.name << "[i] = pyc_r_" << p.name << "[pyc_k];\n";
   return o.str();
+}
+
+// The same loads / stores with an L2 cache policy `pol` (pyc_ldgh / pyc_stgh).
+std::string with_policy(const std::string& code, const std::string& pol) {
+  std::string out, line;
+  std::istringstream in(code);
+  while (std::getline(in, line)) {
+    for (const char* f : {"pyc_ldg<", "pyc_stg<"}) {
+      size_t k = line.find(f);
+      if (k == std::string::npos) continue;
+      line.insert(k + 7, "h");
+      size_t e = line.rfind(");");
+      if (e != std::string::npos) line.insert(e, ", " + pol);
+    }
+    out += line + "\n";
+  }
+  return out;
 }
 
 std::string scalar_io(const ArgSpec& spec, bool load) {
@@ -1030,42 +1141,98 @@ __device__ __noinline__ bool pyc_check_fail(const pyc_scan_params& S, const pyc_
 #define PYC_OK(S, idx, cnt, bound, code, t) true
 #endif
 
+// Descriptors of 4-byte values are packed: one 64-bit word per tile holding
+// (epoch << 2 | state) << 32 | value, written and read with single 64-bit
+// accesses (atomic), so a reader that sees the state sees its value.  Wider
+// values keep the state in flag[t] and the value in agg[t] / inc[t], ordered
+// by release / acquire.
+#define PYC_PACKED (sizeof(pyc_acc_t) == 4)
 __device__ __forceinline__ void pyc_publish(const pyc_scan_params& S, const pyc_i64 t,
                                             const unsigned state, const pyc_acc_t v) {
   if (t == S.stall_tile) return;
   if (!PYC_OK(S, t, 1, S.ntiles, 31, t)) return;
-  if (state == 1u) S.agg[t] = v;
-  else S.inc[t] = v;
-  pyc_st_release(S.flag + t, (S.epoch << 2) | state);
+  if constexpr (PYC_PACKED) {
+    pyc_words<pyc_acc_t> u;
+    u.t = v;
+    const unsigned long long word =
+        ((unsigned long long)((S.epoch << 2) | state) << 32) | (unsigned long long)u.w[0];
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;"
+                 ::"l"(reinterpret_cast<unsigned long long*>(S.flag) + t), "l"(word) : "memory");
+  } else {
+    if (state == 1u) S.agg[t] = v;
+    else S.inc[t] = v;
+    pyc_st_release(S.flag + t, (S.epoch << 2) | state);
+  }
 }
 
-// Exclusive prefix of tile t > 0 by warp 0: look back over the descriptors of
-// tiles t-1, t-2, ... 32 at a time (lane l reads tile j-l) until a window holds
-// an inclusive prefix; the aggregates after it are combined in tile order.
-// Every tile below t was handed out before t, so its CTA is running and
-// publishes without waiting on this one.  The wait is bounded: after
-// spin_limit polls (or once another CTA of the same launch has given up) the
-// error word is set and the neutral element is returned.
-__device__ pyc_acc_t pyc_lookback(const pyc_scan_params& S, const pyc_i64 t) {
+// Exclusive prefix of tile t > 0, computed by one warp: look back over the
+// descriptors of tiles t-1, t-2, ... in windows of 32 lanes x PYC_LB_K tiles
+// (lane l reads the aligned group of PYC_LB_K descriptors l groups below the
+// one holding t-1, flags with one relaxed vector load and an acquire fence)
+// until a window holds an inclusive prefix with every tile after it
+// published; the aggregates after it are combined in tile order.  Every tile
+// below t was handed out before t, so its CTA is running and publishes
+// without waiting on this one.  The wait is bounded: after spin_limit polls
+// (or once another CTA of the same launch has given up) the error word is set
+// and the neutral element is returned.
+#define PYC_LB_K 4
+__device__ __noinline__ pyc_acc_t pyc_lookback(const pyc_scan_params& S, const pyc_i64 t) {
+  constexpr int K = PYC_LB_K;
   const int lane = threadIdx.x & 31;
   const unsigned want = S.epoch;
   pyc_acc_t run = pyc_neutral();
-  pyc_i64 j = t - 1;
+  pyc_i64 g0 = (t - 1) / K;
   pyc_i64 polls = 0;
   for (;;) {
-    const pyc_i64 q = j - lane;
-    unsigned st;
+    const pyc_i64 g = g0 - lane;
+    unsigned st[K];  // 0: not published, 1: aggregate, 2: inclusive prefix, 3: not a predecessor
+    unsigned val[K];  // packed descriptors: the value bits
+    bool has_p, x_above;
+    int jp;
     for (;;) {
-      st = 2u;  // below tile 0: treated as an inclusive prefix never selected
-      if (q >= 0 && PYC_OK(S, q, 1, S.ntiles, 32, t)) {
-        const unsigned f = pyc_ld_acquire(S.flag + q);
-        st = (f >> 2) == want ? (f & 3u) : 0u;
+      if (g >= 0 && PYC_OK(S, g * K, K, S.ntiles + K - 1, 32, t)) {
+        unsigned f[K];
+        if constexpr (PYC_PACKED) {
+          unsigned long long d[K];
+          asm volatile("ld.relaxed.gpu.global.v4.b64 {%0,%1,%2,%3}, [%4];"
+                       : "=l"(d[0]), "=l"(d[1]), "=l"(d[2]), "=l"(d[3])
+                       : "l"(reinterpret_cast<const unsigned long long*>(S.flag) + g * K)
+                       : "memory");
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            f[j] = (unsigned)(d[j] >> 32);
+            val[j] = (unsigned)d[j];
+          }
+        } else {
+          asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(f[0]), "=r"(f[1]), "=r"(f[2]), "=r"(f[3]) : "l"(S.flag + g * K)
+                       : "memory");
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+          st[j] = g * K + j >= t ? 3u : ((f[j] >> 2) == want ? (f[j] & 3u) : 0u);
+      } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) st[j] = 2u;  // below tile 0: never selected
       }
-      // done once every tile after the nearest inclusive prefix has published
-      // (or all 32 have): tiles further back are not needed
-      const unsigned xm = __ballot_sync(0xffffffffu, st == 0u);
-      const unsigned pm0 = __ballot_sync(0xffffffffu, st == 2u);
-      if (xm == 0u || (pm0 != 0u && (xm & ((2u << (__ffs(pm0) - 1)) - 1u)) == 0u)) break;
+      // from the top of the lane's group down: the first inclusive prefix, and
+      // whether a tile above it has not published yet
+      has_p = false;
+      x_above = false;
+      jp = 0;
+#pragma unroll
+      for (int j = K - 1; j >= 0; --j) {
+        if (has_p || st[j] == 3u) continue;
+        if (st[j] == 2u) {
+          has_p = true;
+          jp = j;
+        } else if (st[j] == 0u) {
+          x_above = true;
+        }
+      }
+      const unsigned pm = __ballot_sync(0xffffffffu, has_p);
+      const unsigned xm = __ballot_sync(0xffffffffu, x_above);
+      if (pm ? (xm & ((2u << (__ffs(pm) - 1)) - 1u)) == 0u : xm == 0u) break;
       ++polls;
       bool give_up = polls > S.spin_limit;
       if ((polls & 63) == 0)
@@ -1079,12 +1246,29 @@ __device__ pyc_acc_t pyc_lookback(const pyc_scan_params& S, const pyc_i64 t) {
       }
       __nanosleep(32);
     }
-    const unsigned pm = __ballot_sync(0xffffffffu, st == 2u);
+    if constexpr (!PYC_PACKED) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    const unsigned pm = __ballot_sync(0xffffffffu, has_p);
     const int p = pm ? __ffs(pm) - 1 : 31;
     pyc_acc_t v = pyc_neutral();
-    if (q >= 0 && lane <= p && PYC_OK(S, q, 1, S.ntiles, 33, t))
-      v = st == 2u ? pyc_ld_cg(S.inc + q) : pyc_ld_cg(S.agg + q);
-    // ordered fold: lane p (earliest tile) first, lane 0 (tile j) last
+    if (lane <= p && g >= 0) {
+      // this lane's tiles from its first inclusive prefix (lane p) or its lowest
+      // tile (lanes above p) up to its top, in tile order
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        if (st[j] == 3u || (lane == p && j < jp)) continue;
+        if (!PYC_OK(S, g * K + j, 1, S.ntiles, 33, t)) continue;
+        pyc_acc_t d;
+        if constexpr (PYC_PACKED) {
+          pyc_words<pyc_acc_t> u;
+          u.w[0] = val[j];
+          d = u.t;
+        } else {
+          d = st[j] == 2u ? pyc_ld_cg(S.inc + g * K + j) : pyc_ld_cg(S.agg + g * K + j);
+        }
+        v = pyc_combine(v, d);
+      }
+    }
+    // ordered fold: lane p (earliest tiles) first, lane 0 (tile t-1) last
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const pyc_acc_t o = pyc_shfl_down(v, d);
@@ -1092,7 +1276,7 @@ __device__ pyc_acc_t pyc_lookback(const pyc_scan_params& S, const pyc_i64 t) {
     }
     run = pyc_combine(pyc_shfl_idx(v, 0), run);
     if (pm) return run;
-    j -= 32;
+    g0 -= 32;
   }
 }
 
@@ -1145,14 +1329,16 @@ __device__ __forceinline__ pyc_acc_t pyc_sweep1(const pyc_args& pyc_p, const pyc
   o << aliases(spec, "pyc_p");
   o << R"PYC(  (void)te;
   const pyc_i64 pyc_wb = ts + (pyc_i64)w * G * (U * 32 * E) + (pyc_i64)lane * E;
+  // the tile is read again by sweep 2: keep it in L2
+  const unsigned long long pyc_pk = pyc_policy_keep();
   pyc_acc_t pyc_wagg = pyc_neutral();
   const int pyc_steps = G * (U / RU);
-  for (int pyc_g = 0; pyc_g < pyc_steps; ++pyc_g) {
-    const pyc_i64 pyc_gb = pyc_wb + (pyc_i64)pyc_g * (RU * 32 * E);
+  if constexpr (RAG) {
+    for (int pyc_g = 0; pyc_g < pyc_steps; ++pyc_g) {
+      const pyc_i64 pyc_gb = pyc_wb + (pyc_i64)pyc_g * (32 * E);
 )PYC";
   o << reg_decls(spec, "T");
-  o << R"PYC(    if constexpr (RAG) {
-#pragma unroll
+  o << R"PYC(#pragma unroll
       for (int pyc_k = 0; pyc_k < T; ++pyc_k) {
         const pyc_i64 i = pyc_gb + pyc_k;
         if (i < te) {
@@ -1161,35 +1347,35 @@ __device__ __forceinline__ pyc_acc_t pyc_sweep1(const pyc_args& pyc_p, const pyc
     << "          }\n";
   o << R"PYC(        }
       }
-    } else {
-#pragma unroll
-      for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
-        const pyc_i64 pyc_e0 = pyc_gb + (pyc_i64)pyc_u * (32 * E);
 )PYC";
-  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 11, t)) {\n" << group_loads_used(spec, input_expr)
-    << "        }\n";
-  o << R"PYC(      }
-    }
-#pragma unroll
-    for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
-      pyc_acc_t pyc_v = pyc_neutral();
-#pragma unroll
-      for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
-        const int pyc_k = pyc_u * E + pyc_e;
-        const pyc_i64 i = pyc_gb + (pyc_i64)pyc_u * (32 * E) + pyc_e;
-        (void)i;
-        pyc_acc_t pyc_x = pyc_neutral();
-        if (!RAG || i < te) pyc_x = (pyc_acc_t)()PYC" << input_expr << R"PYC();
-        pyc_v = pyc_e == 0 ? pyc_x : pyc_combine(pyc_v, pyc_x);
-      }
-      // ordered fold across the row: lane 0 ends with lanes 0..31 in order
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const pyc_acc_t o = pyc_shfl_down(pyc_v, d);
-        if (lane + d < 32) pyc_v = pyc_combine(pyc_v, o);
-      }
-      pyc_wagg = pyc_combine(pyc_wagg, pyc_v);
-    }
+  o << fold_rows(input_expr, "pyc_gb", true);
+  o << R"PYC(    }
+  } else {
+    // two register buffers: the rows of group g+1 load while group g folds
+    const pyc_i64 pyc_step = 32 * E;
+    constexpr int pyc_gs = U * 32 * E;  // elements between a warp's row groups
+)PYC";
+  o << buf_decls(spec, "pyc_a_", "T") << buf_decls(spec, "pyc_b_", "T");
+  auto load = [&](const char* prefix, const std::string& base) {
+    std::string l = buf_load_used(spec, prefix, base, input_expr);
+    return "    if (PYC_OK(S, " + base + ", pyc_gs - 31 * E, S.n, 11, t)) {\n" +
+           with_policy(l, "pyc_pk") + "    }\n";
+  };
+  o << load("pyc_a_", "pyc_wb");
+  o << R"PYC(    for (int pyc_g = 0; pyc_g < pyc_steps; pyc_g += 2) {
+      const pyc_i64 pyc_gb = pyc_wb + (pyc_i64)pyc_g * pyc_gs;
+      if (pyc_g + 1 < pyc_steps) {
+)PYC";
+  o << load("pyc_b_", "pyc_gb + pyc_gs");
+  o << "      }\n      {\n" << buf_refs(spec, "pyc_a_") << fold_rows(input_expr, "pyc_gb", false)
+    << "      }\n";
+  o << R"PYC(      if (pyc_g + 1 < pyc_steps) {
+        if (pyc_g + 2 < pyc_steps) {
+)PYC";
+  o << load("pyc_a_", "pyc_gb + 2 * pyc_gs");
+  o << "        }\n        {\n" << buf_refs(spec, "pyc_b_")
+    << fold_rows(input_expr, "pyc_gb + pyc_gs", false) << "        }\n      }\n";
+  o << R"PYC(    }
   }
   return pyc_wagg;
 }
@@ -1207,6 +1393,8 @@ __device__ __forceinline__ void pyc_sweep2(const pyc_args& pyc_p, const pyc_scan
   o << aliases(spec, "pyc_p");
   o << R"PYC(  (void)te;
   const pyc_i64 pyc_wb = ts + (pyc_i64)w * G * (U * 32 * E) + (pyc_i64)lane * E;
+  // the last use of the input, and output that is not read here: evict first
+  const unsigned long long pyc_pd = pyc_policy_drop();
   const int pyc_steps = G * (U / RU);
   for (int pyc_g = 0; pyc_g < pyc_steps; ++pyc_g) {
     const pyc_i64 pyc_gb = pyc_wb + (pyc_i64)pyc_g * (RU * 32 * E);
@@ -1227,7 +1415,8 @@ __device__ __forceinline__ void pyc_sweep2(const pyc_args& pyc_p, const pyc_scan
       for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
         const pyc_i64 pyc_e0 = pyc_gb + (pyc_i64)pyc_u * (32 * E);
 )PYC";
-  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 22, t)) {\n" << group_io(spec, true) << "        }\n";
+  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 22, t)) {\n"
+    << with_policy(group_io(spec, true), "pyc_pd") << "        }\n";
   o << R"PYC(      }
     }
 #pragma unroll
@@ -1272,7 +1461,8 @@ __device__ __forceinline__ void pyc_sweep2(const pyc_args& pyc_p, const pyc_scan
       for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
         const pyc_i64 pyc_e0 = pyc_gb + (pyc_i64)pyc_u * (32 * E);
 )PYC";
-  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 24, t)) {\n" << group_io(spec, false) << "        }\n";
+  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 24, t)) {\n"
+    << with_policy(group_io(spec, false), "pyc_pd") << "        }\n";
   o << R"PYC(      }
     }
   }

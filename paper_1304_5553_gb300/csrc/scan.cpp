@@ -46,12 +46,13 @@ constexpr int64_t kDefaultSpinLimit = 1 << 20;   // about a second of polling
 int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 
 // Row groups per warp in a vector tile.  A tile is read twice (fold, then
-// scan), the second time from L2, so the tiles in flight (one per resident
-// CTA) should fit in about 3/8 of L2; within that, tiles are made as large as
-// possible (fewer look-backs) while leaving at least four tiles per CTA.
+// scan), the second time from L2, and a CTA holds two tiles' input and one
+// tile's output at a time, so one tile's input is kept to 3/16 of L2 over the
+// resident CTAs; within that, tiles are made as large as possible (fewer
+// look-backs) while leaving at least four tiles per CTA.
 int scan_groups(int64_t n, int64_t base, int resident, int elem_bytes, int64_t l2_bytes) {
   int64_t want = n / (4 * (int64_t)resident);
-  if (elem_bytes > 0) want = std::min<int64_t>(want, l2_bytes * 3 / 8 / resident / elem_bytes);
+  if (elem_bytes > 0) want = std::min<int64_t>(want, l2_bytes * 3 / 16 / resident / elem_bytes);
   return (int)std::max<int64_t>(1, std::min<int64_t>(64, want / base));
 }
 
@@ -62,7 +63,9 @@ ScanParams scan_workspace(pyc_scan* h, CUstream stream, int64_t ntiles) {
   std::lock_guard<std::mutex> lk(h->ws_mu);
   pyc_scan::Workspace& w = h->ws[std::make_pair(ctx, stream)];
   const int64_t acc = h->gen.acc_bytes;
-  auto flag_bytes = [](int64_t cap) { return align256(cap * 4); };
+  // descriptors (4-byte flags, or 8-byte packed words) are read in aligned
+  // groups of four: cap is a multiple of 64
+  auto flag_bytes = [](int64_t cap) { return align256(cap * 8); };
   if (ntiles > w.cap) {
     if (w.base) {
       // a launch in flight on this stream may still use the old descriptors
@@ -71,7 +74,7 @@ ScanParams scan_workspace(pyc_scan* h, CUstream stream, int64_t ntiles) {
       w.base = 0;
       w.cap = 0;
     }
-    int64_t cap = std::max<int64_t>(4096, ntiles);
+    int64_t cap = std::max<int64_t>(4096, (ntiles + 63) / 64 * 64);
     int64_t bytes = kCtlBytes + flag_bytes(cap) + 2 * align256(cap * acc);
     PYC_CU(drv().cuMemAlloc(&w.base, (size_t)bytes));
     PYC_CU(drv().cuMemsetD8Async(w.base, 0, (size_t)(kCtlBytes + flag_bytes(cap)), stream));
