@@ -236,9 +236,9 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
 
 
 def bench_scans(torch, pyc, stock, dev, reps=10):
-    """n = 2^28 prefix scans (Sec. 3.2.6): two launches per scan.  GB/s counts the
-    algorithmic bytes (input read once, output written once); the two-pass
-    design reads the input twice, so its traffic is (2 in + 1 out) per element."""
+    """n = 2^28 prefix scans (Sec. 3.2.6), one single-pass launch each.  GB/s
+    counts the algorithmic bytes: input read once, output written once (the
+    kernel's second read of a tile is served by L2)."""
     from paper_1304_5553_gb300 import inputs
     n = N_MAP
     res = {}
@@ -247,10 +247,10 @@ def bench_scans(torch, pyc, stock, dev, reps=10):
     xi = torch.from_numpy(inputs.int_uniform_i32(0, 0, n)).to(dev)
     yf = torch.empty(n, dtype=torch.float32, device=dev)
     yi = torch.empty(n, dtype=torch.int64, device=dev)
-    cases = [("cumsum_f32", xf, yf, 8, 12), ("cummax_f32", xf, yf, 8, 12),
-             ("cumsum_excl_i32_i64", xi, yi, 12, 16)]
+    cases = [("cumsum_f32", xf, yf, 8), ("cummax_f32", xf, yf, 8),
+             ("cumsum_excl_i32_i64", xi, yi, 12)]
     peak, kind = peaks()
-    for name, x, y, bpe, traffic in cases:
+    for name, x, y, bpe in cases:
         h = stock.create(name)
         pyc.pyc_scan_autotune(h, n, s)
         f = (lambda h=h, x=x, y=y: pyc.pyc_scan_launch(h, n, [x.data_ptr(), y.data_ptr()], None, s))
@@ -258,7 +258,7 @@ def bench_scans(torch, pyc, stock, dev, reps=10):
         gbs = bpe * n / (ms * 1e-3) / 1e9
         res[name] = {"n": n, "us": round(ms * 1e3, 2), "GB/s": round(gbs, 1),
                      "frac_of_%s_peak" % kind: round(gbs / peak, 4),
-                     "two_pass_bytes_per_elem": traffic,
+                     "bytes_per_elem": bpe,
                      "config": "vec%d_u%d_b%d" % pyc.launch_config(h, n, reduce="scan")}
     del xf, xi, yf, yi
     torch.cuda.empty_cache()

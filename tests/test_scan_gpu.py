@@ -24,11 +24,18 @@ def _scan(name, x, n=None, out_dtype=torch.float32, **opts):
     return dy.cpu().numpy()
 
 
-def _depth_bound(n):
-    """Worst-case depth of the addition tree behind one prefix: rows of a chunk
-    scanned one after another (at most n / (152 CTAs x 32 threads x 4 elements)),
-    plus the per-thread runs, warp and block trees of both passes (< 256)."""
-    return 256 + n // (152 * 32 * 4)
+def _depth_bound(h, n, elem_bytes=4):
+    """Worst-case depth of the addition tree behind one binary32 prefix for the
+    launch configuration of n.  Within a tile: a lane's run of E elements, the
+    5-level warp fold or scan of a row, at most R = 64*U rows of a warp, the
+    warp-prefix scan (<= 5).  Across tiles: an inclusive prefix is an earlier
+    one plus the aggregates after it, folded per lane (<= 3), across the warp
+    (5), window after window (<= 1 per window) and with its own aggregate (1):
+    <= 11 levels per hop, at most tau hops (tau = number of tiles)."""
+    vec, unroll, block = pyc.launch_config(h, n, reduce="scan")
+    e = vec // elem_bytes
+    tau = -(-n // (block * e * unroll)) + 2
+    return 11 * tau + 2 * (e + 5 + 64 * unroll + 5) + 10
 
 
 def test_integer_valued_floats_are_exact():
@@ -73,7 +80,8 @@ def test_float_scan_within_bound():
         x = inputs.uniform_f32(33, 0, n, -1.0, 1.0)
         y = _scan("cumsum_f32", x).astype(np.float64)
         ref, ab = oracle.scan_sum_f32(x)
-        assert np.all(np.abs(y - ref) <= _depth_bound(n) * U * ab + 1e-30)
+        d = _depth_bound(stock.create("cumsum_f32"), n)
+        assert np.all(np.abs(y - ref) <= d * U * ab * (1 + 1e-6) + 1e-30)
 
 
 def test_in_place_scan():
@@ -97,7 +105,7 @@ def test_full_size_scan_sampled():
     ref, ab = oracle.scan_sum_f32(x)
     idx = np.concatenate([np.arange(0, n, 4096), np.arange(n - 4096, n)])
     err = np.abs(y[idx].astype(np.float64) - ref[idx])
-    assert np.all(err <= _depth_bound(n) * U * ab[idx])
+    assert np.all(err <= _depth_bound(stock.create("cumsum_f32"), n) * U * ab[idx] * (1 + 1e-6))
     xi = inputs.int_uniform_i32(35, 1, n)
     yi = _scan("cumsum_excl_i32_i64", xi, out_dtype=torch.int64)
     assert np.array_equal(yi, oracle.scan_sum_i32_i64(xi, exclusive=True))
