@@ -265,6 +265,39 @@ def bench_scans(torch, pyc, stock, dev, reps=10):
     return res
 
 
+def bench_fused(torch, dev, reps=10):
+    """GPUArray-style expressions at n = 2^28 (Sec. 3.2.4): fused into one kernel
+    vs evaluated operator by operator (one kernel and one temporary per node).
+    GB/s counts the fused pass's algorithmic bytes for both."""
+    from paper_1304_5553_gb300 import gpuarray as ga
+    from paper_1304_5553_gb300 import inputs
+    n = N_MAP
+    res = {}
+    arrs = [torch.from_numpy(inputs.uniform_f32(1, s, n, -2.0, 2.0)).to(dev) for s in range(4)]
+    X, Y, U, W = (ga.GArray(a) for a in arrs)
+    out = ga.GArray(torch.empty(n, dtype=torch.float32, device=dev))
+    cases = [("x*exp(-y*y)+sin(u)*w", lambda: X * ga.exp(-(Y * Y)) + ga.sin(U) * W, 20),
+             ("2.5*x-0.75*y", lambda: 2.5 * X - 0.75 * Y, 12)]
+    for name, build, bpe in cases:
+        e = build()
+        ga.autotune(e)
+        ms_f = _time_fn(torch, lambda: ga.evaluate(e, out=out), reps)
+        kernels = [0]
+
+        def eager():
+            r, k = ga.evaluate_eager(e)
+            kernels[0] = k
+        ms_e = _time_fn(torch, eager, 3, warmup=1)
+        torch.cuda.empty_cache()
+        res[name] = {"n": n, "fused_us": round(ms_f * 1e3, 1), "eager_us": round(ms_e * 1e3, 1),
+                     "speedup": round(ms_e / ms_f, 2), "kernels_fused": 1,
+                     "kernels_eager": kernels[0],
+                     "fused_GB/s": round(bpe * n / (ms_f * 1e-3) / 1e9, 1)}
+    del arrs, X, Y, U, W, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def _time_fn(torch, f, reps, warmup=3):
     for _ in range(warmup):
         f()
@@ -566,6 +599,7 @@ def run_gpu(args):
     if rank == 0 and not args.quick:
         details["reductions"] = bench_reductions(torch, pyc, stock, dev)
         details["scans"] = bench_scans(torch, pyc, stock, dev)
+        details["fused"] = bench_fused(torch, dev)
         details["batched"] = bench_batched(torch, pyc, stock, dev)
         details["serving"] = bench_serving(torch, pyc, stock, dev)
     if not args.quick:

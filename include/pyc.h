@@ -332,6 +332,47 @@ pyc_status pyc_scan_autotune(pyc_scan_t h, int64_t n, pyc_stream_t stream);
 pyc_status pyc_scan_config(pyc_scan_t h, int64_t n, int* vec_bytes, int* unroll, int* block);
 void pyc_scan_destroy(pyc_scan_t h);
 
+/* ------------------------------------------------------------------ fused expressions */
+
+/* Array arithmetic evaluated in one pass (Sec. 3.2.3-3.2.4: GPUArray operators
+ * make one temporary per intermediate result; an ElementwiseKernel evaluates the
+ * whole expression in a single pass).  The expression is compiled into one map
+ * (or map-reduce) kernel, cached like any other spec.
+ *
+ * expr        prefix notation: a leaf or "(op operand ...)".  Leaves: $k (array
+ *             argument k, element i), %k (scalar argument k), numeric literals
+ *             (no suffix; a literal takes the type of the other operand, a
+ *             fractional literal with integers gives double).
+ *             Operators: + - * / min max pow (two operands), < <= > >= == !=
+ *             (0 or 1, int), where (c, a, b: a if c != 0 else b), neg abs exp exp2
+ *             log log2 sin cos tan tanh sqrt rsqrt floor ceil (one operand),
+ *             casts f32 f64 i32 i64.
+ * Typing      C-style: the wider of I32 < I64 < F32 < F64 (BF16 / F16 arrays read
+ *             as F32); "/" and math functions of integers give F64; integer + - *
+ *             wrap in two's complement.  Binary32 operations round each result
+ *             (no contraction unless opts.fmad = 1); math functions are CUDA's.
+ * args        nargs entries: arg_dtypes[k] (F32, F64, BF16, F16, I32, I64) and
+ *             arg_is_array[k] (nonzero: an array of n elements).
+ *
+ * pyc_expr_map_create: the map "out[i] = expr" with argument list (a0 .. a{nargs-1},
+ * out), out of out_dtype (F32, F64, BF16, F16, I32, I64).  Launch it with
+ * pyc_map_launch: ptrs = the array arguments in order, then out; scalars packed
+ * in argument order (pyc_map_param gives offsets).
+ * pyc_expr_reduce_create: the map-reduce of expr with reduce "sum", "max" or
+ * "min" into out_dtype (F32, F64, I32, I64); launch with pyc_reduce_launch (ptrs:
+ * the arrays in order).
+ * Errors: PYC_E_PARSE (syntax, unknown operator, operand count, an argument
+ * used as the wrong kind), PYC_E_ARG (types), PYC_E_COMPILE. */
+pyc_status pyc_expr_map_create(const char* expr, int nargs, const pyc_dtype* arg_dtypes,
+                               const int* arg_is_array, pyc_dtype out_dtype,
+                               const pyc_opts* opts, pyc_map_t* out);
+pyc_status pyc_expr_reduce_create(const char* expr, int nargs, const pyc_dtype* arg_dtypes,
+                                  const int* arg_is_array, pyc_dtype out_dtype,
+                                  const char* reduce, const pyc_opts* opts, pyc_reduce_t* out);
+/* The type of expr under the rules above (F32, F64, I32 or I64) in *out. */
+pyc_status pyc_expr_type(const char* expr, int nargs, const pyc_dtype* arg_dtypes,
+                         const int* arg_is_array, pyc_dtype* out);
+
 /* ------------------------------------------------------------------ serving */
 
 /* A request-serving loop over map and map-reduce handles (continuous

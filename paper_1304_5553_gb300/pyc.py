@@ -99,7 +99,8 @@ EXPORTED = [
     "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
     "pyc_scan_create", "pyc_scan_launch", "pyc_scan_num_params", "pyc_scan_param",
     "pyc_scan_scalar_bytes", "pyc_scan_source", "pyc_scan_autotune", "pyc_scan_config", "pyc_scan_destroy",
-    "pyc_scan_sync", "pyc_scan_launch_test",
+    "pyc_scan_sync", "pyc_scan_launch_test", "pyc_expr_map_create", "pyc_expr_reduce_create",
+    "pyc_expr_type",
 ]
 
 _lib = None
@@ -148,6 +149,12 @@ def load(build_if_missing=True):
                                  ctypes.POINTER(vp)]),
         "pyc_scan_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp]),
         "pyc_scan_sync": (st, [vp, vp]),
+        "pyc_expr_map_create": (st, [cp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), i32,
+                                     ctypes.POINTER(pyc_opts), ctypes.POINTER(vp)]),
+        "pyc_expr_reduce_create": (st, [cp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), i32,
+                                        cp, ctypes.POINTER(pyc_opts), ctypes.POINTER(vp)]),
+        "pyc_expr_type": (st, [cp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                               ctypes.POINTER(i32)]),
         "pyc_scan_launch_test": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, i64, i64]),
         "pyc_scan_num_params": (i32, [vp]),
         "pyc_scan_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
@@ -290,6 +297,35 @@ def pyc_scan_create(dtype, neutral, scan_expr, input_expr, output_stmt, argspec,
 
 def pyc_scan_launch(h, n, ptrs, scalars=None, stream=None):
     _check(load().pyc_scan_launch(h, int(n), _ptr_array(ptrs), scalars, _stream(stream)))
+
+
+def pyc_expr_map_create(expr, arg_dtypes, arg_is_array, out_dtype, opts=None):
+    n = len(arg_dtypes)
+    dt = (ctypes.c_int * max(n, 1))(*[int(d) for d in arg_dtypes])
+    ia = (ctypes.c_int * max(n, 1))(*[int(bool(a)) for a in arg_is_array])
+    h = ctypes.c_void_p()
+    _check(load().pyc_expr_map_create(_enc(expr), n, dt, ia, int(out_dtype), _opts(opts),
+                                      ctypes.byref(h)))
+    return h
+
+
+def pyc_expr_reduce_create(expr, arg_dtypes, arg_is_array, out_dtype, reduce="sum", opts=None):
+    n = len(arg_dtypes)
+    dt = (ctypes.c_int * max(n, 1))(*[int(d) for d in arg_dtypes])
+    ia = (ctypes.c_int * max(n, 1))(*[int(bool(a)) for a in arg_is_array])
+    h = ctypes.c_void_p()
+    _check(load().pyc_expr_reduce_create(_enc(expr), n, dt, ia, int(out_dtype), _enc(reduce),
+                                         _opts(opts), ctypes.byref(h)))
+    return h
+
+
+def pyc_expr_type(expr, arg_dtypes, arg_is_array):
+    n = len(arg_dtypes)
+    dt = (ctypes.c_int * max(n, 1))(*[int(d) for d in arg_dtypes])
+    ia = (ctypes.c_int * max(n, 1))(*[int(bool(a)) for a in arg_is_array])
+    r = ctypes.c_int()
+    _check(load().pyc_expr_type(_enc(expr), n, dt, ia, ctypes.byref(r)))
+    return r.value
 
 
 def pyc_scan_sync(h, stream=None):
