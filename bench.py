@@ -298,6 +298,55 @@ def bench_fused(torch, dev, reps=10):
     return res
 
 
+def bench_pool(torch, pyc, dev):
+    """Memory pools (Sec. 3.2.6): host time of one allocate + free pair served by
+    a pool (reuse) vs by the driver (a pool that retains nothing) vs torch's own
+    caching allocator; and operator-at-a-time evaluation of a 4-node expression
+    at n = 2^20 with its temporaries from each."""
+    import time
+    from paper_1304_5553_gb300 import gpuarray as ga
+    from paper_1304_5553_gb300 import inputs
+    s = torch.cuda.current_stream().cuda_stream
+    pool = pyc.pyc_pool_create(pyc.PYC_POOL_DEVICE)
+    nopool = pyc.pyc_pool_create(pyc.PYC_POOL_DEVICE, max_retained=1)
+    res = {}
+    try:
+        for label, nbytes in (("1MiB", 1 << 20), ("64MiB", 1 << 26)):
+            row = {}
+            for name, p in (("pool", pool), ("driver", nopool)):
+                q = pyc.pyc_pool_alloc(p, nbytes, s)
+                pyc.pyc_pool_free(p, q, s)
+                reps = 2000 if name == "pool" else 200
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    q = pyc.pyc_pool_alloc(p, nbytes, s)
+                    pyc.pyc_pool_free(p, q, s)
+                row[name + "_us"] = round((time.perf_counter() - t0) / reps * 1e6, 2)
+            t0 = time.perf_counter()
+            for _ in range(2000):
+                t = torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
+                del t
+            row["torch_us"] = round((time.perf_counter() - t0) / 2000 * 1e6, 2)
+            res["alloc_free_" + label] = row
+        n = 1 << 20
+        x, y = (torch.from_numpy(inputs.uniform_f32(7, k, n)).to(dev) for k in range(2))
+        X, Y = ga.GArray(x), ga.GArray(y)
+        e = (X * Y + 2.5) * (X - Y)
+        row = {}
+        for name, p in (("pool", pool), ("driver", nopool), ("torch", None)):
+            ga.set_pool(p)
+            row[name + "_us"] = round(_time_fn(torch, lambda: ga.evaluate_eager(e), 50) * 1e3, 1)
+        ga.set_pool(None)
+        row["fused_us"] = round(_time_fn(torch, lambda: ga.evaluate(e), 50) * 1e3, 1)
+        res["eager_4_kernels_n2^20"] = row
+    finally:
+        ga.set_pool(None)
+        torch.cuda.synchronize()
+        pyc.pyc_pool_destroy(pool)
+        pyc.pyc_pool_destroy(nopool)
+    return res
+
+
 def _time_fn(torch, f, reps, warmup=3):
     for _ in range(warmup):
         f()
@@ -600,6 +649,7 @@ def run_gpu(args):
         details["reductions"] = bench_reductions(torch, pyc, stock, dev)
         details["scans"] = bench_scans(torch, pyc, stock, dev)
         details["fused"] = bench_fused(torch, dev)
+        details["pool"] = bench_pool(torch, pyc, dev)
         details["batched"] = bench_batched(torch, pyc, stock, dev)
         details["serving"] = bench_serving(torch, pyc, stock, dev)
     if not args.quick:

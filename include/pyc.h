@@ -373,6 +373,54 @@ pyc_status pyc_expr_reduce_create(const char* expr, int nargs, const pyc_dtype* 
 pyc_status pyc_expr_type(const char* expr, int nargs, const pyc_dtype* arg_dtypes,
                          const int* arg_is_array, pyc_dtype* out);
 
+/* ------------------------------------------------------------------ memory pools */
+
+/* Memory pools (Sec. 3.2.6: allocation calls are expensive, so blocks that a
+ * program frees are retained and handed out again for later requests of a
+ * similar size; pools exist for device and for page-locked host memory).
+ * Requests are rounded up to a size class: 512 bytes, or 8 classes per power
+ * of two above (at most 1/8 of a block unused); a block is reused only for its
+ * own class.  Reuse is stream-ordered: a block freed with stream s is handed out
+ * at once for a request on s, and for requests on other streams once the work
+ * queued on s before the free has finished (an event recorded at the free).
+ * The pool is thread-safe.  Retained blocks return to the system on
+ * pyc_pool_trim, on destroy, when retained bytes pass max_retained, and when a
+ * system allocation fails (the allocation is then retried once). */
+typedef struct pyc_pool* pyc_pool_t;
+typedef enum {
+  PYC_POOL_DEVICE = 0, /* cuMemAlloc: device memory of the current context's device */
+  PYC_POOL_PINNED = 1, /* cuMemAllocHost: page-locked host memory */
+  PYC_POOL_HOST = 2    /* ordinary host memory (aligned_alloc); streams are ignored */
+} pyc_pool_kind;
+typedef struct {
+  int64_t max_bytes;    /* cap on bytes taken from the system (live + retained); 0 = none */
+  int64_t max_retained; /* cap on retained (freed, unreturned) bytes; 0 = none */
+} pyc_pool_cfg;
+typedef struct {
+  int64_t live_bytes, live_blocks;         /* handed out and not yet freed */
+  int64_t retained_bytes, retained_blocks; /* freed, kept for reuse */
+  int64_t system_bytes;                    /* live + retained */
+  int64_t hits, misses;                    /* requests served by reuse / by the system */
+  int64_t system_allocs, system_frees;
+} pyc_pool_stats;
+/* The size class (bytes actually reserved) of a request of `bytes`. */
+int64_t pyc_pool_block_size(int64_t bytes);
+/* cfg may be NULL (no limits).  Device and pinned pools use the current context
+ * (the primary context of device $CUDA_DEVICE, default 0, if none is current). */
+pyc_status pyc_pool_create(pyc_pool_kind kind, const pyc_pool_cfg* cfg, pyc_pool_t* out);
+/* *ptr = a block of at least `bytes` (> 0), 256-byte aligned, to be used first on
+ * `stream`.  PYC_E_NOMEM when the system (or max_bytes) cannot supply it. */
+pyc_status pyc_pool_alloc(pyc_pool_t p, int64_t bytes, pyc_stream_t stream, void** ptr);
+/* Return a block; `stream` is the last stream that uses it (work already queued
+ * there may still be running).  NULL ptr is a no-op; a pointer this pool did not
+ * hand out (or one freed twice) is PYC_E_ARG. */
+pyc_status pyc_pool_free(pyc_pool_t p, void* ptr, pyc_stream_t stream);
+/* Return every retained block to the system (waiting for the work that used it). */
+pyc_status pyc_pool_trim(pyc_pool_t p);
+pyc_status pyc_pool_get_stats(pyc_pool_t p, pyc_pool_stats* stats);
+/* Returns retained AND live blocks to the system: live blocks become invalid. */
+void pyc_pool_destroy(pyc_pool_t p);
+
 /* ------------------------------------------------------------------ serving */
 
 /* A request-serving loop over map and map-reduce handles (continuous

@@ -14,6 +14,10 @@ unfused baseline.
     z = evaluate(x * exp(-y * y) + sin(u) * w)          # one kernel
     s = sum(x * y)                                       # one map-reduce
 
+`set_pool` makes outputs and temporaries come from a device memory pool
+(Sec. 3.2.6: pools integrate with GPUArray, whose operators allocate and free
+arrays of recurring sizes).
+
 Python scalars become scalar kernel arguments (no recompilation when their
 value changes): binary64 if an F64 array appears in the expression, else
 binary32; integers int32 (int64 if they do not fit).
@@ -190,6 +194,20 @@ class _Lowered:
 
 _cache = {}
 _lock = threading.Lock()
+_pool = [None]
+
+
+def set_pool(pool):
+    """Allocate expression outputs (and the temporaries of evaluate_eager) from a
+    device memory pool (pyc_pool_create(PYC_POOL_DEVICE)); None: torch's allocator."""
+    _pool[0] = pool
+
+
+def _empty(n, dtype, device, stream):
+    import torch
+    if _pool[0] is not None:
+        return pyc.pool_empty(_pool[0], n, dtype, stream)
+    return torch.empty(n, dtype=dtype, device=device)
 
 
 def _map_handle(low, out_dtype):
@@ -238,7 +256,7 @@ def evaluate(expr, out=None, dtype=None, stream=None):
     n = low.n()
     if out is None:
         od = dtype if dtype is not None else low.result_dtype()
-        out = GArray(torch.empty(n, dtype=pyc._torch_dtype(od), device=low.arrays[0].tensor.device))
+        out = GArray(_empty(n, pyc._torch_dtype(od), low.arrays[0].tensor.device, stream))
     elif not isinstance(out, GArray):
         out = GArray(out)
     if len(out) != n:

@@ -86,6 +86,18 @@ class pyc_server_stats(ctypes.Structure):
                                               "arena_in_use")]
 
 
+class pyc_pool_cfg(ctypes.Structure):
+    _fields_ = [("max_bytes", ctypes.c_int64), ("max_retained", ctypes.c_int64)]
+
+
+class pyc_pool_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("live_bytes", "live_blocks", "retained_bytes",
+                                              "retained_blocks", "system_bytes", "hits",
+                                              "misses", "system_allocs", "system_frees")]
+
+
+PYC_POOL_DEVICE, PYC_POOL_PINNED, PYC_POOL_HOST = 0, 1, 2
+
 # every symbol include/pyc.h declares (checked by the tests)
 EXPORTED = [
     "pyc_last_error", "pyc_version",
@@ -100,7 +112,8 @@ EXPORTED = [
     "pyc_scan_create", "pyc_scan_launch", "pyc_scan_num_params", "pyc_scan_param",
     "pyc_scan_scalar_bytes", "pyc_scan_source", "pyc_scan_autotune", "pyc_scan_config", "pyc_scan_destroy",
     "pyc_scan_sync", "pyc_scan_launch_test", "pyc_expr_map_create", "pyc_expr_reduce_create",
-    "pyc_expr_type",
+    "pyc_expr_type", "pyc_pool_block_size", "pyc_pool_create", "pyc_pool_alloc", "pyc_pool_free",
+    "pyc_pool_trim", "pyc_pool_get_stats", "pyc_pool_destroy",
 ]
 
 _lib = None
@@ -155,6 +168,13 @@ def load(build_if_missing=True):
                                         cp, ctypes.POINTER(pyc_opts), ctypes.POINTER(vp)]),
         "pyc_expr_type": (st, [cp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                ctypes.POINTER(i32)]),
+        "pyc_pool_block_size": (i64, [i64]),
+        "pyc_pool_create": (st, [i32, ctypes.POINTER(pyc_pool_cfg), ctypes.POINTER(vp)]),
+        "pyc_pool_alloc": (st, [vp, i64, vp, ctypes.POINTER(vp)]),
+        "pyc_pool_free": (st, [vp, vp, vp]),
+        "pyc_pool_trim": (st, [vp]),
+        "pyc_pool_get_stats": (st, [vp, ctypes.POINTER(pyc_pool_stats)]),
+        "pyc_pool_destroy": (None, [vp]),
         "pyc_scan_launch_test": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, i64, i64]),
         "pyc_scan_num_params": (i32, [vp]),
         "pyc_scan_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
@@ -326,6 +346,88 @@ def pyc_expr_type(expr, arg_dtypes, arg_is_array):
     r = ctypes.c_int()
     _check(load().pyc_expr_type(_enc(expr), n, dt, ia, ctypes.byref(r)))
     return r.value
+
+
+def pyc_pool_block_size(nbytes):
+    return int(load().pyc_pool_block_size(int(nbytes)))
+
+
+def pyc_pool_create(kind=PYC_POOL_DEVICE, max_bytes=0, max_retained=0):
+    cfg = pyc_pool_cfg(int(max_bytes), int(max_retained))
+    h = ctypes.c_void_p()
+    _check(load().pyc_pool_create(int(kind), ctypes.byref(cfg), ctypes.byref(h)))
+    _destroyed_pools.discard(h.value)
+    return h
+
+
+def pyc_pool_alloc(p, nbytes, stream=None):
+    q = ctypes.c_void_p()
+    _check(load().pyc_pool_alloc(p, int(nbytes), _stream(stream), ctypes.byref(q)))
+    return q.value
+
+
+def pyc_pool_free(p, ptr, stream=None):
+    _check(load().pyc_pool_free(p, ptr, _stream(stream)))
+
+
+def pyc_pool_trim(p):
+    _check(load().pyc_pool_trim(p))
+
+
+def pyc_pool_get_stats(p):
+    st = pyc_pool_stats()
+    _check(load().pyc_pool_get_stats(p, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in pyc_pool_stats._fields_}
+
+
+_destroyed_pools = set()
+
+
+def pyc_pool_destroy(p):
+    _destroyed_pools.add(p.value if hasattr(p, "value") else p)
+    load().pyc_pool_destroy(p)
+
+
+class _PoolBlock:
+    """A device pool block exposed through __cuda_array_interface__; torch keeps
+    this object alive as long as a tensor made from it, and its deletion returns
+    the block to the pool with the stream current at that time."""
+
+    def __init__(self, pool, n, dtype, stream):
+        import torch
+        self._torch = torch
+        self._pool = pool
+        self._dt = dtype
+        nbytes = max(n, 1) * torch.empty(0, dtype=dtype).element_size()
+        self._ptr = pyc_pool_alloc(pool, nbytes, stream)
+        self.__cuda_array_interface__ = {
+            "shape": (n,), "typestr": torch.empty(0, dtype=dtype).numpy().dtype.str
+            if dtype != torch.bfloat16 else "<V2", "data": (self._ptr, False),
+            "version": 2}
+
+    def __del__(self):
+        ptr, self._ptr = getattr(self, "_ptr", None), None
+        pool = getattr(self, "_pool", None)
+        if not ptr or _lib is None or pool is None:
+            return
+        key = pool.value if hasattr(pool, "value") else pool
+        if key in _destroyed_pools:  # destroy already returned the memory
+            return
+        try:
+            s = self._torch.cuda.current_stream().cuda_stream
+            pyc_pool_free(pool, ptr, s)
+        except Exception:  # interpreter shutdown, or a pool handle reused since
+            pass
+
+
+def pool_empty(pool, n, dtype, stream=None):
+    """A 1-D CUDA tensor of n elements backed by a block of a device pool; the
+    block goes back to the pool when the tensor is deleted."""
+    import torch
+    if dtype == torch.bfloat16:  # the interface has no bfloat16 type string
+        return pool_empty(pool, n, torch.int16, stream).view(torch.bfloat16)
+    blk = _PoolBlock(pool, n, dtype, stream)
+    return torch.as_tensor(blk, device="cuda")
 
 
 def pyc_scan_sync(h, stream=None):
