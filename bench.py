@@ -347,6 +347,54 @@ def bench_pool(torch, pyc, dev):
     return res
 
 
+def bench_cg(torch, pyc, dev, nx=2048, iters=100):
+    """Sparse (Sec. 3.2.6): the 5-point Laplacian on an nx x nx grid (4.19 M
+    unknowns, 21 M nonzeros at nx = 2048).  SpMV GB/s over its algorithmic bytes
+    (values + column indices + row pointers + x once + y); CG time per step over
+    `iters` steps (rtol = 0), whose algorithmic bytes are one SpMV plus 12 vector
+    passes (p.q: 2, x and r update: 6, r.r: 1, p update: 3)."""
+    from paper_1304_5553_gb300 import inputs
+    s = torch.cuda.current_stream().cuda_stream
+    res = {}
+    n = nx * nx
+    for name, vt, npdt, tdt in (("f32", pyc.PYC_F32, np.float32, torch.float32),
+                                ("f64", pyc.PYC_F64, np.float64, torch.float64)):
+        rp, c, v = inputs.poisson2d(nx, nx, npdt)
+        d = [torch.from_numpy(a).to(dev) for a in (rp, c, v)]
+        a = pyc.pyc_csr_create(n, n, c.size, *(t.data_ptr() for t in d), vt)
+        try:
+            vb = np.dtype(npdt).itemsize
+            x = torch.from_numpy(np.random.default_rng(9).uniform(-1, 1, n).astype(npdt)).to(dev)
+            y = torch.empty(n, dtype=tdt, device=dev)
+            pyc.pyc_spmv_autotune(a, x.data_ptr(), y.data_ptr(), s)
+            ms = _time_fn(torch, lambda: pyc.pyc_spmv(a, x.data_ptr(), y.data_ptr(), s), 20)
+            spmv_bytes = c.size * (vb + 4) + (n + 1) * 8 + 2 * n * vb
+            b = torch.ones(n, dtype=tdt, device=dev)
+            xs = torch.zeros(n, dtype=tdt, device=dev)
+            pyc.pyc_cg_solve(a, b.data_ptr(), xs.data_ptr(), 0.0, 8, s)   # warm-up
+            xs.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = pyc.pyc_cg_solve(a, b.data_ptr(), xs.data_ptr(), 0.0, iters, s)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_cg = e0.elapsed_time(e1) / info["iterations"]
+            step_bytes = spmv_bytes + 12 * n * vb
+            res[name] = {"n": n, "nnz": int(c.size), "spmv_us": round(ms * 1e3, 1),
+                         "spmv_GB/s": round(spmv_bytes / (ms * 1e-3) / 1e9, 1),
+                         "lanes_per_row": pyc.pyc_csr_width(a),
+                         "cg_steps": info["iterations"], "cg_us_per_step": round(ms_cg * 1e3, 1),
+                         "cg_GB/s": round(step_bytes / (ms_cg * 1e-3) / 1e9, 1),
+                         "cg_residual": info["residual"]}
+        finally:
+            torch.cuda.synchronize()
+            pyc.pyc_csr_destroy(a)
+        del d, x, y, b, xs
+        torch.cuda.empty_cache()
+    return res
+
+
 def _time_fn(torch, f, reps, warmup=3):
     for _ in range(warmup):
         f()
@@ -650,6 +698,7 @@ def run_gpu(args):
         details["scans"] = bench_scans(torch, pyc, stock, dev)
         details["fused"] = bench_fused(torch, dev)
         details["pool"] = bench_pool(torch, pyc, dev)
+        details["cg"] = bench_cg(torch, pyc, dev)
         details["batched"] = bench_batched(torch, pyc, stock, dev)
         details["serving"] = bench_serving(torch, pyc, stock, dev)
     if not args.quick:

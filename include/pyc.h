@@ -421,6 +421,47 @@ pyc_status pyc_pool_get_stats(pyc_pool_t p, pyc_pool_stats* stats);
 /* Returns retained AND live blocks to the system: live blocks become invalid. */
 void pyc_pool_destroy(pyc_pool_t p);
 
+/* ------------------------------------------------------------------ sparse matrices, CG */
+
+/* Sparse matrices and a conjugate-gradient solver (Sec. 3.2.6: GPU sparse
+ * matrices following Bell and Garland's SpMV, and a CG-based Krylov solver for
+ * large sparse linear systems).
+ *
+ * pyc_csr_create wraps a CSR matrix already in device memory (the caller owns it
+ * and keeps it alive): rowptr int64[nrows + 1] (rowptr[0] = 0, nondecreasing,
+ * rowptr[nrows] = nnz), colidx int32[nnz] (each < ncols < 2^31), vals[nnz] of vt
+ * (F32 or F64).  Indices are not checked: out-of-range ones are undefined
+ * behaviour.  The handle compiles its kernels (cached) and picks T, the lanes per
+ * row, from the mean row length. */
+typedef struct pyc_csr* pyc_csr_t;
+pyc_status pyc_csr_create(int64_t nrows, int64_t ncols, int64_t nnz, const void* rowptr,
+                          const void* colidx, const void* vals, pyc_dtype vt, pyc_csr_t* out);
+/* The lanes per row (1, 2, 4, ..., 32) the matrix-vector product uses; set it. */
+pyc_status pyc_csr_width(pyc_csr_t a, int* width);
+pyc_status pyc_csr_set_width(pyc_csr_t a, int width);
+/* y = A x on `stream` (x: ncols, y: nrows elements of vt, device; x and y must not
+ * overlap).  Each row is folded per lane, then across its lanes in a fixed tree. */
+pyc_status pyc_spmv(pyc_csr_t a, const void* x, void* y, pyc_stream_t stream);
+/* Time every lane count on (x, y) and keep the fastest for this matrix. */
+pyc_status pyc_spmv_autotune(pyc_csr_t a, const void* x, void* y, pyc_stream_t stream);
+
+typedef struct {
+  int64_t iterations; /* CG steps taken */
+  double residual;    /* ||r|| / ||b|| at exit (the recurrence's r; ||r|| if b = 0) */
+  int converged;      /* residual <= rtol */
+  int pad;
+} pyc_cg_info;
+/* Solve A x = b for symmetric positive definite A by conjugate gradients
+ * (Hestenes-Stiefel): x holds the initial guess on entry and the solution on
+ * exit (device, nrows elements; b likewise).  Stops when ||r|| <= rtol ||b|| or
+ * after maxit steps.  Runs on `stream`; the host synchronises every 8 steps to
+ * test convergence.  The handle keeps 3 vectors of work space per (context,
+ * stream).  A breakdown (p.Ap = 0 before convergence) stops progress; the result
+ * then reports converged = 0. */
+pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol, int64_t maxit,
+                        pyc_stream_t stream, pyc_cg_info* info);
+void pyc_csr_destroy(pyc_csr_t a);
+
 /* ------------------------------------------------------------------ serving */
 
 /* A request-serving loop over map and map-reduce handles (continuous

@@ -1,0 +1,339 @@
+// Sparse matrices and the conjugate-gradient solver (Sec. 3.2.6: GPU sparse
+// matrices after Bell and Garland, and a CG-based Krylov solver for large sparse
+// systems).
+//
+// CSR matrix-vector product: T lanes share a row (T in {1, 2, ..., 32}, from the
+// mean row length or timed), lanes stride over the row's nonzeros, products are
+// folded per lane and then across the T lanes by a shuffle tree.  Warps step
+// over rows in lockstep (32 / T rows at a time), so the shuffles never diverge.
+//
+// CG (Hestenes and Stiefel) runs entirely on the device: the dot products are
+// the library's map-reduce, the vector updates its maps, and the step lengths
+// alpha = rs / (p.Ap) and beta = rs' / rs are read by those maps from device
+// memory, so the host synchronises only every few iterations to test
+// convergence.  After convergence the updates freeze (zero step lengths).
+#include <algorithm>
+#include <iterator>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "cudrv.h"
+#include "handles.h"
+#include "kcache.h"
+
+namespace pyc {
+
+namespace {
+
+const char* kSpmvSource = R"PYC(
+// CSR y = A x with T lanes per row (generated for one value type V)
+typedef long long pyc_i64;
+template <int T>
+__device__ __forceinline__ void pyc_spmv(const pyc_i64* __restrict__ rowptr,
+    const int* __restrict__ col, const V* __restrict__ val, const V* __restrict__ x,
+    V* __restrict__ y, const pyc_i64 nrows) {
+  constexpr int R = 32 / T;  // rows per warp step
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % T;
+  const pyc_i64 warp = ((pyc_i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const pyc_i64 nwarps = ((pyc_i64)gridDim.x * blockDim.x) >> 5;
+  for (pyc_i64 base = warp * R; base < nrows; base += nwarps * R) {
+    const pyc_i64 r = base + lane / T;
+    V s = 0;
+    if (r < nrows) {
+      const pyc_i64 b = rowptr[r], e = rowptr[r + 1];
+      for (pyc_i64 k = b + sub; k < e; k += T) s += val[k] * __ldg(x + col[k]);
+    }
+#pragma unroll
+    for (int d = T / 2; d >= 1; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d, T);
+    if (sub == 0 && r < nrows) y[r] = s;
+  }
+}
+#define PYC_SPMV(T) \
+  extern "C" __global__ void __launch_bounds__(256) pyc_spmv_t##T(const pyc_i64* rowptr, \
+      const int* col, const V* val, const V* x, V* y, const pyc_i64 nrows) { \
+    pyc_spmv<T>(rowptr, col, val, x, y, nrows); \
+  }
+PYC_SPMV(1)
+PYC_SPMV(2)
+PYC_SPMV(4)
+PYC_SPMV(8)
+PYC_SPMV(16)
+PYC_SPMV(32)
+)PYC";
+
+const int kWidths[] = {1, 2, 4, 8, 16, 32};
+
+int default_width(int64_t nrows, int64_t nnz) {
+  const double mean = nrows ? (double)nnz / (double)nrows : 1.0;
+  int t = 1;
+  while (t < 32 && 2 * t <= mean) t *= 2;
+  return t;
+}
+
+}  // namespace
+
+}  // namespace pyc
+
+struct pyc_csr {
+  int64_t nrows = 0, ncols = 0, nnz = 0;
+  CUdeviceptr rowptr = 0, col = 0, val = 0;
+  pyc_dtype vt = PYC_F32;
+  int width = 1;
+  std::shared_ptr<pyc::Module> mod;
+  // CG: step kernels (the library's map / map-reduce) and per-stream work space
+  std::mutex mu;
+  pyc_reduce_t dot = nullptr;
+  pyc_map_t init_r = nullptr, copy = nullptr, update_xr = nullptr, update_p = nullptr,
+            bookkeep = nullptr, set_tol = nullptr;
+  struct Work {
+    CUdeviceptr base = 0;
+    int64_t n = 0;
+  };
+  std::map<std::pair<CUcontext, CUstream>, Work> work;
+};
+
+namespace pyc {
+
+namespace {
+
+int vbytes(pyc_dtype t) { return t == PYC_F64 ? 8 : 4; }
+
+void launch_spmv(pyc_csr* a, int width, CUdeviceptr x, CUdeviceptr y, CUstream s) {
+  if (a->nrows == 0) return;
+  CUfunction f = a->mod->function("pyc_spmv_t" + std::to_string(width));
+  const int block = 256;
+  const int64_t rows_per_block = (int64_t)(block / 32) * (32 / width);
+  const int resident = resident_ctas(f, block);
+  const int64_t need = (a->nrows + rows_per_block - 1) / rows_per_block;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, need));
+  void* params[] = {&a->rowptr, &a->col, &a->val, &x, &y, &a->nrows};
+  PYC_CU(drv().cuLaunchKernel(f, grid, 1, 1, block, 1, 1, 0, s, params, nullptr));
+}
+
+void make_cg_kernels(pyc_csr* a) {
+  std::lock_guard<std::mutex> lk(a->mu);
+  if (a->dot) return;
+  const std::string T = a->vt == PYC_F64 ? "double" : "float";
+  auto mk = [&](const std::string& spec, const std::string& stmt, const char* name) {
+    pyc_map_t h = nullptr;
+    pyc_status st = pyc_map_create(spec.c_str(), stmt.c_str(), name, nullptr, &h);
+    if (st != PYC_OK) throw Error(st, pyc_last_error());
+    return h;
+  };
+  // s[0] = rs (r.r), s[1] = p.Ap, s[2] = tol^2, s[3] = r.r after the update, s[4] = b.b
+  pyc_status st = pyc_reduce_create(a->vt, "0", "a+b", "x[i]*y[i]",
+                                    (T + " *x, " + T + " *y").c_str(), nullptr, &a->dot);
+  if (st != PYC_OK) throw Error(st, pyc_last_error());
+  a->init_r = mk(T + " *r, " + T + " *b, " + T + " *q", "r[i] = b[i] - q[i]", "cg_init");
+  a->copy = mk(T + " *d, " + T + " *s", "d[i] = s[i]", "cg_copy");
+  a->update_xr = mk(T + " *x, " + T + " *r, " + T + " *p, " + T + " *q, " + T + " *s",
+                    T + " al = (s[0] > s[2] && s[1] != 0) ? s[0] / s[1] : (" + T +
+                        ")0; x[i] += al * p[i]; r[i] -= al * q[i]",
+                    "cg_xr");
+  a->update_p = mk(T + " *p, " + T + " *r, " + T + " *s",
+                   T + " be = s[0] > s[2] ? s[3] / s[0] : (" + T + ")0; p[i] = r[i] + be * p[i]",
+                   "cg_p");
+  a->bookkeep = mk(T + " *s, long long *it",
+                   "if (i == 0 && s[0] > s[2]) { s[0] = s[3]; it[0] += 1; }", "cg_step");
+  a->set_tol = mk(T + " *s, double rtol2", "if (i == 0) s[2] = (" + T + ")(rtol2 * (double)s[4])",
+                  "cg_tol");
+}
+
+pyc_csr::Work& cg_work(pyc_csr* a, CUstream s, int64_t n) {
+  CUcontext ctx = ensure_context();
+  std::lock_guard<std::mutex> lk(a->mu);
+  auto& w = a->work[std::make_pair(ctx, s)];
+  if (w.n < n) {
+    if (w.base) {
+      PYC_CU(drv().cuStreamSynchronize(s));
+      drv().cuMemFree(w.base);
+      w.base = 0;
+    }
+    const int64_t vb = (int64_t)vbytes(a->vt);
+    const int64_t vec = (n * vb + 255) / 256 * 256;
+    PYC_CU(drv().cuMemAlloc(&w.base, (size_t)(3 * vec + 256)));
+    w.n = n;
+  }
+  return w;
+}
+
+void map_launch(pyc_map_t h, int64_t n, std::initializer_list<CUdeviceptr> ptrs,
+                const void* scalars, CUstream s) {
+  std::vector<void*> p;
+  for (CUdeviceptr d : ptrs) p.push_back(reinterpret_cast<void*>(d));
+  pyc_status st = pyc_map_launch(h, n, p.data(), scalars, s);
+  if (st != PYC_OK) throw Error(st, pyc_last_error());
+}
+
+void dot_launch(pyc_reduce_t h, int64_t n, CUdeviceptr x, CUdeviceptr y, CUdeviceptr out,
+                CUstream s) {
+  void* p[] = {reinterpret_cast<void*>(x), reinterpret_cast<void*>(y)};
+  pyc_status st = pyc_reduce_launch(h, n, p, nullptr, reinterpret_cast<void*>(out), s);
+  if (st != PYC_OK) throw Error(st, pyc_last_error());
+}
+
+}  // namespace
+
+}  // namespace pyc
+
+using namespace pyc;
+
+PYC_API pyc_status pyc_csr_create(int64_t nrows, int64_t ncols, int64_t nnz, const void* rowptr,
+                                  const void* colidx, const void* vals, pyc_dtype vt,
+                                  pyc_csr_t* out) {
+  return guarded([&] {
+    if (!out) fail(PYC_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (nrows < 0 || ncols < 0 || nnz < 0) fail(PYC_E_ARG, "negative size");
+    if (ncols > 0x7fffffffLL) fail(PYC_E_ARG, "column indices are int32: ncols < 2^31");
+    if (vt != PYC_F32 && vt != PYC_F64) fail(PYC_E_ARG, "values are F32 or F64");
+    if (nrows > 0 && !rowptr) fail(PYC_E_ARG, "rowptr is NULL");
+    if (nnz > 0 && (!colidx || !vals)) fail(PYC_E_ARG, "colidx / vals are NULL");
+    auto a = std::make_unique<pyc_csr>();
+    a->nrows = nrows;
+    a->ncols = ncols;
+    a->nnz = nnz;
+    a->rowptr = reinterpret_cast<CUdeviceptr>(rowptr);
+    a->col = reinterpret_cast<CUdeviceptr>(colidx);
+    a->val = reinterpret_cast<CUdeviceptr>(vals);
+    a->vt = vt;
+    a->width = default_width(nrows, nnz);
+    std::string src = std::string("#define V ") + (vt == PYC_F64 ? "double" : "float") + "\n" +
+                      kSpmvSource;
+    a->mod = get_module(src, true);
+    *out = a.release();
+  });
+}
+
+PYC_API pyc_status pyc_csr_width(pyc_csr_t a, int* width) {
+  return guarded([&] {
+    if (!a || !width) fail(PYC_E_ARG, "NULL argument");
+    *width = a->width;
+  });
+}
+
+PYC_API pyc_status pyc_csr_set_width(pyc_csr_t a, int width) {
+  return guarded([&] {
+    if (!a) fail(PYC_E_ARG, "matrix is NULL");
+    if (std::find(std::begin(kWidths), std::end(kWidths), width) == std::end(kWidths))
+      fail(PYC_E_ARG, "width is 1, 2, 4, 8, 16 or 32");
+    a->width = width;
+  });
+}
+
+PYC_API pyc_status pyc_spmv(pyc_csr_t a, const void* x, void* y, pyc_stream_t stream) {
+  return guarded([&] {
+    if (!a) fail(PYC_E_ARG, "matrix is NULL");
+    if (a->nrows > 0 && (!x || !y)) fail(PYC_E_ARG, "x / y is NULL");
+    launch_spmv(a, a->width, reinterpret_cast<CUdeviceptr>(x), reinterpret_cast<CUdeviceptr>(y),
+                reinterpret_cast<CUstream>(stream));
+  });
+}
+
+PYC_API pyc_status pyc_spmv_autotune(pyc_csr_t a, const void* x, void* y, pyc_stream_t stream) {
+  return guarded([&] {
+    if (!a) fail(PYC_E_ARG, "matrix is NULL");
+    if (a->nrows == 0) return;
+    CUstream s = reinterpret_cast<CUstream>(stream);
+    CUevent e0, e1;
+    PYC_CU(drv().cuEventCreate(&e0, CU_EVENT_DEFAULT));
+    PYC_CU(drv().cuEventCreate(&e1, CU_EVENT_DEFAULT));
+    float best = 1e30f;
+    int best_w = a->width;
+    for (int w : kWidths) {
+      for (int k = 0; k < 2; ++k)
+        launch_spmv(a, w, reinterpret_cast<CUdeviceptr>(x), reinterpret_cast<CUdeviceptr>(y), s);
+      PYC_CU(drv().cuEventRecord(e0, s));
+      for (int k = 0; k < 5; ++k)
+        launch_spmv(a, w, reinterpret_cast<CUdeviceptr>(x), reinterpret_cast<CUdeviceptr>(y), s);
+      PYC_CU(drv().cuEventRecord(e1, s));
+      PYC_CU(drv().cuEventSynchronize(e1));
+      float ms = 0;
+      PYC_CU(drv().cuEventElapsedTime(&ms, e0, e1));
+      if (ms < best) best = ms, best_w = w;
+    }
+    drv().cuEventDestroy(e0);
+    drv().cuEventDestroy(e1);
+    a->width = best_w;
+  });
+}
+
+PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol, int64_t maxit,
+                                pyc_stream_t stream, pyc_cg_info* info) {
+  return guarded([&] {
+    if (!a || !b || !x) fail(PYC_E_ARG, "NULL argument");
+    if (a->nrows != a->ncols) fail(PYC_E_ARG, "CG needs a square matrix");
+    if (!(rtol >= 0) || maxit < 0) fail(PYC_E_ARG, "rtol >= 0 and maxit >= 0");
+    const int64_t n = a->nrows;
+    CUstream s = reinterpret_cast<CUstream>(stream);
+    make_cg_kernels(a);
+    pyc_csr::Work& w = cg_work(a, s, n);
+    const int64_t vb = vbytes(a->vt);
+    const int64_t vec = (n * vb + 255) / 256 * 256;
+    const CUdeviceptr r = w.base, p = w.base + vec, q = w.base + 2 * vec;
+    const CUdeviceptr sc = w.base + 3 * vec;   // s[0..4]
+    const CUdeviceptr it = sc + 8 * vb;       // iteration counter (int64)
+    const CUdeviceptr bx = reinterpret_cast<CUdeviceptr>(b), xx = reinterpret_cast<CUdeviceptr>(x);
+    PYC_CU(drv().cuMemsetD8Async(sc, 0, 256, s));
+    int64_t iters = 0;
+    double rs = 0, bb = 0, tol2 = 0;
+    if (n > 0) {
+      // r = b - A x, p = r, s[0] = r.r, s[4] = b.b, s[2] = rtol^2 b.b
+      launch_spmv(a, a->width, xx, q, s);
+      map_launch(a->init_r, n, {r, bx, q}, nullptr, s);
+      map_launch(a->copy, n, {p, r}, nullptr, s);
+      dot_launch(a->dot, n, r, r, sc, s);
+      dot_launch(a->dot, n, bx, bx, sc + 4 * vb, s);
+      const double rt2 = rtol * rtol;
+      map_launch(a->set_tol, 1, {sc}, &rt2, s);
+      int64_t launched = 0;
+      const int64_t chunk = 8;
+      for (;;) {
+        unsigned char host[64];
+        PYC_CU(drv().cuMemcpyDtoHAsync(host, sc, 5 * vb, s));
+        PYC_CU(drv().cuMemcpyDtoHAsync(host + 48, it, 8, s));
+        PYC_CU(drv().cuStreamSynchronize(s));
+        auto get = [&](int k) {
+          return a->vt == PYC_F64 ? reinterpret_cast<double*>(host)[k]
+                                  : (double)reinterpret_cast<float*>(host)[k];
+        };
+        rs = get(0);
+        tol2 = get(2);
+        bb = get(4);
+        iters = *reinterpret_cast<int64_t*>(host + 48);
+        if (!(rs > tol2) || launched >= maxit) break;
+        const int64_t k = std::min<int64_t>(chunk, maxit - launched);
+        for (int64_t j = 0; j < k; ++j) {
+          launch_spmv(a, a->width, p, q, s);                        // q = A p
+          dot_launch(a->dot, n, p, q, sc + vb, s);                  // s[1] = p.q
+          map_launch(a->update_xr, n, {xx, r, p, q, sc}, nullptr, s);  // x += al p, r -= al q
+          dot_launch(a->dot, n, r, r, sc + 3 * vb, s);              // s[3] = r.r
+          map_launch(a->update_p, n, {p, r, sc}, nullptr, s);       // p = r + be p
+          map_launch(a->bookkeep, 1, {sc, it}, nullptr, s);         // s[0] = s[3], it++
+        }
+        launched += k;
+      }
+    }
+    if (info) {
+      info->iterations = iters;
+      info->residual = bb > 0 ? std::sqrt(std::max(rs, 0.0) / bb) : std::sqrt(std::max(rs, 0.0));
+      info->converged = n == 0 || !(rs > tol2) ? 1 : 0;
+    }
+  });
+}
+
+PYC_API void pyc_csr_destroy(pyc_csr_t a) {
+  if (!a) return;
+  try {
+    for (auto& kv : a->work)
+      if (kv.second.base) drv().cuMemFree(kv.second.base);
+    pyc_reduce_destroy(a->dot);
+    for (pyc_map_t h : {a->init_r, a->copy, a->update_xr, a->update_p, a->bookkeep, a->set_tol})
+      pyc_map_destroy(h);
+  } catch (...) {
+  }
+  delete a;
+}

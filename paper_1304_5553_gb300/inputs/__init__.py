@@ -139,3 +139,63 @@ def argmin_with_minima(seed, n, frac=0.01, minimum=-2.5, stream_vals=0, stream_p
         pos = index_sample(seed, stream_pos, k, n)
         x[pos] = np.float32(minimum)
     return x
+
+
+# ------------------------------------------------------------------ sparse matrices
+
+def poisson2d(nx, ny, dtype=np.float32):
+    """CSR of the 5-point Laplacian on an nx x ny grid (Dirichlet boundary):
+    4 on the diagonal, -1 for each grid neighbour; rows in grid order
+    (row = iy * nx + ix).  Returns (rowptr int64, col int32, val)."""
+    n = nx * ny
+    iy, ix = np.divmod(np.arange(n, dtype=np.int64), nx)
+    cols, vals = [], []
+    for dx, dy, v in ((0, -1, -1.0), (-1, 0, -1.0), (0, 0, 4.0), (1, 0, -1.0), (0, 1, -1.0)):
+        ok = (ix + dx >= 0) & (ix + dx < nx) & (iy + dy >= 0) & (iy + dy < ny)
+        cols.append(np.where(ok, (iy + dy) * nx + ix + dx, -1))
+        vals.append(np.full(n, v))
+    c = np.stack(cols, 1)
+    v = np.stack(vals, 1)
+    keep = c >= 0
+    counts = keep.sum(1)
+    rowptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return rowptr, c[keep].astype(np.int32), v[keep].astype(dtype)
+
+
+def random_spd(n, seed, max_degree=1000, empty_every=0, dtype=np.float64):
+    """A seeded symmetric, strictly diagonally dominant (so positive definite)
+    CSR matrix: row i draws log-uniform in [1, max_degree] partners j (both a_ij
+    and a_ji are set, values uniform in [-1, 0)), the diagonal is the row's sum
+    of |off-diagonal| + 1.  With empty_every = k, every k-th row and column are
+    left empty (not SPD then; for products only).  Returns (rowptr, col, val)."""
+    rng = np.random.default_rng(seed)
+    deg = np.floor(2.0 ** (rng.random(n) * np.log2(max_degree))).astype(np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), deg)
+    cols = rng.integers(0, n, rows.size)
+    vals = -rng.random(rows.size)
+    r = np.concatenate([rows, cols])
+    c = np.concatenate([cols, rows])
+    v = np.concatenate([vals, vals])
+    off = r != c
+    r, c, v = r[off], c[off], v[off]
+    if empty_every:
+        live = (r % empty_every != 0) & (c % empty_every != 0)
+        r, c, v = r[live], c[live], v[live]
+    key = r * n + c
+    order = np.argsort(key, kind="stable")
+    key, v = key[order], v[order]
+    uniq, first = np.unique(key, return_index=True)
+    v = np.add.reduceat(v, first)           # merge duplicate draws of one entry
+    r, c = np.divmod(uniq, n)
+    diag = np.bincount(r, weights=np.abs(v), minlength=n) + 1.0
+    di = np.arange(n, dtype=np.int64)
+    if empty_every:
+        keepd = di % empty_every != 0
+        di, diag = di[keepd], diag[keepd]
+    R = np.concatenate([r, di])
+    C = np.concatenate([c, di])
+    V = np.concatenate([v, diag[di] if not empty_every else diag])
+    order = np.lexsort((C, R))
+    R, C, V = R[order], C[order], V[order]
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(R, minlength=n))]).astype(np.int64)
+    return rowptr, C.astype(np.int32), V.astype(dtype)

@@ -98,6 +98,11 @@ class pyc_pool_stats(ctypes.Structure):
 
 PYC_POOL_DEVICE, PYC_POOL_PINNED, PYC_POOL_HOST = 0, 1, 2
 
+
+class pyc_cg_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("residual", ctypes.c_double),
+                ("converged", ctypes.c_int), ("pad", ctypes.c_int)]
+
 # every symbol include/pyc.h declares (checked by the tests)
 EXPORTED = [
     "pyc_last_error", "pyc_version",
@@ -114,6 +119,8 @@ EXPORTED = [
     "pyc_scan_sync", "pyc_scan_launch_test", "pyc_expr_map_create", "pyc_expr_reduce_create",
     "pyc_expr_type", "pyc_pool_block_size", "pyc_pool_create", "pyc_pool_alloc", "pyc_pool_free",
     "pyc_pool_trim", "pyc_pool_get_stats", "pyc_pool_destroy",
+    "pyc_csr_create", "pyc_csr_width", "pyc_csr_set_width", "pyc_spmv", "pyc_spmv_autotune", "pyc_cg_solve",
+    "pyc_csr_destroy",
 ]
 
 _lib = None
@@ -175,6 +182,13 @@ def load(build_if_missing=True):
         "pyc_pool_trim": (st, [vp]),
         "pyc_pool_get_stats": (st, [vp, ctypes.POINTER(pyc_pool_stats)]),
         "pyc_pool_destroy": (None, [vp]),
+        "pyc_csr_create": (st, [i64, i64, i64, vp, vp, vp, i32, ctypes.POINTER(vp)]),
+        "pyc_csr_width": (st, [vp, ctypes.POINTER(i32)]),
+        "pyc_csr_set_width": (st, [vp, i32]),
+        "pyc_spmv": (st, [vp, vp, vp, vp]),
+        "pyc_spmv_autotune": (st, [vp, vp, vp, vp]),
+        "pyc_cg_solve": (st, [vp, vp, vp, ctypes.c_double, i64, vp, ctypes.POINTER(pyc_cg_info)]),
+        "pyc_csr_destroy": (None, [vp]),
         "pyc_scan_launch_test": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, i64, i64]),
         "pyc_scan_num_params": (i32, [vp]),
         "pyc_scan_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
@@ -428,6 +442,43 @@ def pool_empty(pool, n, dtype, stream=None):
         return pool_empty(pool, n, torch.int16, stream).view(torch.bfloat16)
     blk = _PoolBlock(pool, n, dtype, stream)
     return torch.as_tensor(blk, device="cuda")
+
+
+def pyc_csr_create(nrows, ncols, nnz, rowptr, colidx, vals, vt=PYC_F32):
+    h = ctypes.c_void_p()
+    _check(load().pyc_csr_create(int(nrows), int(ncols), int(nnz), rowptr, colidx, vals, int(vt),
+                                 ctypes.byref(h)))
+    return h
+
+
+def pyc_csr_width(a):
+    w = ctypes.c_int()
+    _check(load().pyc_csr_width(a, ctypes.byref(w)))
+    return w.value
+
+
+def pyc_csr_set_width(a, width):
+    _check(load().pyc_csr_set_width(a, int(width)))
+
+
+def pyc_spmv(a, x, y, stream=None):
+    _check(load().pyc_spmv(a, x, y, _stream(stream)))
+
+
+def pyc_spmv_autotune(a, x, y, stream=None):
+    _check(load().pyc_spmv_autotune(a, x, y, _stream(stream)))
+
+
+def pyc_cg_solve(a, b, x, rtol=1e-6, maxit=1000, stream=None):
+    info = pyc_cg_info()
+    _check(load().pyc_cg_solve(a, b, x, float(rtol), int(maxit), _stream(stream),
+                               ctypes.byref(info)))
+    return {"iterations": info.iterations, "residual": info.residual,
+            "converged": bool(info.converged)}
+
+
+def pyc_csr_destroy(a):
+    load().pyc_csr_destroy(a)
 
 
 def pyc_scan_sync(h, stream=None):

@@ -1,0 +1,111 @@
+"""CSR matrix-vector products and the CG solver on the GPU (Sec. 3.2.6),
+against the binary64 sparse oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sparse as osp
+from paper_1304_5553_gb300 import inputs, pyc
+
+pytestmark = pytest.mark.gpu
+
+U = {pyc.PYC_F32: 2.0 ** -24, pyc.PYC_F64: 2.0 ** -53}
+NP = {pyc.PYC_F32: np.float32, pyc.PYC_F64: np.float64}
+
+
+class Mat:
+    def __init__(self, rp, c, v, n, vt):
+        self.rp, self.c, self.v, self.n, self.vt = rp, c, v.astype(NP[vt]), n, vt
+        self.d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rp, c, self.v)]
+        self.h = pyc.pyc_csr_create(n, n, c.size, *(t.data_ptr() for t in self.d), vt)
+
+    def vec(self, a):
+        return torch.from_numpy(np.ascontiguousarray(a, NP[self.vt])).cuda()
+
+    def __del__(self):
+        pyc.pyc_csr_destroy(self.h)
+
+
+def _matrices(vt):
+    return [Mat(*inputs.poisson2d(300, 200), 60000, vt),
+            Mat(*inputs.random_spd(50000, 7, max_degree=2000, empty_every=11), 50000, vt)]
+
+
+@pytest.mark.parametrize("vt", [pyc.PYC_F32, pyc.PYC_F64])
+def test_spmv_every_width_within_bound(vt):
+    s = torch.cuda.current_stream().cuda_stream
+    for m in _matrices(vt):
+        x = np.random.default_rng(90).uniform(-1, 1, m.n).astype(NP[vt])
+        dx = m.vec(x)
+        dy = torch.empty(m.n, dtype=dx.dtype, device="cuda")
+        y64, ab = osp.spmv(m.rp, m.c, m.v, x)
+        length = np.diff(m.rp)
+        for w in (1, 2, 4, 8, 16, 32):
+            pyc.pyc_csr_set_width(m.h, w)
+            dy.fill_(np.nan)
+            pyc.pyc_spmv(m.h, dx.data_ptr(), dy.data_ptr(), s)
+            y = dy.cpu().numpy().astype(np.float64)
+            # a row is folded in at most len + 5 steps (lane runs, then a 5-level tree)
+            assert np.all(np.abs(y - y64) <= (length + 6) * U[vt] * ab), w
+        pyc.pyc_spmv_autotune(m.h, dx.data_ptr(), dy.data_ptr(), s)
+        assert pyc.pyc_csr_width(m.h) in (1, 2, 4, 8, 16, 32)
+
+
+def _true_residual(m, b, x):
+    return np.linalg.norm(b.astype(np.float64) - osp.spmv(m.rp, m.c, m.v, x)[0])
+
+
+def test_cg_f64_matches_the_oracle():
+    s = torch.cuda.current_stream().cuda_stream
+    rp, c, v = inputs.poisson2d(64, 64, np.float64)
+    m = Mat(rp, c, v, 4096, pyc.PYC_F64)
+    b = np.random.default_rng(91).standard_normal(4096)
+    db, dx = m.vec(b), m.vec(np.zeros(4096))
+    info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dx.data_ptr(), 1e-8, 5000, s)
+    x = dx.cpu().numpy()
+    xo, k, hist = osp.cg(rp, c, v, b, np.zeros(4096), 1e-8, 5000)
+    assert info["converged"] and abs(info["iterations"] - k) <= 2, (info, k)
+    assert _true_residual(m, b, x) <= 1e-8 * np.linalg.norm(b) * 1.01
+    assert abs(info["residual"] - hist[min(info["iterations"], len(hist) - 1)] /
+               np.linalg.norm(b)) <= 1e-9
+
+
+def test_cg_f32_and_irregular():
+    s = torch.cuda.current_stream().cuda_stream
+    rp, c, v = inputs.poisson2d(256, 256, np.float32)
+    m = Mat(rp, c, v, 65536, pyc.PYC_F32)
+    b = np.random.default_rng(92).uniform(-1, 1, 65536).astype(np.float32)
+    db, dx = m.vec(b), m.vec(np.zeros(65536))
+    info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dx.data_ptr(), 1e-4, 20000, s)
+    _, k, _ = osp.cg(rp, c, v.astype(np.float64), b, np.zeros(65536), 1e-4, 20000)
+    assert info["converged"] and 0.8 * k <= info["iterations"] <= 1.25 * k, (info, k)
+    assert _true_residual(m, b, dx.cpu().numpy()) <= 2e-4 * np.linalg.norm(b.astype(np.float64))
+    # irregular rows (log-uniform degrees up to 300), binary64
+    rp, c, v = inputs.random_spd(30000, 8, max_degree=300)
+    m2 = Mat(rp, c, v, 30000, pyc.PYC_F64)
+    b2 = np.random.default_rng(93).standard_normal(30000)
+    db2, dx2 = m2.vec(b2), m2.vec(np.zeros(30000))
+    info2 = pyc.pyc_cg_solve(m2.h, db2.data_ptr(), dx2.data_ptr(), 1e-10, 1000, s)
+    _, k2, _ = osp.cg(rp, c, v, b2, np.zeros(30000), 1e-10, 1000)
+    assert info2["converged"] and abs(info2["iterations"] - k2) <= 2
+    assert _true_residual(m2, b2, dx2.cpu().numpy()) <= 1e-10 * np.linalg.norm(b2) * 1.01
+
+
+def test_cg_edge_cases():
+    s = torch.cuda.current_stream().cuda_stream
+    rp, c, v = inputs.poisson2d(32, 32, np.float64)
+    m = Mat(rp, c, v, 1024, pyc.PYC_F64)
+    zero = m.vec(np.zeros(1024))
+    dx = m.vec(np.zeros(1024))
+    info = pyc.pyc_cg_solve(m.h, zero.data_ptr(), dx.data_ptr(), 1e-6, 100, s)
+    assert info["iterations"] == 0 and info["converged"] and not dx.any().item()
+    b = np.ones(1024)
+    xs, _, _ = osp.cg(rp, c, v, b, np.zeros(1024), 1e-13, 5000)
+    db, dx = m.vec(b), m.vec(xs)
+    info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dx.data_ptr(), 1e-6, 100, s)  # already solved
+    assert info["iterations"] == 0 and info["converged"]
+    dx = m.vec(np.zeros(1024))
+    info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dx.data_ptr(), 1e-12, 5, s)
+    assert info["iterations"] == 5 and not info["converged"]
+    _, _, hist = osp.cg(rp, c, v, b, np.zeros(1024), 1e-12, 5)
+    assert abs(info["residual"] - hist[5] / np.linalg.norm(b)) <= 1e-9
