@@ -351,8 +351,8 @@ def bench_cg(torch, pyc, dev, nx=2048, iters=100):
     """Sparse (Sec. 3.2.6): the 5-point Laplacian on an nx x nx grid (4.19 M
     unknowns, 21 M nonzeros at nx = 2048).  SpMV GB/s over its algorithmic bytes
     (values + column indices + row pointers + x once + y); CG time per step over
-    `iters` steps (rtol = 0), whose algorithmic bytes are one SpMV plus 12 vector
-    passes (p.q: 2, x and r update: 6, r.r: 1, p update: 3)."""
+    `iters` steps (rtol = 0), whose algorithmic bytes are one SpMV (p.q folded
+    in) plus 9 vector passes (x and r update with r.r folded in: 6, p update: 3)."""
     from paper_1304_5553_gb300 import inputs
     s = torch.cuda.current_stream().cuda_stream
     res = {}
@@ -380,7 +380,7 @@ def bench_cg(torch, pyc, dev, nx=2048, iters=100):
             e1.record()
             torch.cuda.synchronize()
             ms_cg = e0.elapsed_time(e1) / info["iterations"]
-            step_bytes = spmv_bytes + 12 * n * vb
+            step_bytes = spmv_bytes + 9 * n * vb
             res[name] = {"n": n, "nnz": int(c.size), "spmv_us": round(ms * 1e3, 1),
                          "spmv_GB/s": round(spmv_bytes / (ms * 1e-3) / 1e9, 1),
                          "lanes_per_row": pyc.pyc_csr_width(a),

@@ -7,11 +7,13 @@
 // folded per lane and then across the T lanes by a shuffle tree.  Warps step
 // over rows in lockstep (32 / T rows at a time), so the shuffles never diverge.
 //
-// CG (Hestenes and Stiefel) runs entirely on the device: the dot products are
-// the library's map-reduce, the vector updates its maps, and the step lengths
-// alpha = rs / (p.Ap) and beta = rs' / rs are read by those maps from device
-// memory, so the host synchronises only every few iterations to test
-// convergence.  After convergence the updates freeze (zero step lengths).
+// CG (Hestenes and Stiefel) runs entirely on the device.  Set-up (r = b - Ax,
+// p = r, r.r, b.b) uses the library's map and map-reduce kernels; each step is
+// three kernels of this module -- q = Ap with p.q folded in; the x and r
+// updates with r.r folded in (its last CTA also forms beta and counts the
+// step); p = r + beta p -- and the step lengths stay in device memory, so the
+// host synchronises only every 8 steps to test convergence.  After convergence
+// the updates freeze (zero step lengths).
 #include <algorithm>
 #include <iterator>
 #include <cmath>
@@ -62,9 +64,128 @@ PYC_SPMV(4)
 PYC_SPMV(8)
 PYC_SPMV(16)
 PYC_SPMV(32)
+
+// ---- fused conjugate-gradient step: 3 kernels.  s[0] = r.r, s[1] = p.Ap,
+// s[2] = tol^2, s[3] = new r.r, s[4] = b.b, s[5] = beta; it = steps taken.
+// Dot products are finished deterministically: per-CTA partials, then the last
+// CTA to arrive folds them in index order (fixed grid, fixed assignment).
+__device__ __forceinline__ V pyc_block_sum(V v) {
+  __shared__ V sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = 0;
+  if (w == 0) {
+    v = lane < nw ? sh[lane] : (V)0;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  }
+  return v;  // thread 0: the block's sum
+}
+// Thread 0 of every CTA passes its sum; returns true (in every thread) in the
+// last CTA to arrive, where *total = the partials folded in index order.
+__device__ __forceinline__ bool pyc_grid_sum(V mine, V* part, unsigned* ticket, V* total) {
+  __shared__ unsigned last;
+  __shared__ V res;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = mine;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  V v = 0;
+  for (unsigned j = threadIdx.x; j < gridDim.x; j += blockDim.x) v += __ldcg(part + j);
+  v = pyc_block_sum(v);
+  if (threadIdx.x == 0) {
+    res = v;
+    *ticket = 0u;
+  }
+  __syncthreads();
+  *total = res;
+  return true;
+}
+// q = A p and s[1] = p.q
+template <int T>
+__device__ __forceinline__ void pyc_cg_a(const pyc_i64* __restrict__ rowptr,
+    const int* __restrict__ col, const V* __restrict__ val, const V* __restrict__ p,
+    V* __restrict__ q, const pyc_i64 nrows, V* part, unsigned* ticket, V* s) {
+  constexpr int R = 32 / T;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % T;
+  const pyc_i64 warp = ((pyc_i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const pyc_i64 nwarps = ((pyc_i64)gridDim.x * blockDim.x) >> 5;
+  V dot = 0;
+  for (pyc_i64 base = warp * R; base < nrows; base += nwarps * R) {
+    const pyc_i64 r = base + lane / T;
+    V y = 0;
+    if (r < nrows) {
+      const pyc_i64 b = rowptr[r], e = rowptr[r + 1];
+      for (pyc_i64 k = b + sub; k < e; k += T) y += val[k] * __ldg(p + col[k]);
+    }
+#pragma unroll
+    for (int d = T / 2; d >= 1; d >>= 1) y += __shfl_down_sync(0xffffffffu, y, d, T);
+    if (sub == 0 && r < nrows) {
+      q[r] = y;
+      dot += p[r] * y;
+    }
+  }
+  V tot;
+  if (pyc_grid_sum(pyc_block_sum(dot), part, ticket, &tot) && threadIdx.x == 0) s[1] = tot;
+}
+#define PYC_CGA(T) \
+  extern "C" __global__ void __launch_bounds__(256) pyc_cg_a_t##T(const pyc_i64* rowptr, \
+      const int* col, const V* val, const V* p, V* q, const pyc_i64 nrows, V* part, \
+      unsigned* ticket, V* s) { \
+    pyc_cg_a<T>(rowptr, col, val, p, q, nrows, part, ticket, s); \
+  }
+PYC_CGA(1)
+PYC_CGA(2)
+PYC_CGA(4)
+PYC_CGA(8)
+PYC_CGA(16)
+PYC_CGA(32)
+// x += al p, r -= al q, s[3] = r.r; the last CTA sets beta and advances the step
+extern "C" __global__ void __launch_bounds__(256) pyc_cg_b(V* __restrict__ x,
+    V* __restrict__ r, const V* __restrict__ p, const V* __restrict__ q, const pyc_i64 n,
+    V* part, unsigned* ticket, V* s, pyc_i64* it) {
+  const V s0 = s[0], s1 = s[1], s2 = s[2];
+  const bool go = s0 > s2;
+  const V al = (go && s1 != 0) ? s0 / s1 : (V)0;
+  V acc = 0;
+  const pyc_i64 stride = (pyc_i64)gridDim.x * blockDim.x;
+  for (pyc_i64 i = (pyc_i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    x[i] += al * p[i];
+    const V ri = r[i] - al * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  V tot;
+  if (pyc_grid_sum(pyc_block_sum(acc), part, ticket, &tot) && threadIdx.x == 0) {
+    s[3] = tot;
+    s[5] = go ? tot / s0 : (V)0;
+    if (go) {
+      s[0] = tot;
+      it[0] += 1;
+    }
+  }
+}
+// p = r + beta p
+extern "C" __global__ void __launch_bounds__(256) pyc_cg_c(V* __restrict__ p,
+    const V* __restrict__ r, const pyc_i64 n, const V* __restrict__ s) {
+  const V be = s[5];
+  const pyc_i64 stride = (pyc_i64)gridDim.x * blockDim.x;
+  for (pyc_i64 i = (pyc_i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    p[i] = r[i] + be * p[i];
+}
 )PYC";
 
 const int kWidths[] = {1, 2, 4, 8, 16, 32};
+constexpr int kMaxPartials = 4096;  // CTAs of one CG-step launch (per-CTA partial sums)
 
 int default_width(int64_t nrows, int64_t nnz) {
   const double mean = nrows ? (double)nnz / (double)nrows : 1.0;
@@ -86,8 +207,7 @@ struct pyc_csr {
   // CG: step kernels (the library's map / map-reduce) and per-stream work space
   std::mutex mu;
   pyc_reduce_t dot = nullptr;
-  pyc_map_t init_r = nullptr, copy = nullptr, update_xr = nullptr, update_p = nullptr,
-            bookkeep = nullptr, set_tol = nullptr;
+  pyc_map_t init_r = nullptr, copy = nullptr, set_tol = nullptr;
   struct Work {
     CUdeviceptr base = 0;
     int64_t n = 0;
@@ -113,6 +233,14 @@ void launch_spmv(pyc_csr* a, int width, CUdeviceptr x, CUdeviceptr y, CUstream s
   PYC_CU(drv().cuLaunchKernel(f, grid, 1, 1, block, 1, 1, 0, s, params, nullptr));
 }
 
+// Grid of a CG vector kernel: resident CTAs, at most one per 256 elements and
+// at most kMaxPartials.
+unsigned cg_grid(CUfunction f, int64_t units) {
+  const int resident = resident_ctas(f, 256);
+  return (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)resident, (units + 255) / 256, (int64_t)kMaxPartials}));
+}
+
 void make_cg_kernels(pyc_csr* a) {
   std::lock_guard<std::mutex> lk(a->mu);
   if (a->dot) return;
@@ -129,15 +257,6 @@ void make_cg_kernels(pyc_csr* a) {
   if (st != PYC_OK) throw Error(st, pyc_last_error());
   a->init_r = mk(T + " *r, " + T + " *b, " + T + " *q", "r[i] = b[i] - q[i]", "cg_init");
   a->copy = mk(T + " *d, " + T + " *s", "d[i] = s[i]", "cg_copy");
-  a->update_xr = mk(T + " *x, " + T + " *r, " + T + " *p, " + T + " *q, " + T + " *s",
-                    T + " al = (s[0] > s[2] && s[1] != 0) ? s[0] / s[1] : (" + T +
-                        ")0; x[i] += al * p[i]; r[i] -= al * q[i]",
-                    "cg_xr");
-  a->update_p = mk(T + " *p, " + T + " *r, " + T + " *s",
-                   T + " be = s[0] > s[2] ? s[3] / s[0] : (" + T + ")0; p[i] = r[i] + be * p[i]",
-                   "cg_p");
-  a->bookkeep = mk(T + " *s, long long *it",
-                   "if (i == 0 && s[0] > s[2]) { s[0] = s[3]; it[0] += 1; }", "cg_step");
   a->set_tol = mk(T + " *s, double rtol2", "if (i == 0) s[2] = (" + T + ")(rtol2 * (double)s[4])",
                   "cg_tol");
 }
@@ -154,7 +273,7 @@ pyc_csr::Work& cg_work(pyc_csr* a, CUstream s, int64_t n) {
     }
     const int64_t vb = (int64_t)vbytes(a->vt);
     const int64_t vec = (n * vb + 255) / 256 * 256;
-    PYC_CU(drv().cuMemAlloc(&w.base, (size_t)(3 * vec + 256)));
+    PYC_CU(drv().cuMemAlloc(&w.base, (size_t)(3 * vec + 256 + kMaxPartials * vb)));
     w.n = n;
   }
   return w;
@@ -274,9 +393,13 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
     const int64_t vb = vbytes(a->vt);
     const int64_t vec = (n * vb + 255) / 256 * 256;
     const CUdeviceptr r = w.base, p = w.base + vec, q = w.base + 2 * vec;
-    const CUdeviceptr sc = w.base + 3 * vec;   // s[0..4]
+    const CUdeviceptr sc = w.base + 3 * vec;   // s[0..5]
     const CUdeviceptr it = sc + 8 * vb;       // iteration counter (int64)
+    CUdeviceptr ticket = sc + 128;            // last-CTA ticket of the step kernels
+    CUdeviceptr part = sc + 256;              // per-CTA partial sums
+    int64_t nn = n;
     const CUdeviceptr bx = reinterpret_cast<CUdeviceptr>(b), xx = reinterpret_cast<CUdeviceptr>(x);
+    CUdeviceptr xx_v = xx, sc_v = sc, it_v = it;
     PYC_CU(drv().cuMemsetD8Async(sc, 0, 256, s));
     int64_t iters = 0;
     double rs = 0, bb = 0, tol2 = 0;
@@ -291,6 +414,16 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
       map_launch(a->set_tol, 1, {sc}, &rt2, s);
       int64_t launched = 0;
       const int64_t chunk = 8;
+      CUfunction fa = a->mod->function("pyc_cg_a_t" + std::to_string(a->width));
+      CUfunction fb = a->mod->function("pyc_cg_b");
+      CUfunction fc = a->mod->function("pyc_cg_c");
+      const int64_t rows_per_cta = (int64_t)(256 / 32) * (32 / a->width);
+      const unsigned ga = cg_grid(fa, (n + rows_per_cta - 1) / rows_per_cta * 256);
+      const unsigned gb = cg_grid(fb, n), gc = cg_grid(fc, n);
+      CUdeviceptr pp = p, qq = q, rr = r;
+      void* pa[] = {&a->rowptr, &a->col, &a->val, &pp, &qq, &nn, &part, &ticket, &sc_v};
+      void* pb[] = {&xx_v, &rr, &pp, &qq, &nn, &part, &ticket, &sc_v, &it_v};
+      void* pc[] = {&pp, &rr, &nn, &sc_v};
       for (;;) {
         unsigned char host[64];
         PYC_CU(drv().cuMemcpyDtoHAsync(host, sc, 5 * vb, s));
@@ -307,12 +440,12 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
         if (!(rs > tol2) || launched >= maxit) break;
         const int64_t k = std::min<int64_t>(chunk, maxit - launched);
         for (int64_t j = 0; j < k; ++j) {
-          launch_spmv(a, a->width, p, q, s);                        // q = A p
-          dot_launch(a->dot, n, p, q, sc + vb, s);                  // s[1] = p.q
-          map_launch(a->update_xr, n, {xx, r, p, q, sc}, nullptr, s);  // x += al p, r -= al q
-          dot_launch(a->dot, n, r, r, sc + 3 * vb, s);              // s[3] = r.r
-          map_launch(a->update_p, n, {p, r, sc}, nullptr, s);       // p = r + be p
-          map_launch(a->bookkeep, 1, {sc, it}, nullptr, s);         // s[0] = s[3], it++
+          // q = A p, s[1] = p.q
+          PYC_CU(drv().cuLaunchKernel(fa, ga, 1, 1, 256, 1, 1, 0, s, pa, nullptr));
+          // x += al p, r -= al q, s[3] = r.r, beta, step count
+          PYC_CU(drv().cuLaunchKernel(fb, gb, 1, 1, 256, 1, 1, 0, s, pb, nullptr));
+          // p = r + beta p
+          PYC_CU(drv().cuLaunchKernel(fc, gc, 1, 1, 256, 1, 1, 0, s, pc, nullptr));
         }
         launched += k;
       }
@@ -331,7 +464,7 @@ PYC_API void pyc_csr_destroy(pyc_csr_t a) {
     for (auto& kv : a->work)
       if (kv.second.base) drv().cuMemFree(kv.second.base);
     pyc_reduce_destroy(a->dot);
-    for (pyc_map_t h : {a->init_r, a->copy, a->update_xr, a->update_p, a->bookkeep, a->set_tol})
+    for (pyc_map_t h : {a->init_r, a->copy, a->set_tol})
       pyc_map_destroy(h);
   } catch (...) {
   }
