@@ -454,10 +454,13 @@ typedef struct {
 /* Solve A x = b for symmetric positive definite A by conjugate gradients
  * (Hestenes-Stiefel): x holds the initial guess on entry and the solution on
  * exit (device, nrows elements; b likewise).  Stops when ||r|| <= rtol ||b|| or
- * after maxit steps.  Runs on `stream`; the host synchronises every 8 steps to
- * test convergence.  The handle keeps 3 vectors of work space per (context,
- * stream).  A breakdown (p.Ap = 0 before convergence) stops progress; the result
- * then reports converged = 0. */
+ * after maxit steps.  Runs on `stream`: steps are queued as CUDA graphs of 8
+ * (re-captured when x, the lanes per row or the work space change) with two
+ * groups in flight while the host tests the previous group's residual; steps
+ * queued past convergence change nothing.  The handle keeps 3 vectors of work
+ * space per (context, stream); one solve at a time per (handle, stream).  A
+ * breakdown (p.Ap = 0 before convergence) stops progress; the result then
+ * reports converged = 0. */
 pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol, int64_t maxit,
                         pyc_stream_t stream, pyc_cg_info* info);
 void pyc_csr_destroy(pyc_csr_t a);

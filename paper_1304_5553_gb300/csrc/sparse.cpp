@@ -12,8 +12,9 @@
 // three kernels of this module -- q = Ap with p.q folded in; the x and r
 // updates with r.r folded in (its last CTA also forms beta and counts the
 // step); p = r + beta p -- and the step lengths stay in device memory, so the
-// host synchronises only every 8 steps to test convergence.  After convergence
-// the updates freeze (zero step lengths).
+// host reads the scalars back every 8 steps (a CUDA graph of 8 steps, two in
+// flight, so the GPU does not wait for the host).  After convergence the updates
+// freeze (zero step lengths).
 #include <algorithm>
 #include <iterator>
 #include <cmath>
@@ -211,6 +212,14 @@ struct pyc_csr {
   struct Work {
     CUdeviceptr base = 0;
     int64_t n = 0;
+    // a graph of 8 steps for one x pointer, captured on a private stream
+    CUstream cap = nullptr;
+    CUgraphExec graph = nullptr;
+    CUdeviceptr graph_x = 0, graph_base = 0;
+    int graph_width = 0;
+    // page-locked read-back slots of the device scalars, one event each
+    unsigned char* host = nullptr;
+    CUevent ev[2] = {nullptr, nullptr};
   };
   std::map<std::pair<CUcontext, CUstream>, Work> work;
 };
@@ -412,7 +421,6 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
       dot_launch(a->dot, n, bx, bx, sc + 4 * vb, s);
       const double rt2 = rtol * rtol;
       map_launch(a->set_tol, 1, {sc}, &rt2, s);
-      int64_t launched = 0;
       const int64_t chunk = 8;
       CUfunction fa = a->mod->function("pyc_cg_a_t" + std::to_string(a->width));
       CUfunction fb = a->mod->function("pyc_cg_b");
@@ -424,30 +432,91 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
       void* pa[] = {&a->rowptr, &a->col, &a->val, &pp, &qq, &nn, &part, &ticket, &sc_v};
       void* pb[] = {&xx_v, &rr, &pp, &qq, &nn, &part, &ticket, &sc_v, &it_v};
       void* pc[] = {&pp, &rr, &nn, &sc_v};
-      for (;;) {
-        unsigned char host[64];
-        PYC_CU(drv().cuMemcpyDtoHAsync(host, sc, 5 * vb, s));
-        PYC_CU(drv().cuMemcpyDtoHAsync(host + 48, it, 8, s));
-        PYC_CU(drv().cuStreamSynchronize(s));
+      auto steps = [&](CUstream st, int64_t k) {
+        for (int64_t j = 0; j < k; ++j) {
+          // q = A p, s[1] = p.q
+          PYC_CU(drv().cuLaunchKernel(fa, ga, 1, 1, 256, 1, 1, 0, st, pa, nullptr));
+          // x += al p, r -= al q, s[3] = r.r, beta, step count
+          PYC_CU(drv().cuLaunchKernel(fb, gb, 1, 1, 256, 1, 1, 0, st, pb, nullptr));
+          // p = r + beta p
+          PYC_CU(drv().cuLaunchKernel(fc, gc, 1, 1, 256, 1, 1, 0, st, pc, nullptr));
+        }
+      };
+      {
+        std::lock_guard<std::mutex> lk(a->mu);
+        if (!w.host) {
+          void* h = nullptr;
+          PYC_CU(drv().cuMemAllocHost(&h, 256));
+          w.host = static_cast<unsigned char*>(h);
+          for (CUevent& e : w.ev) PYC_CU(drv().cuEventCreate(&e, CU_EVENT_DISABLE_TIMING));
+        }
+        if (w.graph && (w.graph_x != xx || w.graph_base != w.base || w.graph_width != a->width)) {
+          drv().cuGraphExecDestroy(w.graph);
+          w.graph = nullptr;
+        }
+        if (!w.graph && maxit >= chunk) {
+          if (!w.cap) PYC_CU(drv().cuStreamCreate(&w.cap, CU_STREAM_NON_BLOCKING));
+          PYC_CU(drv().cuStreamBeginCapture(w.cap, CU_STREAM_CAPTURE_MODE_RELAXED));
+          CUgraph g = nullptr;
+          try {
+            steps(w.cap, chunk);
+          } catch (...) {
+            drv().cuStreamEndCapture(w.cap, &g);
+            if (g) drv().cuGraphDestroy(g);
+            throw;
+          }
+          PYC_CU(drv().cuStreamEndCapture(w.cap, &g));
+          CUresult ir = drv().cuGraphInstantiateWithFlags(&w.graph, g, 0);
+          drv().cuGraphDestroy(g);
+          check(ir, "cuGraphInstantiateWithFlags");
+          w.graph_x = xx;
+          w.graph_base = w.base;
+          w.graph_width = a->width;
+        }
+      }
+      // read back s[0..5] and the step count of the chunk just queued
+      auto readback = [&](int slot) {
+        PYC_CU(drv().cuMemcpyDtoHAsync(w.host + 128 * slot, sc, 6 * vb, s));
+        PYC_CU(drv().cuMemcpyDtoHAsync(w.host + 128 * slot + 64, it, 8, s));
+        PYC_CU(drv().cuEventRecord(w.ev[slot], s));
+      };
+      auto consume = [&](int slot) {
+        PYC_CU(drv().cuEventSynchronize(w.ev[slot]));
+        const unsigned char* hb = w.host + 128 * slot;
         auto get = [&](int k) {
-          return a->vt == PYC_F64 ? reinterpret_cast<double*>(host)[k]
-                                  : (double)reinterpret_cast<float*>(host)[k];
+          return a->vt == PYC_F64 ? reinterpret_cast<const double*>(hb)[k]
+                                  : (double)reinterpret_cast<const float*>(hb)[k];
         };
         rs = get(0);
         tol2 = get(2);
         bb = get(4);
-        iters = *reinterpret_cast<int64_t*>(host + 48);
-        if (!(rs > tol2) || launched >= maxit) break;
-        const int64_t k = std::min<int64_t>(chunk, maxit - launched);
-        for (int64_t j = 0; j < k; ++j) {
-          // q = A p, s[1] = p.q
-          PYC_CU(drv().cuLaunchKernel(fa, ga, 1, 1, 256, 1, 1, 0, s, pa, nullptr));
-          // x += al p, r -= al q, s[3] = r.r, beta, step count
-          PYC_CU(drv().cuLaunchKernel(fb, gb, 1, 1, 256, 1, 1, 0, s, pb, nullptr));
-          // p = r + beta p
-          PYC_CU(drv().cuLaunchKernel(fc, gc, 1, 1, 256, 1, 1, 0, s, pc, nullptr));
+        iters = *reinterpret_cast<const int64_t*>(hb + 64);
+      };
+      readback(0);
+      consume(0);
+      // two chunks in flight: the GPU runs chunk c + 1 while the host checks c;
+      // steps after convergence are frozen, so running ahead changes nothing
+      int64_t launched = 0;
+      int slot = 0, inflight = 0;
+      int order[2];
+      while (rs > tol2 && (launched < maxit || inflight > 0)) {
+        while (inflight < 2 && launched < maxit) {
+          const int64_t k = std::min<int64_t>(chunk, maxit - launched);
+          if (k == chunk && w.graph) PYC_CU(drv().cuGraphLaunch(w.graph, s));
+          else steps(s, k);
+          readback(slot);
+          order[inflight++] = slot;
+          slot ^= 1;
+          launched += k;
         }
-        launched += k;
+        consume(order[0]);
+        order[0] = order[1];
+        --inflight;
+      }
+      while (inflight > 0) {  // let the queued chunks finish; keep the latest numbers
+        consume(order[0]);
+        order[0] = order[1];
+        --inflight;
       }
     }
     if (info) {
@@ -461,8 +530,15 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
 PYC_API void pyc_csr_destroy(pyc_csr_t a) {
   if (!a) return;
   try {
-    for (auto& kv : a->work)
-      if (kv.second.base) drv().cuMemFree(kv.second.base);
+    for (auto& kv : a->work) {
+      auto& w = kv.second;
+      if (w.graph) drv().cuGraphExecDestroy(w.graph);
+      if (w.cap) drv().cuStreamDestroy(w.cap);
+      if (w.host) drv().cuMemFreeHost(w.host);
+      for (CUevent e : w.ev)
+        if (e) drv().cuEventDestroy(e);
+      if (w.base) drv().cuMemFree(w.base);
+    }
     pyc_reduce_destroy(a->dot);
     for (pyc_map_t h : {a->init_r, a->copy, a->set_tol})
       pyc_map_destroy(h);
