@@ -637,6 +637,38 @@ def profile_scan(args):
                       "note": "profiling driver, not a bench value"}))
 
 
+def profile_cg(args):
+    """Profiling driver (not a bench line): CG on the 5-point Laplacian of an
+    nx x nx grid (binary32), a warm-up solve of 8 steps, then `steps` steps."""
+    import torch
+    from paper_1304_5553_gb300 import inputs, pyc
+    torch.cuda.set_device(0)
+    nx = 1 << (args.n_log2 // 2)
+    n = nx * nx
+    rp, c, v = inputs.poisson2d(nx, nx, np.float32)
+    d = [torch.from_numpy(a).cuda() for a in (rp, c, v)]
+    a = pyc.pyc_csr_create(n, n, c.size, *(t.data_ptr() for t in d), pyc.PYC_F32)
+    s = torch.cuda.current_stream().cuda_stream
+    b = torch.ones(n, dtype=torch.float32, device="cuda")
+    x = torch.zeros(n, dtype=torch.float32, device="cuda")
+    if args.autotune == "on":  # as the bench: time the lanes per row first
+        y = torch.empty(n, dtype=torch.float32, device="cuda")
+        pyc.pyc_spmv_autotune(a, b.data_ptr(), y.data_ptr(), s)
+    pyc.pyc_cg_solve(a, b.data_ptr(), x.data_ptr(), 0.0, 8, s)
+    x.zero_()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    info = pyc.pyc_cg_solve(a, b.data_ptr(), x.data_ptr(), 0.0, args.steps, s)
+    t1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_cg": "poisson2d %dx%d f32" % (nx, nx), "nnz": int(c.size),
+                      "lanes_per_row": pyc.pyc_csr_width(a), "steps": info["iterations"],
+                      "us_per_step": round(t0.elapsed_time(t1) * 1e3 / max(1, info["iterations"]), 1),
+                      "note": "profiling driver, not a bench value"}))
+    pyc.pyc_csr_destroy(a)
+
+
 def run_gpu(args):
     import torch
     from paper_1304_5553_gb300 import pyc, stock
@@ -778,6 +810,8 @@ def main():
                     help="profiling driver: time one stock reduction only (not a bench line)")
     ap.add_argument("--profile-scan", default="",
                     help="profiling driver: time one stock scan only (not a bench line)")
+    ap.add_argument("--profile-cg", action="store_true",
+                    help="profiling driver: CG steps on a Poisson matrix of 2^n_log2 rows")
     ap.add_argument("--config", default="",
                     help="with --profile-scan: fixed launch configuration, e.g. vec32_u4_b512")
     ap.add_argument("--autotune", default="on", choices=["on", "off"],
@@ -793,6 +827,8 @@ def main():
         profile_reduce(args)
     elif args.profile_scan:
         profile_scan(args)
+    elif args.profile_cg:
+        profile_cg(args)
     else:
         run_gpu(args)
 
