@@ -651,7 +651,9 @@ def profile_cg(args):
     s = torch.cuda.current_stream().cuda_stream
     b = torch.ones(n, dtype=torch.float32, device="cuda")
     x = torch.zeros(n, dtype=torch.float32, device="cuda")
-    if args.autotune == "on":  # as the bench: time the lanes per row first
+    if args.lanes:  # a fixed lanes-per-row count (no tuning launches)
+        pyc.pyc_csr_set_width(a, args.lanes)
+    elif args.autotune == "on":  # as the bench: time the lanes per row first
         y = torch.empty(n, dtype=torch.float32, device="cuda")
         pyc.pyc_spmv_autotune(a, b.data_ptr(), y.data_ptr(), s)
     pyc.pyc_cg_solve(a, b.data_ptr(), x.data_ptr(), 0.0, 8, s)
@@ -812,6 +814,8 @@ def main():
                     help="profiling driver: time one stock scan only (not a bench line)")
     ap.add_argument("--profile-cg", action="store_true",
                     help="profiling driver: CG steps on a Poisson matrix of 2^n_log2 rows")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="with --profile-cg: fixed lanes per row (1, 2, ..., 32)")
     ap.add_argument("--config", default="",
                     help="with --profile-scan: fixed launch configuration, e.g. vec32_u4_b512")
     ap.add_argument("--autotune", default="on", choices=["on", "off"],

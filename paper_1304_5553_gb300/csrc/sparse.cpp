@@ -150,16 +150,44 @@ PYC_CGA(4)
 PYC_CGA(8)
 PYC_CGA(16)
 PYC_CGA(32)
-// x += al p, r -= al q, s[3] = r.r; the last CTA sets beta and advances the step
-extern "C" __global__ void __launch_bounds__(256) pyc_cg_b(V* __restrict__ x,
-    V* __restrict__ r, const V* __restrict__ p, const V* __restrict__ q, const pyc_i64 n,
-    V* part, unsigned* ticket, V* s, pyc_i64* it) {
+// x += al p, r -= al q, s[3] = r.r; the last CTA sets beta and advances the step.
+// VEC: 16-byte accesses (x 16-byte aligned; the work vectors always are).
+struct __align__(16) pyc_vw {
+  V v[16 / sizeof(V)];
+};
+template <bool VEC>
+__device__ __forceinline__ void pyc_cg_b_body(V* __restrict__ x, V* __restrict__ r,
+    const V* __restrict__ p, const V* __restrict__ q, const pyc_i64 n, V* part,
+    unsigned* ticket, V* s, pyc_i64* it) {
+  constexpr int W = 16 / sizeof(V);
   const V s0 = s[0], s1 = s[1], s2 = s[2];
   const bool go = s0 > s2;
   const V al = (go && s1 != 0) ? s0 / s1 : (V)0;
   V acc = 0;
   const pyc_i64 stride = (pyc_i64)gridDim.x * blockDim.x;
-  for (pyc_i64 i = (pyc_i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  const pyc_i64 t0 = (pyc_i64)blockIdx.x * blockDim.x + threadIdx.x;
+  pyc_i64 done = 0;
+  if (VEC) {
+    const pyc_i64 nv = n / W;
+    pyc_vw* xv = reinterpret_cast<pyc_vw*>(x);
+    pyc_vw* rv = reinterpret_cast<pyc_vw*>(r);
+    const pyc_vw* pv = reinterpret_cast<const pyc_vw*>(p);
+    const pyc_vw* qv = reinterpret_cast<const pyc_vw*>(q);
+    for (pyc_i64 j = t0; j < nv; j += stride) {
+      pyc_vw xa = xv[j], ra = rv[j];
+      const pyc_vw pa = pv[j], qa = qv[j];
+#pragma unroll
+      for (int l = 0; l < W; ++l) {
+        xa.v[l] += al * pa.v[l];
+        ra.v[l] -= al * qa.v[l];
+        acc += ra.v[l] * ra.v[l];
+      }
+      xv[j] = xa;
+      rv[j] = ra;
+    }
+    done = nv * W;
+  }
+  for (pyc_i64 i = done + t0; i < n; i += stride) {
     x[i] += al * p[i];
     const V ri = r[i] - al * q[i];
     r[i] = ri;
@@ -175,13 +203,32 @@ extern "C" __global__ void __launch_bounds__(256) pyc_cg_b(V* __restrict__ x,
     }
   }
 }
-// p = r + beta p
+extern "C" __global__ void __launch_bounds__(256) pyc_cg_b(V* x, V* r, const V* p,
+    const V* q, const pyc_i64 n, V* part, unsigned* ticket, V* s, pyc_i64* it) {
+  pyc_cg_b_body<true>(x, r, p, q, n, part, ticket, s, it);
+}
+extern "C" __global__ void __launch_bounds__(256) pyc_cg_b_s(V* x, V* r, const V* p,
+    const V* q, const pyc_i64 n, V* part, unsigned* ticket, V* s, pyc_i64* it) {
+  pyc_cg_b_body<false>(x, r, p, q, n, part, ticket, s, it);
+}
+// p = r + beta p (16-byte accesses; p and r are work vectors)
 extern "C" __global__ void __launch_bounds__(256) pyc_cg_c(V* __restrict__ p,
     const V* __restrict__ r, const pyc_i64 n, const V* __restrict__ s) {
+  constexpr int W = 16 / sizeof(V);
   const V be = s[5];
   const pyc_i64 stride = (pyc_i64)gridDim.x * blockDim.x;
-  for (pyc_i64 i = (pyc_i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    p[i] = r[i] + be * p[i];
+  const pyc_i64 t0 = (pyc_i64)blockIdx.x * blockDim.x + threadIdx.x;
+  const pyc_i64 nv = n / W;
+  pyc_vw* pv = reinterpret_cast<pyc_vw*>(p);
+  const pyc_vw* rv = reinterpret_cast<const pyc_vw*>(r);
+  for (pyc_i64 j = t0; j < nv; j += stride) {
+    pyc_vw pa = pv[j];
+    const pyc_vw ra = rv[j];
+#pragma unroll
+    for (int l = 0; l < W; ++l) pa.v[l] = ra.v[l] + be * pa.v[l];
+    pv[j] = pa;
+  }
+  for (pyc_i64 i = nv * W + t0; i < n; i += stride) p[i] = r[i] + be * p[i];
 }
 )PYC";
 
@@ -423,11 +470,13 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
       map_launch(a->set_tol, 1, {sc}, &rt2, s);
       const int64_t chunk = 8;
       CUfunction fa = a->mod->function("pyc_cg_a_t" + std::to_string(a->width));
-      CUfunction fb = a->mod->function("pyc_cg_b");
+      // 16-byte accesses to x need a 16-byte aligned x (the work vectors are)
+      CUfunction fb = a->mod->function(xx % 16 == 0 ? "pyc_cg_b" : "pyc_cg_b_s");
       CUfunction fc = a->mod->function("pyc_cg_c");
       const int64_t rows_per_cta = (int64_t)(256 / 32) * (32 / a->width);
       const unsigned ga = cg_grid(fa, (n + rows_per_cta - 1) / rows_per_cta * 256);
-      const unsigned gb = cg_grid(fb, n), gc = cg_grid(fc, n);
+      const int64_t wv = 16 / vb;  // elements per 16-byte access
+      const unsigned gb = cg_grid(fb, (n + wv - 1) / wv), gc = cg_grid(fc, (n + wv - 1) / wv);
       CUdeviceptr pp = p, qq = q, rr = r;
       void* pa[] = {&a->rowptr, &a->col, &a->val, &pp, &qq, &nn, &part, &ticket, &sc_v};
       void* pb[] = {&xx_v, &rr, &pp, &qq, &nn, &part, &ticket, &sc_v, &it_v};

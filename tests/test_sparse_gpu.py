@@ -104,6 +104,13 @@ def test_cg_edge_cases():
     db, dx = m.vec(b), m.vec(xs)
     info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dx.data_ptr(), 1e-6, 100, s)  # already solved
     assert info["iterations"] == 0 and info["converged"]
+    # x not 16-byte aligned (an offset view): the element-wise update kernel
+    buf = m.vec(np.zeros(1025))
+    xv = buf[1:]
+    info = pyc.pyc_cg_solve(m.h, db.data_ptr(), xv.data_ptr(), 1e-9, 5000, s)
+    assert info["converged"]
+    assert _true_residual(m, b, xv.cpu().numpy()) <= 1e-9 * np.linalg.norm(b) * 1.01
+    assert buf[0].item() == 0
     dx = m.vec(np.zeros(1024))
     info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dx.data_ptr(), 1e-12, 5, s)
     assert info["iterations"] == 5 and not info["converged"]
