@@ -651,7 +651,7 @@ def profile_cg(args):
     s = torch.cuda.current_stream().cuda_stream
     b = torch.ones(n, dtype=torch.float32, device="cuda")
     x = torch.zeros(n, dtype=torch.float32, device="cuda")
-    if args.lanes:  # a fixed lanes-per-row count (no tuning launches)
+    if args.lanes is not None:  # a fixed width (no tuning launches)
         pyc.pyc_csr_set_width(a, args.lanes)
     elif args.autotune == "on":  # as the bench: time the lanes per row first
         y = torch.empty(n, dtype=torch.float32, device="cuda")
@@ -814,8 +814,9 @@ def main():
                     help="profiling driver: time one stock scan only (not a bench line)")
     ap.add_argument("--profile-cg", action="store_true",
                     help="profiling driver: CG steps on a Poisson matrix of 2^n_log2 rows")
-    ap.add_argument("--lanes", type=int, default=0,
-                    help="with --profile-cg: fixed lanes per row (1, 2, ..., 32)")
+    ap.add_argument("--lanes", type=int, default=None,
+                    help="with --profile-cg: fixed width (0: rows in chunks of 32; "
+                         "else lanes per row 1, 2, ..., 32)")
     ap.add_argument("--config", default="",
                     help="with --profile-scan: fixed launch configuration, e.g. vec32_u4_b512")
     ap.add_argument("--autotune", default="on", choices=["on", "off"],

@@ -33,6 +33,85 @@ namespace {
 const char* kSpmvSource = R"PYC(
 // CSR y = A x with T lanes per row (generated for one value type V)
 typedef long long pyc_i64;
+// L2 eviction policies (createpolicy).  A CG step keeps the work vectors that fit
+// in L2 together (evict_last) across its three kernels; the matrix, read once per
+// step, and the vectors that do not fit go first (evict_first).
+__device__ __forceinline__ unsigned long long pyc_pol(bool keep) {
+  unsigned long long p;
+  if (keep) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  else asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Loads with a policy: read-only data through the non-coherent path (not volatile,
+// so that the compiler may batch them); stores are ordered.
+__device__ __forceinline__ int pyc_ldnc(const int* a, unsigned long long pol) {
+  int v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ pyc_i64 pyc_ldnc(const pyc_i64* a, unsigned long long pol) {
+  pyc_i64 v;
+  asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float pyc_ldnc(const float* a, unsigned long long pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double pyc_ldnc(const double* a, unsigned long long pol) {
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void pyc_sth(float* a, float v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" :: "l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void pyc_sth(double* a, double v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" :: "l"(a), "d"(v), "l"(pol) : "memory");
+}
+// 16 bytes of V
+struct __align__(16) pyc_vw {
+  V v[16 / sizeof(V)];
+};
+// a thread loads and stores only its own 16-byte groups, so a load may move
+// freely except past the store of the same group, which depends on it
+__device__ __forceinline__ void pyc_ld16(const float* a, float* v, unsigned long long pol) {
+  asm("ld.global.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(a), "l"(pol));
+}
+__device__ __forceinline__ void pyc_ld16(const double* a, double* v, unsigned long long pol) {
+  asm("ld.global.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+      : "=d"(v[0]), "=d"(v[1]) : "l"(a), "l"(pol));
+}
+__device__ __forceinline__ void pyc_st16(float* a, const float* v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;"
+               :: "l"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void pyc_st16(double* a, const double* v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;"
+               :: "l"(a), "d"(v[0]), "d"(v[1]), "l"(pol) : "memory");
+}
+__device__ __forceinline__ pyc_vw pyc_ldv(const pyc_vw* a, unsigned long long pol) {
+  pyc_vw r;
+  pyc_ld16(a->v, r.v, pol);
+  return r;
+}
+__device__ __forceinline__ void pyc_stv(pyc_vw* a, const pyc_vw& r, unsigned long long pol) {
+  pyc_st16(a->v, r.v, pol);
+}
+// Returns the L2 lines of [a, a + bytes) to normal eviction priority (after a
+// solve, so that kept lines do not crowd later work).  Every 128-byte line
+// visited holds at least one byte of the range.
+extern "C" __global__ void __launch_bounds__(256) pyc_l2_release(const char* a,
+    const pyc_i64 bytes) {
+  const unsigned long long lo = (unsigned long long)a & ~127ull;
+  const unsigned long long hi = (unsigned long long)a + (unsigned long long)bytes;
+  const unsigned long long step = 128ull * gridDim.x * blockDim.x;
+  for (unsigned long long l = lo + 128ull * (blockIdx.x * blockDim.x + threadIdx.x); l < hi;
+       l += step)
+    asm volatile("applypriority.global.L2::evict_normal [%0], 128;" :: "l"(l) : "memory");
+}
 template <int T>
 __device__ __forceinline__ void pyc_spmv(const pyc_i64* __restrict__ rowptr,
     const int* __restrict__ col, const V* __restrict__ val, const V* __restrict__ x,
@@ -110,11 +189,13 @@ __device__ __forceinline__ bool pyc_grid_sum(V mine, V* part, unsigned* ticket, 
   *total = res;
   return true;
 }
-// q = A p and s[1] = p.q
+// q = A p and s[1] = p.q.  keep: bit 0 p, bit 1 r, bit 2 q, bit 3 x stay in L2.
 template <int T>
 __device__ __forceinline__ void pyc_cg_a(const pyc_i64* __restrict__ rowptr,
     const int* __restrict__ col, const V* __restrict__ val, const V* __restrict__ p,
-    V* __restrict__ q, const pyc_i64 nrows, V* part, unsigned* ticket, V* s) {
+    V* __restrict__ q, const pyc_i64 nrows, V* part, unsigned* ticket, V* s,
+    const unsigned keep) {
+  const unsigned long long pm = pyc_pol(false), pp = pyc_pol(keep & 1u), pq = pyc_pol(keep & 4u);
   constexpr int R = 32 / T;
   const int lane = threadIdx.x & 31;
   const int sub = lane % T;
@@ -125,14 +206,15 @@ __device__ __forceinline__ void pyc_cg_a(const pyc_i64* __restrict__ rowptr,
     const pyc_i64 r = base + lane / T;
     V y = 0;
     if (r < nrows) {
-      const pyc_i64 b = rowptr[r], e = rowptr[r + 1];
-      for (pyc_i64 k = b + sub; k < e; k += T) y += val[k] * __ldg(p + col[k]);
+      const pyc_i64 b = pyc_ldnc(rowptr + r, pm), e = pyc_ldnc(rowptr + r + 1, pm);
+      for (pyc_i64 k = b + sub; k < e; k += T)
+        y += pyc_ldnc(val + k, pm) * pyc_ldnc(p + pyc_ldnc(col + k, pm), pp);
     }
 #pragma unroll
     for (int d = T / 2; d >= 1; d >>= 1) y += __shfl_down_sync(0xffffffffu, y, d, T);
     if (sub == 0 && r < nrows) {
-      q[r] = y;
-      dot += p[r] * y;
+      pyc_sth(q + r, y, pq);
+      dot += pyc_ldnc(p + r, pp) * y;
     }
   }
   V tot;
@@ -141,8 +223,8 @@ __device__ __forceinline__ void pyc_cg_a(const pyc_i64* __restrict__ rowptr,
 #define PYC_CGA(T) \
   extern "C" __global__ void __launch_bounds__(256) pyc_cg_a_t##T(const pyc_i64* rowptr, \
       const int* col, const V* val, const V* p, V* q, const pyc_i64 nrows, V* part, \
-      unsigned* ticket, V* s) { \
-    pyc_cg_a<T>(rowptr, col, val, p, q, nrows, part, ticket, s); \
+      unsigned* ticket, V* s, const unsigned keep) { \
+    pyc_cg_a<T>(rowptr, col, val, p, q, nrows, part, ticket, s, keep); \
   }
 PYC_CGA(1)
 PYC_CGA(2)
@@ -151,14 +233,12 @@ PYC_CGA(8)
 PYC_CGA(16)
 PYC_CGA(32)
 // x += al p, r -= al q, s[3] = r.r; the last CTA sets beta and advances the step.
-// VEC: 16-byte accesses (x 16-byte aligned; the work vectors always are).
-struct __align__(16) pyc_vw {
-  V v[16 / sizeof(V)];
-};
+// VEC: 16-byte accesses with L2 policies (x 16-byte aligned; the work vectors
+// always are).
 template <bool VEC>
 __device__ __forceinline__ void pyc_cg_b_body(V* __restrict__ x, V* __restrict__ r,
     const V* __restrict__ p, const V* __restrict__ q, const pyc_i64 n, V* part,
-    unsigned* ticket, V* s, pyc_i64* it) {
+    unsigned* ticket, V* s, pyc_i64* it, const unsigned keep) {
   constexpr int W = 16 / sizeof(V);
   const V s0 = s[0], s1 = s[1], s2 = s[2];
   const bool go = s0 > s2;
@@ -173,17 +253,19 @@ __device__ __forceinline__ void pyc_cg_b_body(V* __restrict__ x, V* __restrict__
     pyc_vw* rv = reinterpret_cast<pyc_vw*>(r);
     const pyc_vw* pv = reinterpret_cast<const pyc_vw*>(p);
     const pyc_vw* qv = reinterpret_cast<const pyc_vw*>(q);
+    const unsigned long long pp = pyc_pol(keep & 1u), pr = pyc_pol(keep & 2u),
+                             pq = pyc_pol(keep & 4u), px = pyc_pol(keep & 8u);
     for (pyc_i64 j = t0; j < nv; j += stride) {
-      pyc_vw xa = xv[j], ra = rv[j];
-      const pyc_vw pa = pv[j], qa = qv[j];
+      pyc_vw xa = pyc_ldv(xv + j, px), ra = pyc_ldv(rv + j, pr);
+      const pyc_vw pa = pyc_ldv(pv + j, pp), qa = pyc_ldv(qv + j, pq);
 #pragma unroll
       for (int l = 0; l < W; ++l) {
         xa.v[l] += al * pa.v[l];
         ra.v[l] -= al * qa.v[l];
         acc += ra.v[l] * ra.v[l];
       }
-      xv[j] = xa;
-      rv[j] = ra;
+      pyc_stv(xv + j, xa, px);
+      pyc_stv(rv + j, ra, pr);
     }
     done = nv * W;
   }
@@ -204,16 +286,18 @@ __device__ __forceinline__ void pyc_cg_b_body(V* __restrict__ x, V* __restrict__
   }
 }
 extern "C" __global__ void __launch_bounds__(256) pyc_cg_b(V* x, V* r, const V* p,
-    const V* q, const pyc_i64 n, V* part, unsigned* ticket, V* s, pyc_i64* it) {
-  pyc_cg_b_body<true>(x, r, p, q, n, part, ticket, s, it);
+    const V* q, const pyc_i64 n, V* part, unsigned* ticket, V* s, pyc_i64* it,
+    const unsigned keep) {
+  pyc_cg_b_body<true>(x, r, p, q, n, part, ticket, s, it, keep);
 }
 extern "C" __global__ void __launch_bounds__(256) pyc_cg_b_s(V* x, V* r, const V* p,
-    const V* q, const pyc_i64 n, V* part, unsigned* ticket, V* s, pyc_i64* it) {
-  pyc_cg_b_body<false>(x, r, p, q, n, part, ticket, s, it);
+    const V* q, const pyc_i64 n, V* part, unsigned* ticket, V* s, pyc_i64* it,
+    const unsigned keep) {
+  pyc_cg_b_body<false>(x, r, p, q, n, part, ticket, s, it, keep);
 }
 // p = r + beta p (16-byte accesses; p and r are work vectors)
 extern "C" __global__ void __launch_bounds__(256) pyc_cg_c(V* __restrict__ p,
-    const V* __restrict__ r, const pyc_i64 n, const V* __restrict__ s) {
+    const V* __restrict__ r, const pyc_i64 n, const V* __restrict__ s, const unsigned keep) {
   constexpr int W = 16 / sizeof(V);
   const V be = s[5];
   const pyc_i64 stride = (pyc_i64)gridDim.x * blockDim.x;
@@ -221,12 +305,13 @@ extern "C" __global__ void __launch_bounds__(256) pyc_cg_c(V* __restrict__ p,
   const pyc_i64 nv = n / W;
   pyc_vw* pv = reinterpret_cast<pyc_vw*>(p);
   const pyc_vw* rv = reinterpret_cast<const pyc_vw*>(r);
+  const unsigned long long pp = pyc_pol(keep & 1u), pr = pyc_pol(keep & 2u);
   for (pyc_i64 j = t0; j < nv; j += stride) {
-    pyc_vw pa = pv[j];
-    const pyc_vw ra = rv[j];
+    pyc_vw pa = pyc_ldv(pv + j, pp);
+    const pyc_vw ra = pyc_ldv(rv + j, pr);
 #pragma unroll
     for (int l = 0; l < W; ++l) pa.v[l] = ra.v[l] + be * pa.v[l];
-    pv[j] = pa;
+    pyc_stv(pv + j, pa, pp);
   }
   for (pyc_i64 i = nv * W + t0; i < n; i += stride) p[i] = r[i] + be * p[i];
 }
@@ -291,6 +376,21 @@ void launch_spmv(pyc_csr* a, int width, CUdeviceptr x, CUdeviceptr y, CUstream s
 
 // Grid of a CG vector kernel: resident CTAs, at most one per 256 elements and
 // at most kMaxPartials.
+// Work vectors a CG step keeps in L2 (bit 0 p, bit 1 r, bit 2 q, bit 3 x, in
+// order of use): as many as fit together in 9/16 of L2; the matrix streams
+// through the rest.
+unsigned cg_keep(int64_t vec_bytes) {
+  const int64_t budget = (int64_t)current_device_props().l2_bytes * 9 / 16;
+  unsigned keep = 0;
+  int64_t used = 0;
+  for (unsigned bit : {1u, 2u, 4u, 8u}) {
+    if (used + vec_bytes > budget) break;
+    used += vec_bytes;
+    keep |= bit;
+  }
+  return keep;
+}
+
 unsigned cg_grid(CUfunction f, int64_t units) {
   const int resident = resident_ctas(f, 256);
   return (unsigned)std::max<int64_t>(
@@ -478,9 +578,10 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
       const int64_t wv = 16 / vb;  // elements per 16-byte access
       const unsigned gb = cg_grid(fb, (n + wv - 1) / wv), gc = cg_grid(fc, (n + wv - 1) / wv);
       CUdeviceptr pp = p, qq = q, rr = r;
-      void* pa[] = {&a->rowptr, &a->col, &a->val, &pp, &qq, &nn, &part, &ticket, &sc_v};
-      void* pb[] = {&xx_v, &rr, &pp, &qq, &nn, &part, &ticket, &sc_v, &it_v};
-      void* pc[] = {&pp, &rr, &nn, &sc_v};
+      unsigned keep = cg_keep(n * vb);
+      void* pa[] = {&a->rowptr, &a->col, &a->val, &pp, &qq, &nn, &part, &ticket, &sc_v, &keep};
+      void* pb[] = {&xx_v, &rr, &pp, &qq, &nn, &part, &ticket, &sc_v, &it_v, &keep};
+      void* pc[] = {&pp, &rr, &nn, &sc_v, &keep};
       auto steps = [&](CUstream st, int64_t k) {
         for (int64_t j = 0; j < k; ++j) {
           // q = A p, s[1] = p.q
@@ -566,6 +667,17 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
         consume(order[0]);
         order[0] = order[1];
         --inflight;
+      }
+      // kept vectors back to normal eviction priority
+      CUfunction fr = a->mod->function("pyc_l2_release");
+      const unsigned gr = cg_grid(fr, (n * vb + 127) / 128);
+      const CUdeviceptr vecs[] = {p, r, q, xx};
+      for (int k = 0; k < 4; ++k) {
+        if (!(keep & (1u << k))) continue;
+        CUdeviceptr v = vecs[k];
+        int64_t bytes = n * vb;
+        void* pr[] = {&v, &bytes};
+        PYC_CU(drv().cuLaunchKernel(fr, gr, 1, 1, 256, 1, 1, 0, s, pr, nullptr));
       }
     }
     if (info) {
