@@ -160,16 +160,20 @@ pyc_status pyc_map_launch(pyc_map_t h, int64_t n, void* const* ptrs, const void*
                           pyc_stream_t stream);
 
 /* Run a map on HOST arrays and return when the results are in host memory.
- * The arrays are streamed through device staging buffers in chunks of 2^22
- * elements, overlapping host-to-device copies, kernels and device-to-host
- * copies on three streams of the library's own.  Arrays the statement reads
- * are copied in and arrays it writes are copied back (one it may leave
- * unwritten is also copied in).  Every array must be accessed as name[i] alone
- * (an elementwise statement), else PYC_E_ARG.  host_ptrs: one host pointer per
- * array; page-locked memory gives full copy bandwidth.  The staging buffers
- * (three chunks of every array) are allocated by the first call and kept by the
- * handle.  Synchronous: returns after the last copy back.  Errors as for
- * pyc_map_launch. */
+ * Every array must be accessed as name[i] alone (an elementwise statement),
+ * else PYC_E_ARG.  host_ptrs: one host pointer per array.
+ * If every array's n elements lie in page-locked host memory that the driver
+ * maps into the device's address space at the same address (cuMemAllocHost,
+ * cudaHostAlloc or registered memory, under unified addressing), the kernel runs
+ * on the host arrays themselves: its loads and stores cross the chip-to-chip
+ * link, with no staging copies.  Otherwise the arrays are streamed through
+ * device staging buffers in chunks of 2^22 elements, overlapping host-to-device
+ * copies, kernels and device-to-host copies on three streams of the library's
+ * own: arrays the statement reads are copied in and arrays it writes are copied
+ * back (one it may leave unwritten is also copied in); the staging buffers
+ * (three chunks of every array) are allocated by the first staged call and kept
+ * by the handle.  Synchronous: returns when the results are in host memory.
+ * Errors as for pyc_map_launch. */
 pyc_status pyc_map_launch_host(pyc_map_t h, int64_t n, void* const* host_ptrs,
                                const void* scalars);
 

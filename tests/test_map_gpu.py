@@ -232,8 +232,10 @@ def test_launch_argument_errors():
 
 @pytest.mark.parametrize("bf16", [False, True])
 def test_host_array_launch(bf16):
-    """pyc_map_launch_host on page-locked host arrays: several chunks plus a
-    ragged tail, bit-exact against binary32 source order; in-place too."""
+    """pyc_map_launch_host on page-locked host arrays (the kernel runs on them
+    directly) and on pageable ones (staged through device buffers): several
+    chunks plus a ragged tail, bit-exact against binary32 source order; in-place
+    too; an offset prefix of a page-locked allocation."""
     n = 3 * (1 << 22) + 12345
     x = inputs.uniform_f32(40, 0, n, -2.0, 2.0)
     y = inputs.uniform_f32(40, 1, n, -2.0, 2.0)
@@ -250,6 +252,22 @@ def test_host_array_launch(bf16):
     a = torch.from_numpy(x.astype(np.float32)).pin_memory()
     pyc.pyc_map_launch_host(stock.create("scale2_f32"), n, [a.data_ptr()])
     assert np.array_equal(a.numpy(), oracle.map_scale(2, x)[0])
+    # pageable inputs (numpy memory, not mapped into the device): the staged path
+    px = torch.from_numpy(x).to(dt)
+    py = torch.from_numpy(y).to(dt)
+    hz.fill_(-4096.0)
+    pyc.pyc_map_launch_host(h, n, [px.data_ptr(), py.data_ptr(), hz.data_ptr()],
+                            pyc.pack_scalars(h, [A, B]))
+    assert np.array_equal(hz.float().numpy(), oracle.map_lin_comb_f32ops(A, x, B, y, out_bf16=bf16))
+    # page-locked, but the launch covers a prefix of a larger allocation, at an offset
+    m = n - 1000
+    hz.fill_(-4096.0)
+    pyc.pyc_map_launch_host(h, m, [hx.data_ptr() + 2 * hx.element_size(),
+                                   hy.data_ptr() + 2 * hy.element_size(), hz.data_ptr()],
+                            pyc.pack_scalars(h, [A, B]))
+    want = oracle.map_lin_comb_f32ops(A, x[2:m + 2], B, y[2:m + 2], out_bf16=bf16)
+    assert np.array_equal(hz[:m].float().numpy(), want)
+    assert (hz[m:].float() == -4096.0).all()
     with pytest.raises(pyc.PycError) as e:  # not elementwise: rejected
         k = pyc.pyc_map_create("float *x, float *z", "z[i] = i + 1 < n ? x[i + 1] : 0.0f")
         pyc.pyc_map_launch_host(k, 10, [hx.data_ptr(), hz.data_ptr()])

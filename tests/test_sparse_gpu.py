@@ -26,9 +26,22 @@ class Mat:
         pyc.pyc_csr_destroy(self.h)
 
 
+def _mixed(n, seed):
+    """Rows of 3 entries, every 7th empty, and a band of 40-entry rows."""
+    rng = np.random.default_rng(seed)
+    deg = np.full(n, 3, np.int64)
+    deg[2560:3840] = 40
+    deg[::7] = 0
+    rp = np.r_[0, np.cumsum(deg)].astype(np.int64)
+    c = rng.integers(0, n, rp[-1]).astype(np.int32)
+    v = rng.uniform(-1, 1, rp[-1])
+    return rp, c, v
+
+
 def _matrices(vt):
     return [Mat(*inputs.poisson2d(300, 200), 60000, vt),
-            Mat(*inputs.random_spd(50000, 7, max_degree=2000, empty_every=11), 50000, vt)]
+            Mat(*inputs.random_spd(50000, 7, max_degree=2000, empty_every=11), 50000, vt),
+            Mat(*_mixed(20011, 17), 20011, vt)]
 
 
 @pytest.mark.parametrize("vt", [pyc.PYC_F32, pyc.PYC_F64])
