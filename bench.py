@@ -169,9 +169,11 @@ def time_steps(torch, launchers, names, steps, warmup, barrier):
 
 def bench_e2e(torch, pyc, stock, host, dev, steps=3, warmup=1):
     """Same step through the C ABI with HOST buffers: pyc_map_launch_host on
-    page-locked host arrays; it copies the inputs in and the output back (chunked,
-    overlapped on three streams) inside the timed region, and returns when the
-    output is in host memory."""
+    page-locked host arrays, inside the timed region.  The arrays are mapped into
+    the device's address space, so each kernel loads its inputs from host memory
+    and stores its output there over the chip-to-chip link (pageable arrays would
+    be staged through device buffers instead); it returns when the output is in
+    host memory."""
     pinned = {k: [torch.from_numpy(a).to(torch.bfloat16 if k.endswith("bf16") else torch.float32)
                   .pin_memory() for a in arrs] for k, arrs in host.items()}
     outs_h = {k: torch.empty(N_MAP, dtype=pinned[k][0].dtype).pin_memory() for k in pinned}
