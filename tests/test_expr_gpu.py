@@ -149,3 +149,27 @@ def test_one_compile_per_shape():
         got = _host(ga.evaluate(X * c + Y))
         assert np.array_equal(got, ox.eval_f32(("+", ("*", x, np.float32(c)), y)))
     assert pyc.pyc_cache_stats()["compiled"] == before["compiled"]
+
+
+def test_full_size_sampled():
+    """The bench's expressions at n = 2^28, tuned as the bench tunes them: every
+    4096th element and the last 4096 against the oracle (bit-exact for the
+    correctly rounded tree, within the first-order bound for the other)."""
+    n = 1 << 28
+    xs = [inputs.uniform_f32(1, s, n, -2.0, 2.0) for s in range(4)]
+    X, Y, U, W = (_dev(a) for a in xs)
+    idx = np.concatenate([np.arange(0, n, 4096), np.arange(n - 4096, n)])
+    x, y, u, w = (a[idx] for a in xs)
+    out = ga.GArray(torch.empty(n, dtype=torch.float32, device="cuda"))
+    e = 2.5 * X - 0.75 * Y
+    ga.autotune(e)
+    ga.evaluate(e, out=out)
+    want = ox.eval_f32(("-", ("*", np.float32(2.5), x), ("*", np.float32(0.75), y)))
+    assert np.array_equal(_host(out)[idx], want)
+    e = X * ga.exp(-(Y * Y)) + ga.sin(U) * W
+    ga.autotune(e)
+    ga.evaluate(e, out=out)
+    v, err = ox.eval_bound(("+", ("*", x, ("exp", ("neg", ("*", y, y)))), ("*", ("sin", u), w)))
+    assert np.all(np.abs(_host(out)[idx].astype(np.float64) - v) <= err * (1 + 1e-6) + 1e-30)
+    del X, Y, U, W, out
+    torch.cuda.empty_cache()

@@ -129,3 +129,39 @@ def test_cg_edge_cases():
     assert info["iterations"] == 5 and not info["converged"]
     _, _, hist = osp.cg(rp, c, v, b, np.zeros(1024), 1e-12, 5)
     assert abs(info["residual"] - hist[5] / np.linalg.norm(b)) <= 1e-9
+
+
+@pytest.mark.parametrize("vt", [pyc.PYC_F32, pyc.PYC_F64])
+def test_full_size_laplacian(vt):
+    """The bench's system, the 5-point Laplacian on 2048 x 2048 (4.19 M rows),
+    tuned as the bench tunes it: the product on every 1024th row and the last
+    1024 within the bound; 20 CG steps from x = 0 with b = 1 against the
+    oracle's 20 steps (binary64: to 1e-9; binary32: to 1e-3)."""
+    s = torch.cuda.current_stream().cuda_stream
+    nx = 2048
+    n = nx * nx
+    rp, c, v = inputs.poisson2d(nx, nx, NP[vt])
+    m = Mat(rp, c, v, n, vt)
+    x = np.random.default_rng(9).uniform(-1, 1, n).astype(NP[vt])
+    dx = m.vec(x)
+    dy = torch.empty(n, dtype=dx.dtype, device="cuda")
+    pyc.pyc_spmv_autotune(m.h, dx.data_ptr(), dy.data_ptr(), s)
+    pyc.pyc_spmv(m.h, dx.data_ptr(), dy.data_ptr(), s)
+    y = dy.cpu().numpy().astype(np.float64)
+    y64, ab = osp.spmv(rp, c, v, x)
+    idx = np.concatenate([np.arange(0, n, 1024), np.arange(n - 1024, n)])
+    length = np.diff(rp)[idx]
+    assert np.all(np.abs(y[idx] - y64[idx]) <= (length + 6) * U[vt] * ab[idx])
+    b = np.ones(n)
+    db, dxs = m.vec(b), m.vec(np.zeros(n))
+    info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dxs.data_ptr(), 0.0, 20, s)
+    assert info["iterations"] == 20 and not info["converged"]
+    xo, k, hist = osp.cg(rp, c, v.astype(np.float64), b, np.zeros(n), 0.0, 20)
+    assert k == 20
+    tol = 1e-9 if vt == pyc.PYC_F64 else 1e-3
+    xg = dxs.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(xg - xo) <= tol * np.linalg.norm(xo)
+    r20 = hist[20] / np.linalg.norm(b)
+    assert abs(info["residual"] - r20) <= tol * r20
+    del m, dx, dy, db, dxs
+    torch.cuda.empty_cache()
