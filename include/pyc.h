@@ -484,7 +484,9 @@ void pyc_csr_destroy(pyc_csr_t a);
  * requests of its batch.  The server owns a device arena (arena_bytes) for map
  * outputs it allocates: a written-only array of a map request may be passed as
  * NULL and is then allocated from the arena (returned in pyc_result.d_out) and
- * kept until pyc_server_release. */
+ * kept until pyc_server_release.  It starts at the address of the request's
+ * first given array modulo 256 (rounded down to its element size), so that all
+ * of the request's arrays can take the vector path together. */
 typedef struct pyc_server* pyc_server_t;
 
 #define PYC_REQ_MAP 0

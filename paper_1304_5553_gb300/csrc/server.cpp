@@ -138,6 +138,21 @@ struct Batch {
   int out_bytes = 0;
 };
 
+// Offset (bytes, below 256) at which a server-allocated output starts inside
+// its arena block (256-byte granules): the address of the request's first given
+// array modulo 256, rounded down to the output's element size.  Arrays at equal
+// addresses modulo the vector width take the vector path together; inputs at
+// arbitrary element offsets would otherwise leave a 256-byte-aligned output
+// alone and the whole request element-wise.
+int64_t align_shift(const HandleBase& h, void* const* ptrs, int64_t out_eb) {
+  for (auto& q : h.spec.params)
+    if (q.is_ptr && q.lifted && ptrs[q.ptr_slot]) {
+      const int64_t m = (int64_t)(reinterpret_cast<uintptr_t>(ptrs[q.ptr_slot]) % 256);
+      return m / out_eb * out_eb;
+    }
+  return 0;
+}
+
 // Launch configuration the server uses for a handle's batches: fixed per
 // handle so that a request's result never depends on its batch.
 LaunchCfg batch_cfg(HandleBase& h, bool reduce) { return batched_cfg(h, reduce); }
@@ -292,8 +307,8 @@ void retire(pyc_server* s, Batch& b, int status) {
     SReq* r = b.reqs[k];
     if (status == PYC_OK && b.kind == PYC_REQ_REDUCE)
       std::memcpy(r->res.value, sl.host + b.res_host_off + (int64_t)k * b.out_bytes, b.out_bytes);
-    if (status == PYC_OK && b.kind == PYC_REQ_MAP && !r->out_offs.empty())
-      r->res.d_out = reinterpret_cast<void*>(s->arena_mem + r->out_offs[0]);
+    if (status == PYC_OK && b.kind == PYC_REQ_MAP && !r->alloc_slots.empty())
+      r->res.d_out = r->ptrs[r->alloc_slots[0]];
     finish_req(s, r, status, t);
   }
   sl.busy = false;
@@ -342,12 +357,14 @@ void scheduler(pyc_server* s) {
         const Param* p = nullptr;
         for (auto& q : r->mh->spec.params)
           if (q.is_ptr && q.ptr_slot == slot) p = &q;
-        if (!s->arena.alloc(r->n * type_info(p->dtype).bytes, &off)) {
+        const int64_t eb = type_info(p->dtype).bytes;
+        const int64_t shift = align_shift(*r->mh, r->ptrs.data(), eb);
+        if (!s->arena.alloc(r->n * eb + shift, &off)) {
           ok = false;
           break;
         }
         r->out_offs.push_back(off);
-        r->ptrs[slot] = reinterpret_cast<void*>(s->arena_mem + off);
+        r->ptrs[slot] = reinterpret_cast<void*>(s->arena_mem + off + shift);
       }
       if (!ok) {
         for (int64_t off : r->out_offs) s->arena.release(off);
@@ -742,6 +759,7 @@ void replay_direct(pyc_server* s, int64_t nreq, const pyc_request* reqs, const i
   struct Out {
     int64_t k;
     std::vector<int64_t> offs;
+    void* out = nullptr;  // first server-allocated output
     CUdeviceptr val = 0;
   };
   std::deque<Out> pending;  // launched, in stream order
@@ -792,13 +810,16 @@ void replay_direct(pyc_server* s, int64_t nreq, const pyc_request* reqs, const i
       for (auto& p : h->spec.params)
         if (p.is_ptr && !ptrs[p.ptr_slot] && q.kind == PYC_REQ_MAP) {
           int64_t off;
+          const int64_t eb = type_info(p.dtype).bytes;
+          const int64_t shift = align_shift(*h, ptrs.data(), eb);
           std::lock_guard<std::mutex> lk(s->mu);
-          if (!s->arena.alloc(q.n * type_info(p.dtype).bytes, &off)) {
+          if (!s->arena.alloc(q.n * eb + shift, &off)) {
             ok = false;
             break;
           }
           o.offs.push_back(off);
-          ptrs[p.ptr_slot] = reinterpret_cast<void*>(s->arena_mem + off);
+          ptrs[p.ptr_slot] = reinterpret_cast<void*>(s->arena_mem + off + shift);
+          if (!o.out) o.out = ptrs[p.ptr_slot];
         }
       if (!ok) {  // arena full: wait for the oldest launch, then retry
         {
@@ -813,7 +834,7 @@ void replay_direct(pyc_server* s, int64_t nreq, const pyc_request* reqs, const i
       if (q.kind == PYC_REQ_MAP) {
         pyc_map* h2 = static_cast<pyc_map*>(q.handle);
         launch_map(h2, choose_cfg(*h2, q.n, false), q.n, ptrs.data(), q.scalars, st);
-        if (!o.offs.empty()) r.d_out = reinterpret_cast<void*>(s->arena_mem + o.offs[0]);
+        if (o.out) r.d_out = o.out;
       } else {
         pyc_reduce* h2 = static_cast<pyc_reduce*>(q.handle);
         o.val = vals + (next % kEvents) * 16;
