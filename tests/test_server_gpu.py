@@ -78,6 +78,8 @@ def test_alone_and_in_the_mix_are_identical(pools):
             rid, res = _run_one(srv, req)
             val = bytes(res.value)
             out = _map_out(res, p[2]).cpu().numpy().copy() if p[0] == pyc.PYC_REQ_MAP else None
+            if p[0] == pyc.PYC_REQ_MAP:  # the output shares its inputs' address mod 256
+                assert res.d_out % 256 == (dev["x"].data_ptr() + 4 * p[3]) % 256
             pyc.pyc_server_release(srv, rid)
             alone.append((val, out))
         blocker = pyc.make_request(pyc.PYC_REQ_REDUCE, stock.create("dot_f32"), nb,
