@@ -231,9 +231,26 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
     pyc.pyc_reduce_autotune(h, m, s)
     f = lambda: pyc.pyc_reduce_launch(h, m, [x.data_ptr(), y.data_ptr()], None, out.data_ptr(), s)
     ms = _time_fn(torch, f, 200)
+    # the same launch replayed from a CUDA graph of 100 launches (no per-launch
+    # stream submission cost): the kernel's own latency
+    g = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(gs):
+        for _ in range(3):
+            pyc.pyc_reduce_launch(h, m, [x.data_ptr(), y.data_ptr()], None, out.data_ptr(),
+                                  gs.cuda_stream)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=gs):
+        for _ in range(100):
+            pyc.pyc_reduce_launch(h, m, [x.data_ptr(), y.data_ptr()], None, out.data_ptr(),
+                                  gs.cuda_stream)
+    ms_g = _time_fn(torch, g.replay, 20) / 100
     res["dot_f32_n2^20"] = {"n": m, "us": round(ms * 1e3, 2),
                             "GB/s": round(8 * m / (ms * 1e-3) / 1e9, 1), "cache": "warm (fits L2)",
+                            "graph_us": round(ms_g * 1e3, 2),
                             "config": "vec%d_u%d_b%d" % pyc.launch_config(h, m, reduce=True)}
+    del g
     return res
 
 
