@@ -440,13 +440,23 @@ void pyc_pool_destroy(pyc_pool_t p);
 typedef struct pyc_csr* pyc_csr_t;
 pyc_status pyc_csr_create(int64_t nrows, int64_t ncols, int64_t nnz, const void* rowptr,
                           const void* colidx, const void* vals, pyc_dtype vt, pyc_csr_t* out);
-/* The lanes per row (1, 2, 4, ..., 32) the matrix-vector product uses; set it. */
+/* The width the matrix-vector product uses; set it.  1, 2, 4, ..., 32: lanes per
+ * row over the CSR arrays.  0: a sliced-ELL copy that the handle builds from the
+ * CSR arrays when width 0 is set (or tried by pyc_spmv_autotune): rows in slices
+ * of 32, each slice padded to its longest row and stored entry-major, so that a
+ * warp reads its rows' entries in 128-byte pieces and no row pointers; row
+ * lengths of 1, 2 or 4 bytes.  Each row is still added in entry order (the same
+ * bits as one lane per row).  The copy is a snapshot: later changes to the
+ * caller's arrays are seen after width 0 is set again.  Setting width 0 runs on
+ * the legacy default stream and returns when the copy is built; another width
+ * frees the copy. */
 pyc_status pyc_csr_width(pyc_csr_t a, int* width);
 pyc_status pyc_csr_set_width(pyc_csr_t a, int width);
 /* y = A x on `stream` (x: ncols, y: nrows elements of vt, device; x and y must not
  * overlap).  Each row is folded per lane, then across its lanes in a fixed tree. */
 pyc_status pyc_spmv(pyc_csr_t a, const void* x, void* y, pyc_stream_t stream);
-/* Time every lane count on (x, y) and keep the fastest for this matrix. */
+/* Time every width on (x, y) and keep the fastest for this matrix (building the
+ * sliced copy to try width 0, and freeing it if another width wins). */
 pyc_status pyc_spmv_autotune(pyc_csr_t a, const void* x, void* y, pyc_stream_t stream);
 
 typedef struct {

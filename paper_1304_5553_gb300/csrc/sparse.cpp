@@ -145,6 +145,95 @@ PYC_SPMV(8)
 PYC_SPMV(16)
 PYC_SPMV(32)
 
+// Width 0: a sliced-ELL copy of the matrix.  Rows are taken in slices of 32;
+// slice c holds m_c = (off[c+1] - off[c]) / 32 entries per row (its longest
+// row), stored entry-major: entry j of row 32c + l at off[c] + 32 j + l, so a
+// warp's 32 lanes read 128 consecutive bytes per entry and no row pointers.
+// len[r] is row r's own length (LT: 1, 2 or 4 bytes); slots past it hold
+// zeros and are loaded but never used.  Row r is added in entry order, as one
+// lane per row adds it.
+template <class LT>
+__device__ __forceinline__ V pyc_sell_row(const pyc_i64* __restrict__ off,
+    const int* __restrict__ scol, const V* __restrict__ sval, const LT* __restrict__ len,
+    const V* __restrict__ x, const pyc_i64 c, const int l, const pyc_i64 nrows,
+    const unsigned long long pm, const unsigned long long px) {
+  const pyc_i64 o = pyc_ldnc(off + c, pm), m = (pyc_ldnc(off + c + 1, pm) - o) >> 5;
+  const pyc_i64 r = c * 32 + l;
+  const int lr = r < nrows ? (int)len[r] : 0;
+  V y = 0;
+  pyc_i64 j = 0;
+  for (; j + 4 <= m; j += 4) {  // four entries' loads in flight, then added in order
+    int ck[4];
+    V vk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ck[u] = pyc_ldnc(scol + o + (j + u) * 32 + l, pm);
+      vk[u] = pyc_ldnc(sval + o + (j + u) * 32 + l, pm);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (j + u < lr) y += vk[u] * pyc_ldnc(x + ck[u], px);
+  }
+  for (; j < m; ++j)
+    if (j < lr) y += pyc_ldnc(sval + o + j * 32 + l, pm) * pyc_ldnc(x + pyc_ldnc(scol + o + j * 32 + l, pm), px);
+  return y;
+}
+#define PYC_SELL(LT, TAG) \
+  extern "C" __global__ void __launch_bounds__(256) pyc_spmv_sell_##TAG(const pyc_i64* off, \
+      const int* scol, const V* sval, const LT* len, const V* x, V* y, const pyc_i64 nrows) { \
+    const pyc_i64 warp = ((pyc_i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; \
+    const pyc_i64 nwarps = ((pyc_i64)gridDim.x * blockDim.x) >> 5; \
+    const int l = threadIdx.x & 31; \
+    const unsigned long long pm = pyc_pol(false), px = pyc_pol(true); \
+    for (pyc_i64 c = warp; c * 32 < nrows; c += nwarps) { \
+      const V v = pyc_sell_row<LT>(off, scol, sval, len, x, c, l, nrows, pm, px); \
+      if (c * 32 + l < nrows) y[c * 32 + l] = v; \
+    } \
+  }
+PYC_SELL(unsigned char, u8)
+PYC_SELL(unsigned short, u16)
+PYC_SELL(unsigned, u32)
+// Building the copy.  pyc_sell_len: len[r] and each slice's longest row
+// (one warp per slice).  pyc_sell_fill: the entries, zeros past each row.
+extern "C" __global__ void __launch_bounds__(256) pyc_sell_len(const pyc_i64* rowptr,
+    const pyc_i64 nrows, int* cmax) {
+  const pyc_i64 warp = ((pyc_i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const pyc_i64 nwarps = ((pyc_i64)gridDim.x * blockDim.x) >> 5;
+  const int l = threadIdx.x & 31;
+  for (pyc_i64 c = warp; c * 32 < nrows; c += nwarps) {
+    const pyc_i64 r = c * 32 + l;
+    int len = r < nrows ? (int)(rowptr[r + 1] - rowptr[r]) : 0;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, d));
+    if (l == 0) cmax[c] = len;
+  }
+}
+template <class LT>
+__device__ __forceinline__ void pyc_sell_fill(const pyc_i64* rowptr, const int* col,
+    const V* val, const pyc_i64 nrows, const pyc_i64* off, int* scol, V* sval, LT* len) {
+  const pyc_i64 warp = ((pyc_i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const pyc_i64 nwarps = ((pyc_i64)gridDim.x * blockDim.x) >> 5;
+  const int l = threadIdx.x & 31;
+  for (pyc_i64 c = warp; c * 32 < nrows; c += nwarps) {
+    const pyc_i64 o = off[c], m = (off[c + 1] - o) >> 5, r = c * 32 + l;
+    const pyc_i64 b = r < nrows ? rowptr[r] : 0, lr = r < nrows ? rowptr[r + 1] - b : 0;
+    if (r < nrows) len[r] = (LT)lr;
+    for (pyc_i64 j = 0; j < m; ++j) {
+      scol[o + j * 32 + l] = j < lr ? col[b + j] : 0;
+      sval[o + j * 32 + l] = j < lr ? val[b + j] : (V)0;
+    }
+  }
+}
+#define PYC_SELL_FILL(LT, TAG) \
+  extern "C" __global__ void __launch_bounds__(256) pyc_sell_fill_##TAG(const pyc_i64* rowptr, \
+      const int* col, const V* val, const pyc_i64 nrows, const pyc_i64* off, int* scol, V* sval, \
+      LT* len) { \
+    pyc_sell_fill<LT>(rowptr, col, val, nrows, off, scol, sval, len); \
+  }
+PYC_SELL_FILL(unsigned char, u8)
+PYC_SELL_FILL(unsigned short, u16)
+PYC_SELL_FILL(unsigned, u32)
+
 // ---- fused conjugate-gradient step: 3 kernels.  s[0] = r.r, s[1] = p.Ap,
 // s[2] = tol^2, s[3] = new r.r, s[4] = b.b, s[5] = beta; it = steps taken.
 // Dot products are finished deterministically: per-CTA partials, then the last
@@ -232,6 +321,31 @@ PYC_CGA(4)
 PYC_CGA(8)
 PYC_CGA(16)
 PYC_CGA(32)
+// width 0 (the sliced-ELL copy): q = A p and s[1] = p.q
+#define PYC_CGA_SELL(LT, TAG) \
+  extern "C" __global__ void __launch_bounds__(256) pyc_cg_a_sell_##TAG(const pyc_i64* off, \
+      const int* scol, const V* sval, const LT* len, const V* p, V* q, const pyc_i64 nrows, \
+      V* part, unsigned* ticket, V* s, const unsigned keep) { \
+    const pyc_i64 warp = ((pyc_i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; \
+    const pyc_i64 nwarps = ((pyc_i64)gridDim.x * blockDim.x) >> 5; \
+    const int l = threadIdx.x & 31; \
+    const unsigned long long pm = pyc_pol(false), pp = pyc_pol(keep & 1u), \
+                             pq = pyc_pol(keep & 4u); \
+    V dot = 0; \
+    for (pyc_i64 c = warp; c * 32 < nrows; c += nwarps) { \
+      const V y = pyc_sell_row<LT>(off, scol, sval, len, p, c, l, nrows, pm, pp); \
+      const pyc_i64 r = c * 32 + l; \
+      if (r < nrows) { \
+        pyc_sth(q + r, y, pq); \
+        dot += pyc_ldnc(p + r, pp) * y; \
+      } \
+    } \
+    V tot; \
+    if (pyc_grid_sum(pyc_block_sum(dot), part, ticket, &tot) && threadIdx.x == 0) s[1] = tot; \
+  }
+PYC_CGA_SELL(unsigned char, u8)
+PYC_CGA_SELL(unsigned short, u16)
+PYC_CGA_SELL(unsigned, u32)
 // x += al p, r -= al q, s[3] = r.r; the last CTA sets beta and advances the step.
 // VEC: 16-byte accesses with L2 policies (x 16-byte aligned; the work vectors
 // always are).
@@ -317,7 +431,8 @@ extern "C" __global__ void __launch_bounds__(256) pyc_cg_c(V* __restrict__ p,
 }
 )PYC";
 
-const int kWidths[] = {1, 2, 4, 8, 16, 32};
+// Widths: lanes per row, or 0 for the sliced-ELL copy.
+const int kWidths[] = {0, 1, 2, 4, 8, 16, 32};
 constexpr int kMaxPartials = 4096;  // CTAs of one CG-step launch (per-CTA partial sums)
 
 int default_width(int64_t nrows, int64_t nnz) {
@@ -336,6 +451,10 @@ struct pyc_csr {
   CUdeviceptr rowptr = 0, col = 0, val = 0;
   pyc_dtype vt = PYC_F32;
   int width = 1;
+  // width 0: the sliced-ELL copy (slice offsets, entries, values, row lengths of
+  // s_lb bytes; s_lb = 0: no copy), built from the CSR arrays when selected
+  CUdeviceptr s_off = 0, s_col = 0, s_val = 0, s_len = 0;
+  int s_lb = 0;
   std::shared_ptr<pyc::Module> mod;
   // CG: step kernels (the library's map / map-reduce) and per-stream work space
   std::mutex mu;
@@ -347,7 +466,7 @@ struct pyc_csr {
     // a graph of 8 steps for one x pointer, captured on a private stream
     CUstream cap = nullptr;
     CUgraphExec graph = nullptr;
-    CUdeviceptr graph_x = 0, graph_base = 0;
+    CUdeviceptr graph_x = 0, graph_base = 0, graph_sell = 0;
     int graph_width = 0;
     // page-locked read-back slots of the device scalars, one event each
     unsigned char* host = nullptr;
@@ -362,8 +481,79 @@ namespace {
 
 int vbytes(pyc_dtype t) { return t == PYC_F64 ? 8 : 4; }
 
+const char* sell_tag(int lb) { return lb == 1 ? "u8" : lb == 2 ? "u16" : "u32"; }
+
+void free_sell(pyc_csr* a) {
+  for (CUdeviceptr* d : {&a->s_off, &a->s_col, &a->s_val, &a->s_len})
+    if (*d) {
+      drv().cuMemFree(*d);
+      *d = 0;
+    }
+  a->s_lb = 0;
+}
+
+// Builds the sliced-ELL copy from the CSR arrays as they are now (on `s`,
+// synchronously): slice lengths on the device, slice offsets on the host, then
+// the entries.
+void build_sell(pyc_csr* a, CUstream s) {
+  free_sell(a);
+  const int64_t n = a->nrows, nch = (n + 31) / 32;
+  if (n == 0) {
+    a->s_lb = 1;
+    return;
+  }
+  const Driver& d = drv();
+  CUdeviceptr cmax = 0;
+  PYC_CU(d.cuMemAlloc(&cmax, (size_t)(nch * 4)));
+  try {
+    CUfunction fl = a->mod->function("pyc_sell_len");
+    const unsigned gl =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident_ctas(fl, 256), (nch + 7) / 8));
+    int64_t nn = n;
+    void* pl[] = {&a->rowptr, &nn, &cmax};
+    PYC_CU(d.cuLaunchKernel(fl, gl, 1, 1, 256, 1, 1, 0, s, pl, nullptr));
+    PYC_CU(d.cuStreamSynchronize(s));
+    std::vector<int> hmax((size_t)nch);
+    PYC_CU(d.cuMemcpyDtoH(hmax.data(), cmax, (size_t)(nch * 4)));
+    std::vector<int64_t> off((size_t)nch + 1, 0);
+    int mx = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+      if (hmax[c] < 0) fail(PYC_E_ARG, "rowptr is not nondecreasing");
+      off[c + 1] = off[c] + 32 * (int64_t)hmax[c];
+      mx = std::max(mx, hmax[c]);
+    }
+    const int lb = mx <= 255 ? 1 : mx <= 65535 ? 2 : 4;
+    const int64_t total = off[nch], vb = vbytes(a->vt);
+    PYC_CU(d.cuMemAlloc(&a->s_off, (size_t)((nch + 1) * 8)));
+    PYC_CU(d.cuMemAlloc(&a->s_col, (size_t)std::max<int64_t>(total * 4, 4)));
+    PYC_CU(d.cuMemAlloc(&a->s_val, (size_t)std::max<int64_t>(total * vb, vb)));
+    PYC_CU(d.cuMemAlloc(&a->s_len, (size_t)(n * lb)));
+    PYC_CU(d.cuMemcpyHtoD(a->s_off, off.data(), (size_t)((nch + 1) * 8)));
+    CUfunction ff = a->mod->function(std::string("pyc_sell_fill_") + sell_tag(lb));
+    void* pf[] = {&a->rowptr, &a->col, &a->val, &nn, &a->s_off, &a->s_col, &a->s_val, &a->s_len};
+    PYC_CU(d.cuLaunchKernel(ff, gl, 1, 1, 256, 1, 1, 0, s, pf, nullptr));
+    PYC_CU(d.cuStreamSynchronize(s));
+    a->s_lb = lb;
+  } catch (...) {
+    d.cuMemFree(cmax);
+    free_sell(a);
+    throw;
+  }
+  d.cuMemFree(cmax);
+}
+
 void launch_spmv(pyc_csr* a, int width, CUdeviceptr x, CUdeviceptr y, CUstream s) {
   if (a->nrows == 0) return;
+  if (width == 0) {
+    if (!a->s_lb) fail(PYC_E_INTERNAL, "width 0 without its sliced copy");
+    CUfunction f = a->mod->function(std::string("pyc_spmv_sell_") + sell_tag(a->s_lb));
+    const int64_t nch = (a->nrows + 31) / 32;
+    const unsigned grid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident_ctas(f, 256), (nch + 7) / 8));
+    void* params[] = {&a->s_off, &a->s_col, &a->s_val, &a->s_len, &x, &y, &a->nrows};
+    PYC_CU(drv().cuLaunchKernel(f, grid, 1, 1, 256, 1, 1, 0, s, params, nullptr));
+    return;
+  }
   CUfunction f = a->mod->function("pyc_spmv_t" + std::to_string(width));
   const int block = 256;
   const int64_t rows_per_block = (int64_t)(block / 32) * (32 / width);
@@ -494,7 +684,12 @@ PYC_API pyc_status pyc_csr_set_width(pyc_csr_t a, int width) {
   return guarded([&] {
     if (!a) fail(PYC_E_ARG, "matrix is NULL");
     if (std::find(std::begin(kWidths), std::end(kWidths), width) == std::end(kWidths))
-      fail(PYC_E_ARG, "width is 1, 2, 4, 8, 16 or 32");
+      fail(PYC_E_ARG, "width is 0, 1, 2, 4, 8, 16 or 32");
+    if (width == 0) {
+      build_sell(a, nullptr);
+    } else {
+      free_sell(a);
+    }
     a->width = width;
   });
 }
@@ -519,6 +714,7 @@ PYC_API pyc_status pyc_spmv_autotune(pyc_csr_t a, const void* x, void* y, pyc_st
     float best = 1e30f;
     int best_w = a->width;
     for (int w : kWidths) {
+      if (w == 0) build_sell(a, s);
       for (int k = 0; k < 2; ++k)
         launch_spmv(a, w, reinterpret_cast<CUdeviceptr>(x), reinterpret_cast<CUdeviceptr>(y), s);
       PYC_CU(drv().cuEventRecord(e0, s));
@@ -532,6 +728,7 @@ PYC_API pyc_status pyc_spmv_autotune(pyc_csr_t a, const void* x, void* y, pyc_st
     }
     drv().cuEventDestroy(e0);
     drv().cuEventDestroy(e1);
+    if (best_w != 0) free_sell(a);
     a->width = best_w;
   });
 }
@@ -569,17 +766,23 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
       const double rt2 = rtol * rtol;
       map_launch(a->set_tol, 1, {sc}, &rt2, s);
       const int64_t chunk = 8;
-      CUfunction fa = a->mod->function("pyc_cg_a_t" + std::to_string(a->width));
+      CUfunction fa = a->width == 0
+                          ? a->mod->function(std::string("pyc_cg_a_sell_") + sell_tag(a->s_lb))
+                          : a->mod->function("pyc_cg_a_t" + std::to_string(a->width));
       // 16-byte accesses to x need a 16-byte aligned x (the work vectors are)
       CUfunction fb = a->mod->function(xx % 16 == 0 ? "pyc_cg_b" : "pyc_cg_b_s");
       CUfunction fc = a->mod->function("pyc_cg_c");
-      const int64_t rows_per_cta = (int64_t)(256 / 32) * (32 / a->width);
-      const unsigned ga = cg_grid(fa, (n + rows_per_cta - 1) / rows_per_cta * 256);
+      const int64_t rows_per_cta = (int64_t)(256 / 32) * (a->width == 0 ? 32 : 32 / a->width);
+      const unsigned ga = a->width == 0 ? cg_grid(fa, (n + 31) / 32 * 32)
+                                        : cg_grid(fa, (n + rows_per_cta - 1) / rows_per_cta * 256);
       const int64_t wv = 16 / vb;  // elements per 16-byte access
       const unsigned gb = cg_grid(fb, (n + wv - 1) / wv), gc = cg_grid(fc, (n + wv - 1) / wv);
       CUdeviceptr pp = p, qq = q, rr = r;
       unsigned keep = cg_keep(n * vb);
-      void* pa[] = {&a->rowptr, &a->col, &a->val, &pp, &qq, &nn, &part, &ticket, &sc_v, &keep};
+      void* pa_csr[] = {&a->rowptr, &a->col, &a->val, &pp, &qq, &nn, &part, &ticket, &sc_v, &keep};
+      void* pa_sell[] = {&a->s_off, &a->s_col, &a->s_val, &a->s_len, &pp, &qq, &nn,
+                         &part, &ticket, &sc_v, &keep};
+      void** pa = a->width == 0 ? pa_sell : pa_csr;
       void* pb[] = {&xx_v, &rr, &pp, &qq, &nn, &part, &ticket, &sc_v, &it_v, &keep};
       void* pc[] = {&pp, &rr, &nn, &sc_v, &keep};
       auto steps = [&](CUstream st, int64_t k) {
@@ -600,7 +803,8 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
           w.host = static_cast<unsigned char*>(h);
           for (CUevent& e : w.ev) PYC_CU(drv().cuEventCreate(&e, CU_EVENT_DISABLE_TIMING));
         }
-        if (w.graph && (w.graph_x != xx || w.graph_base != w.base || w.graph_width != a->width)) {
+        if (w.graph && (w.graph_x != xx || w.graph_base != w.base || w.graph_width != a->width ||
+                        w.graph_sell != a->s_col)) {
           drv().cuGraphExecDestroy(w.graph);
           w.graph = nullptr;
         }
@@ -622,6 +826,7 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
           w.graph_x = xx;
           w.graph_base = w.base;
           w.graph_width = a->width;
+          w.graph_sell = a->s_col;
         }
       }
       // read back s[0..5] and the step count of the chunk just queued
@@ -703,6 +908,7 @@ PYC_API void pyc_csr_destroy(pyc_csr_t a) {
     pyc_reduce_destroy(a->dot);
     for (pyc_map_t h : {a->init_r, a->copy, a->set_tol})
       pyc_map_destroy(h);
+    free_sell(a);
   } catch (...) {
   }
   delete a;

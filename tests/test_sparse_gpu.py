@@ -53,25 +53,62 @@ def test_spmv_every_width_within_bound(vt):
         dy = torch.empty(m.n, dtype=dx.dtype, device="cuda")
         y64, ab = osp.spmv(m.rp, m.c, m.v, x)
         length = np.diff(m.rp)
-        for w in (1, 2, 4, 8, 16, 32):
+        got = {}
+        for w in (0, 1, 2, 4, 8, 16, 32):
             pyc.pyc_csr_set_width(m.h, w)
             dy.fill_(np.nan)
             pyc.pyc_spmv(m.h, dx.data_ptr(), dy.data_ptr(), s)
-            y = dy.cpu().numpy().astype(np.float64)
+            got[w] = dy.cpu().numpy()
+            y = got[w].astype(np.float64)
             # a row is folded in at most len + 5 steps (lane runs, then a 5-level tree)
             assert np.all(np.abs(y - y64) <= (length + 6) * U[vt] * ab), w
+        # the sliced copy adds each row in entry order, as one lane per row does
+        assert np.array_equal(got[0], got[1])
         pyc.pyc_spmv_autotune(m.h, dx.data_ptr(), dy.data_ptr(), s)
-        assert pyc.pyc_csr_width(m.h) in (1, 2, 4, 8, 16, 32)
+        assert pyc.pyc_csr_width(m.h) in (0, 1, 2, 4, 8, 16, 32)
+
+
+def test_sliced_copy_is_a_snapshot():
+    """Width 0 multiplies by the matrix as it was when the width was set; setting
+    it again takes the caller's current values.  Row lengths wider than a byte
+    (a 300-entry row) take the 2-byte length table."""
+    s = torch.cuda.current_stream().cuda_stream
+    rp, c, v = _mixed(5003, 21)
+    deg = np.diff(rp)
+    deg[100] = 300
+    rp = np.r_[0, np.cumsum(deg)].astype(np.int64)
+    rng = np.random.default_rng(22)
+    c = rng.integers(0, 5003, rp[-1]).astype(np.int32)
+    v = rng.uniform(-1, 1, rp[-1])
+    m = Mat(rp, c, v, 5003, pyc.PYC_F64)
+    x = rng.uniform(-1, 1, 5003)
+    dx = m.vec(x)
+    dy = torch.empty(5003, dtype=torch.float64, device="cuda")
+    pyc.pyc_csr_set_width(m.h, 1)
+    pyc.pyc_spmv(m.h, dx.data_ptr(), dy.data_ptr(), s)
+    y1 = dy.cpu().numpy()
+    pyc.pyc_csr_set_width(m.h, 0)
+    pyc.pyc_spmv(m.h, dx.data_ptr(), dy.data_ptr(), s)
+    assert np.array_equal(dy.cpu().numpy(), y1)
+    m.d[2].mul_(2.0)      # the caller changes its values
+    pyc.pyc_spmv(m.h, dx.data_ptr(), dy.data_ptr(), s)
+    assert np.array_equal(dy.cpu().numpy(), y1)   # the snapshot
+    pyc.pyc_csr_set_width(m.h, 0)
+    pyc.pyc_spmv(m.h, dx.data_ptr(), dy.data_ptr(), s)
+    assert np.array_equal(dy.cpu().numpy(), 2.0 * y1)   # exact: a power of two
 
 
 def _true_residual(m, b, x):
     return np.linalg.norm(b.astype(np.float64) - osp.spmv(m.rp, m.c, m.v, x)[0])
 
 
-def test_cg_f64_matches_the_oracle():
+@pytest.mark.parametrize("width", [None, 0])
+def test_cg_f64_matches_the_oracle(width):
     s = torch.cuda.current_stream().cuda_stream
     rp, c, v = inputs.poisson2d(64, 64, np.float64)
     m = Mat(rp, c, v, 4096, pyc.PYC_F64)
+    if width is not None:
+        pyc.pyc_csr_set_width(m.h, width)
     b = np.random.default_rng(91).standard_normal(4096)
     db, dx = m.vec(b), m.vec(np.zeros(4096))
     info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dx.data_ptr(), 1e-8, 5000, s)
@@ -96,6 +133,7 @@ def test_cg_f32_and_irregular():
     # irregular rows (log-uniform degrees up to 300), binary64
     rp, c, v = inputs.random_spd(30000, 8, max_degree=300)
     m2 = Mat(rp, c, v, 30000, pyc.PYC_F64)
+    pyc.pyc_csr_set_width(m2.h, 0)   # the sliced copy (slices padded to 300-entry rows)
     b2 = np.random.default_rng(93).standard_normal(30000)
     db2, dx2 = m2.vec(b2), m2.vec(np.zeros(30000))
     info2 = pyc.pyc_cg_solve(m2.h, db2.data_ptr(), dx2.data_ptr(), 1e-10, 1000, s)
