@@ -468,6 +468,27 @@ std::string group_loads_used(const ArgSpec& spec, const std::string& code) {
   return o.str();
 }
 
+// L2 prefetch hints (evict-last) over [ts, te) of every lifted array `code`
+// reads: thread tid of nt takes every nt-th 128-byte line, from the line that
+// holds element ts; every line touched holds at least one element of the range.
+std::string prefetch_used(const ArgSpec& spec, const std::string& code) {
+  std::ostringstream o;
+  for (auto& p : spec.params) {
+    if (!(p.is_ptr && p.lifted && p.read)) continue;
+    if (code.find("pyc_r_" + p.name + " ") == std::string::npos &&
+        code.find("pyc_r_" + p.name + "[") == std::string::npos)
+      continue;
+    o << "  {\n"
+      << "    const unsigned long long pyc_pb = (unsigned long long)(" << p.name << " + ts);\n"
+      << "    const unsigned long long pyc_pe = (unsigned long long)(" << p.name << " + te);\n"
+      << "    for (unsigned long long q = (pyc_pb & ~127ull) + 128ull * tid; q < pyc_pe;\n"
+      << "         q += 128ull * nt)\n"
+      << "      asm volatile(\"prefetch.global.L2::evict_last [%0];\" ::\"l\"(q));\n"
+      << "  }\n";
+  }
+  return o.str();
+}
+
 // Element-wise loads into register slot pyc_k at index i of the lifted arrays
 // read (by `code` only, if it is not empty), and stores of those written.
 std::string scalar_loads_k(const ArgSpec& spec, const std::string& code) {
@@ -1510,6 +1531,15 @@ __device__ __forceinline__ pyc_tinfo pyc_tile_info(const pyc_scan_params& S, con
   return r;
 }
 
+// Start the whole input of tile [ts, te) moving from DRAM into L2 at once, so
+// that sweep 1 is not held to the loads its registers can keep in flight.
+)PYC";
+  o << "__device__ __forceinline__ void pyc_prefetch_tile(const pyc_args& pyc_p, const pyc_i64 ts,\n"
+       "    const pyc_i64 te, const int tid, const int nt) {\n";
+  o << aliases(spec, "pyc_p");
+  o << prefetch_used(spec, input_expr);
+  o << "  (void)ts; (void)te; (void)tid; (void)nt;\n}\n";
+  o << R"PYC(
 // Persistent single-pass scan with a look-back warp.  The CTA has nw compute
 // warps and one look-back warp (the last).  Iteration k of the compute warps:
 // take tile k, sweep 1 over it, publish its aggregate and hand the warp
@@ -1582,6 +1612,7 @@ __device__ __forceinline__ void pyc_scan_body(const pyc_args& pyc_p, const pyc_s
       if (t < S.ntiles && PYC_OK(S, t, 0, S.ntiles, 42, t)) {
         const pyc_tinfo I = pyc_tile_info(S, t, base);
         if (!PYC_OK(S, I.ts, I.te - I.ts, S.n, 43, t)) return;
+        pyc_prefetch_tile(pyc_p, I.ts, I.te, (int)threadIdx.x, nw * 32);
         const pyc_acc_t a =
             I.rag ? pyc_sweep1<VB, U, true>(pyc_p, S, t, I.ts, I.te, I.g, w, lane)
                   : pyc_sweep1<VB, U, false>(pyc_p, S, t, I.ts, I.te, I.g, w, lane);
