@@ -70,3 +70,25 @@ def test_cg_edge_cases():
     assert k == 0
     x, k, hist = osp.cg(rp, c, v, np.ones(n), np.zeros(n), 1e-14, 3)
     assert k == 3 and len(hist) == 4
+
+
+def _rank_one_plus_identity(n, seed):
+    """A = I + u u^T (dense pattern, CSR): eigenvalues 1 (n - 1 times) and 1 + |u|^2."""
+    u = np.random.default_rng(seed).standard_normal(n)
+    A = np.eye(n) + np.outer(u, u)
+    rp = np.arange(0, n * n + 1, n, dtype=np.int64)
+    c = np.tile(np.arange(n, dtype=np.int32), n)
+    return rp, c, A.ravel(), A
+
+
+def test_cg_two_eigenvalues_two_steps():
+    """CG's residual polynomial of degree k can vanish on k distinct eigenvalues, so a
+    matrix with two of them is solved in two steps (to rounding); one step is not
+    enough unless b happens to be an eigenvector."""
+    n = 60
+    rp, c, v, A = _rank_one_plus_identity(n, 7)
+    b = np.random.default_rng(8).standard_normal(n)
+    x, k, hist = osp.cg(rp, c, v, b, np.zeros(n), 1e-12, 50)
+    assert k == 2
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+    assert hist[1] > 1e-3 * hist[0]

@@ -142,6 +142,24 @@ def test_cg_f32_and_irregular():
     assert _true_residual(m2, b2, dx2.cpu().numpy()) <= 1e-10 * np.linalg.norm(b2) * 1.01
 
 
+@pytest.mark.parametrize("width", [1, 0])
+def test_cg_two_eigenvalues_two_steps(width):
+    """A = I + u u^T has two distinct eigenvalues: CG solves it in two steps."""
+    n = 60
+    u = np.random.default_rng(7).standard_normal(n)
+    A = np.eye(n) + np.outer(u, u)
+    rp = np.arange(0, n * n + 1, n, dtype=np.int64)
+    c = np.tile(np.arange(n, dtype=np.int32), n)
+    m = Mat(rp, c, A.ravel(), n, pyc.PYC_F64)
+    pyc.pyc_csr_set_width(m.h, width)
+    b = np.random.default_rng(8).standard_normal(n)
+    db, dx = m.vec(b), m.vec(np.zeros(n))
+    s = torch.cuda.current_stream().cuda_stream
+    info = pyc.pyc_cg_solve(m.h, db.data_ptr(), dx.data_ptr(), 1e-12, 50, s)
+    assert info["converged"] and info["iterations"] == 2
+    assert np.allclose(dx.cpu().numpy(), np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+
+
 def test_cg_edge_cases():
     s = torch.cuda.current_stream().cuda_stream
     rp, c, v = inputs.poisson2d(32, 32, np.float64)
