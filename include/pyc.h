@@ -442,7 +442,8 @@ pyc_status pyc_csr_create(int64_t nrows, int64_t ncols, int64_t nnz, const void*
                           const void* colidx, const void* vals, pyc_dtype vt, pyc_csr_t* out);
 /* The width the matrix-vector product uses; set it.  1, 2, 4, ..., 32: lanes per
  * row over the CSR arrays.  0: a sliced-ELL copy that the handle builds from the
- * CSR arrays when width 0 is set (or tried by pyc_spmv_autotune): rows in slices
+ * CSR arrays when width 0 is set (or tried by pyc_spmv_autotune, when padding
+ * would at most double the stored entries): rows in slices
  * of 32, each slice padded to its longest row and stored entry-major, so that a
  * warp reads its rows' entries in 128-byte pieces and no row pointers; row
  * lengths of 1, 2 or 4 bytes.  Each row is still added in entry order (the same

@@ -494,13 +494,14 @@ void free_sell(pyc_csr* a) {
 
 // Builds the sliced-ELL copy from the CSR arrays as they are now (on `s`,
 // synchronously): slice lengths on the device, slice offsets on the host, then
-// the entries.
-void build_sell(pyc_csr* a, CUstream s) {
+// the entries.  With max_entries >= 0, a copy that would hold more padded
+// entries than that is not built (returns false).
+bool build_sell(pyc_csr* a, CUstream s, int64_t max_entries = -1) {
   free_sell(a);
   const int64_t n = a->nrows, nch = (n + 31) / 32;
   if (n == 0) {
     a->s_lb = 1;
-    return;
+    return true;
   }
   const Driver& d = drv();
   CUdeviceptr cmax = 0;
@@ -524,6 +525,10 @@ void build_sell(pyc_csr* a, CUstream s) {
     }
     const int lb = mx <= 255 ? 1 : mx <= 65535 ? 2 : 4;
     const int64_t total = off[nch], vb = vbytes(a->vt);
+    if (max_entries >= 0 && total > max_entries) {
+      d.cuMemFree(cmax);
+      return false;
+    }
     PYC_CU(d.cuMemAlloc(&a->s_off, (size_t)((nch + 1) * 8)));
     PYC_CU(d.cuMemAlloc(&a->s_col, (size_t)std::max<int64_t>(total * 4, 4)));
     PYC_CU(d.cuMemAlloc(&a->s_val, (size_t)std::max<int64_t>(total * vb, vb)));
@@ -540,6 +545,7 @@ void build_sell(pyc_csr* a, CUstream s) {
     throw;
   }
   d.cuMemFree(cmax);
+  return true;
 }
 
 void launch_spmv(pyc_csr* a, int width, CUdeviceptr x, CUdeviceptr y, CUstream s) {
@@ -714,7 +720,8 @@ PYC_API pyc_status pyc_spmv_autotune(pyc_csr_t a, const void* x, void* y, pyc_st
     float best = 1e30f;
     int best_w = a->width;
     for (int w : kWidths) {
-      if (w == 0) build_sell(a, s);
+      // the sliced copy is tried only while padding at most doubles the entries
+      if (w == 0 && !build_sell(a, s, 2 * a->nnz + 32 * ((a->nrows + 31) / 32))) continue;
       for (int k = 0; k < 2; ++k)
         launch_spmv(a, w, reinterpret_cast<CUdeviceptr>(x), reinterpret_cast<CUdeviceptr>(y), s);
       PYC_CU(drv().cuEventRecord(e0, s));

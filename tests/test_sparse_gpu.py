@@ -38,6 +38,16 @@ def _mixed(n, seed):
     return rp, c, v
 
 
+def _padding_over_limit(rp):
+    """True if slices of 32 rows padded to their longest row would hold more than
+    2 nnz + 32 entries per slice (the tuner's limit for the sliced copy)."""
+    n = rp.size - 1
+    nch = (n + 31) // 32
+    d = np.zeros(nch * 32, np.int64)
+    d[:n] = np.diff(rp)
+    return 32 * d.reshape(nch, 32).max(1).sum() > 2 * rp[-1] + 32 * nch
+
+
 def _matrices(vt):
     return [Mat(*inputs.poisson2d(300, 200), 60000, vt),
             Mat(*inputs.random_spd(50000, 7, max_degree=2000, empty_every=11), 50000, vt),
@@ -66,6 +76,8 @@ def test_spmv_every_width_within_bound(vt):
         assert np.array_equal(got[0], got[1])
         pyc.pyc_spmv_autotune(m.h, dx.data_ptr(), dy.data_ptr(), s)
         assert pyc.pyc_csr_width(m.h) in (0, 1, 2, 4, 8, 16, 32)
+        if _padding_over_limit(m.rp):   # the tuner does not try the sliced copy
+            assert pyc.pyc_csr_width(m.h) != 0
 
 
 def test_sliced_copy_is_a_snapshot():
