@@ -317,6 +317,51 @@ def bench_fused(torch, dev, reps=10):
     return res
 
 
+def bench_compile(pyc):
+    """Spec to kernel (Sec. 2, Fig. 1; Sec. 3.3.2): host time of pyc_*_create for
+    a spec never seen before (parse, generate, NVRTC compile for sm_103a, write
+    the disk cache, load the module), for the same spec again in this process
+    (parse, generate, hash, in-process hit), and in a fresh process whose
+    context is already up (disk-cache hit)."""
+    import subprocess
+    import time
+    import uuid
+    tag = uuid.uuid4().int % 1000003  # a constant no earlier run compiled
+    cases = {
+        "map": ("pyc_map_create", "pyc_map_destroy",
+                ("float a, float *x, float b, float *y, float *z",
+                 "z[i] = a*x[i] + b*y[i] + %d.0f" % tag)),
+        "reduce": ("pyc_reduce_create", "pyc_reduce_destroy",
+                   (pyc.PYC_F32, "0", "a+b", "x[i]*y[i] + %d.0f" % tag, "float *x, float *y")),
+    }
+    res = {}
+    for name, (fn, fd, args) in cases.items():
+        f, destroy = getattr(pyc, fn), getattr(pyc, fd)
+        t0 = time.perf_counter()
+        h = f(*args)
+        cold = time.perf_counter() - t0
+        destroy(h)
+        reps = 200
+        warm = 0.0
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            h = f(*args)
+            warm += time.perf_counter() - t0
+            destroy(h)
+        warm /= reps
+        code = ("import sys, time; sys.path.insert(0, %r)\n"
+                "from paper_1304_5553_gb300 import pyc\n"
+                "pyc.pyc_map_create('float *x, float *y', 'y[i] = x[i]')\n"
+                "t0 = time.perf_counter(); pyc.%s(*%r)\n"
+                "print(time.perf_counter() - t0)\n" % (ROOT, fn, args))
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                             timeout=600)
+        disk = float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+        res[name] = {"cold_ms": round(cold * 1e3, 1), "warm_us": round(warm * 1e6, 1),
+                     "disk_hit_ms": round(disk * 1e3, 2) if disk is not None else None}
+    return res
+
+
 def bench_pool(torch, pyc, dev):
     """Memory pools (Sec. 3.2.6): host time of one allocate + free pair served by
     a pool (reuse) vs by the driver (a pool that retains nothing) vs torch's own
@@ -751,6 +796,7 @@ def run_gpu(args):
         details["scans"] = bench_scans(torch, pyc, stock, dev)
         details["fused"] = bench_fused(torch, dev)
         details["pool"] = bench_pool(torch, pyc, dev)
+        details["compile"] = bench_compile(pyc)
         details["cg"] = bench_cg(torch, pyc, dev)
         details["batched"] = bench_batched(torch, pyc, stock, dev)
         details["serving"] = bench_serving(torch, pyc, stock, dev)
