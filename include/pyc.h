@@ -470,12 +470,15 @@ typedef struct {
  * (Hestenes-Stiefel): x holds the initial guess on entry and the solution on
  * exit (device, nrows elements; b likewise).  Stops when ||r|| <= rtol ||b|| or
  * after maxit steps.  Runs on `stream`: steps are queued as CUDA graphs of 8
- * (re-captured when x, the lanes per row or the work space change) with two
+ * (re-captured when x, the width, the sliced copy or the work space change) with two
  * groups in flight while the host tests the previous group's residual; steps
  * queued past convergence change nothing.  The handle keeps 3 vectors of work
  * space per (context, stream); one solve at a time per (handle, stream).  A
  * breakdown (p.Ap = 0 before convergence) stops progress; the result then
- * reports converged = 0. */
+ * reports converged = 0.  While it runs, the work vectors (and x) that fit
+ * together in 9/16 of L2 are held there with an evict-last cache policy and the
+ * matrix is read evict-first; at exit their L2 lines return to normal priority.
+ * The width in use (lanes per row or the sliced copy) is the handle's. */
 pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol, int64_t maxit,
                         pyc_stream_t stream, pyc_cg_info* info);
 void pyc_csr_destroy(pyc_csr_t a);
