@@ -268,6 +268,17 @@ def bench_scans(torch, pyc, stock, dev, reps=10):
     yi = torch.empty(n, dtype=torch.int64, device=dev)
     cases = [("cumsum_f32", xf, yf, 8), ("cummax_f32", xf, yf, 8),
              ("cumsum_excl_i32_i64", xi, yi, 12)]
+    # the map with the same reads and writes per element and no dependence between
+    # elements (a copy for the 4-byte scans, a widening copy for int32 -> int64):
+    # the bandwidth this read/write mix reaches at all, beside the scan's
+    mix = {}
+    for spec in ("float *x, float *y", "int *x, long long *y"):
+        hm = pyc.pyc_map_create(spec, "y[i] = x[i]")
+        x, y = (xf, yf) if spec.startswith("float") else (xi, yi)
+        pyc.pyc_map_autotune(hm, n, s)
+        mix[spec] = _time_fn(torch, lambda hm=hm, x=x, y=y: pyc.pyc_map_launch(
+            hm, n, [x.data_ptr(), y.data_ptr()], None, s), reps)
+        pyc.pyc_map_destroy(hm)
     peak, kind = peaks()
     for name, x, y, bpe in cases:
         h = stock.create(name)
@@ -275,10 +286,13 @@ def bench_scans(torch, pyc, stock, dev, reps=10):
         f = (lambda h=h, x=x, y=y: pyc.pyc_scan_launch(h, n, [x.data_ptr(), y.data_ptr()], None, s))
         ms = _time_fn(torch, f, reps)
         gbs = bpe * n / (ms * 1e-3) / 1e9
+        mix_ms = mix["int *x, long long *y" if bpe == 12 else "float *x, float *y"]
         res[name] = {"n": n, "us": round(ms * 1e3, 2), "GB/s": round(gbs, 1),
                      "frac_of_%s_peak" % kind: round(gbs / peak, 4),
                      "bytes_per_elem": bpe,
-                     "config": "vec%d_u%d_b%d" % pyc.launch_config(h, n, reduce="scan")}
+                     "config": "vec%d_u%d_b%d" % pyc.launch_config(h, n, reduce="scan"),
+                     "same_mix_map_us": round(mix_ms * 1e3, 2),
+                     "frac_of_same_mix_map": round(mix_ms / ms, 4)}
     del xf, xi, yf, yi
     torch.cuda.empty_cache()
     return res
@@ -498,7 +512,8 @@ def bench_batched(torch, pyc, stock, dev, reps=5):
                                                        y.data_ptr() + int(off[k]) * es],
                                       None, out.data_ptr() + 4 * k, s)
         ms_p = _time_fn(torch, per_seg, 1, warmup=1)
-        res[name] = {"batched_ms": round(ms_b, 3), "per_segment_launches_ms": round(ms_p, 3),
+        res[name] = {"config": "vec%d_u%d_b%d" % pyc.batched_config(h),
+                     "batched_ms": round(ms_b, 3), "per_segment_launches_ms": round(ms_p, 3),
                      "speedup": round(ms_p / ms_b, 2),
                      "batched_GB/s": round(bpe * total / (ms_b * 1e-3) / 1e9, 1),
                      "reqs/s": round(lens.size / (ms_b * 1e-3), 1)}
@@ -701,6 +716,40 @@ def profile_scan(args):
                       "note": "profiling driver, not a bench value"}))
 
 
+def profile_batched(args):
+    """Profiling driver (not a bench line): the segmented dot product over the
+    first `segments` segments of the bench's segment table (lengths log-uniform in
+    [1, 2^20]), warm-up then `steps` batched launches, for ncu captures of the
+    persistent segmented kernel."""
+    import torch
+    from paper_1304_5553_gb300 import inputs, pyc, stock
+    torch.cuda.set_device(0)
+    name = args.profile_batched
+    dt = torch.bfloat16 if name.endswith("bf16") else torch.float32
+    lens = inputs.segment_lengths(nseg=args.segments)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    total = int(off[-1])
+    x = torch.from_numpy(inputs.uniform_f32(2, 0, total, -1.0, 1.0)).to(dt).cuda()
+    y = torch.from_numpy(inputs.uniform_f32(2, 1, total, -1.0, 1.0)).to(dt).cuda()
+    out = torch.zeros(lens.size, dtype=torch.float32, device="cuda")
+    opts = {}
+    if args.config:  # vecV_uU_bB: a fixed launch configuration (no tuning launches)
+        v, u, b = (int(q[1:] if q[0] in "ub" else q[3:]) for q in args.config.split("_"))
+        opts = dict(vec_bytes=v, items_per_thread=u, block=b)
+    h = stock.create(name, **opts)
+    s = torch.cuda.current_stream().cuda_stream
+    ptrs = [x.data_ptr(), y.data_ptr()]
+    if args.autotune == "on" and not opts:
+        pyc.pyc_reduce_batched_autotune(h, lens.size, off, ptrs, None, out.data_ptr(), s)
+    print("config vec%d_u%d_b%d" % pyc.batched_config(h), file=sys.stderr)
+    f = lambda: pyc.pyc_reduce_batched(h, lens.size, off, ptrs, None, out.data_ptr(), s)
+    ms = _time_fn(torch, f, args.steps, warmup=args.warmup)
+    bpe = x.element_size() * 2
+    print(json.dumps({"profile_batched": name, "segments": int(lens.size), "elements": total,
+                      "us": round(ms * 1e3, 2), "GB/s": round(bpe * total / (ms * 1e-3) / 1e9, 1),
+                      "note": "profiling driver, not a bench value"}))
+
+
 def profile_cg(args):
     """Profiling driver (not a bench line): CG on the 5-point Laplacian of an
     nx x nx grid (binary32), a warm-up solve of 8 steps, then `steps` steps."""
@@ -877,6 +926,10 @@ def main():
                     help="profiling driver: time one stock reduction only (not a bench line)")
     ap.add_argument("--profile-scan", default="",
                     help="profiling driver: time one stock scan only (not a bench line)")
+    ap.add_argument("--profile-batched", default="",
+                    help="profiling driver: the segmented dot (dot_f32 / dot_bf16) only")
+    ap.add_argument("--segments", type=int, default=20000,
+                    help="with --profile-batched: the first K segments of the segment table")
     ap.add_argument("--profile-cg", action="store_true",
                     help="profiling driver: CG steps on a Poisson matrix of 2^n_log2 rows")
     ap.add_argument("--lanes", type=int, default=None,
@@ -897,6 +950,8 @@ def main():
         profile_reduce(args)
     elif args.profile_scan:
         profile_scan(args)
+    elif args.profile_batched:
+        profile_batched(args)
     elif args.profile_cg:
         profile_cg(args)
     else:

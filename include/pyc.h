@@ -280,6 +280,12 @@ int pyc_reduce_out_bytes(pyc_reduce_t h);
 const char* pyc_reduce_source(pyc_reduce_t h);
 pyc_status pyc_reduce_autotune(pyc_reduce_t h, int64_t n, pyc_stream_t stream);
 pyc_status pyc_reduce_config(pyc_reduce_t h, int64_t n, int* vec_bytes, int* unroll, int* block);
+/* Launch configuration (vector bytes, unroll, block size) of the handle's
+ * batched launches (pyc_reduce_batched and the server's map-reduce batches):
+ * the tuned one after pyc_reduce_batched_autotune, else the default, with any
+ * fixed pyc_opts fields applied.  Any output pointer may be NULL.  Sec. 3.3.1
+ * (the kept variants).  PYC_E_ARG for a NULL handle. */
+pyc_status pyc_reduce_batched_config(pyc_reduce_t h, int* vec_bytes, int* unroll, int* block);
 void pyc_reduce_destroy(pyc_reduce_t h);
 
 /* ------------------------------------------------------------------ scan */

@@ -210,6 +210,17 @@ PYC_API pyc_status pyc_reduce_config(pyc_reduce_t h, int64_t n, int* vec_bytes, 
   });
 }
 
+PYC_API pyc_status pyc_reduce_batched_config(pyc_reduce_t h, int* vec_bytes, int* unroll,
+                                             int* block) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    LaunchCfg c = batched_cfg(*h, true);
+    if (vec_bytes) *vec_bytes = c.v.vec_bytes;
+    if (unroll) *unroll = c.v.unroll;
+    if (block) *block = c.block;
+  });
+}
+
 PYC_API pyc_status pyc_map_autotune(pyc_map_t h, int64_t n, pyc_stream_t stream) {
   return guarded([&] {
     if (!h) fail(PYC_E_ARG, "handle is NULL");

@@ -114,6 +114,7 @@ EXPORTED = [
     "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
     "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay", "pyc_map_launch_host",
     "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
+    "pyc_reduce_batched_config",
     "pyc_scan_create", "pyc_scan_launch", "pyc_scan_num_params", "pyc_scan_param",
     "pyc_scan_scalar_bytes", "pyc_scan_source", "pyc_scan_autotune", "pyc_scan_config", "pyc_scan_destroy",
     "pyc_scan_sync", "pyc_scan_launch_test", "pyc_expr_map_create", "pyc_expr_reduce_create",
@@ -152,6 +153,7 @@ def load(build_if_missing=True):
         "pyc_map_launch_host": (st, [vp, i64, ctypes.POINTER(vp), vp]),
         "pyc_map_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_reduce_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
+        "pyc_reduce_batched_config": (st, [vp] + [ctypes.POINTER(i32)] * 3),
         "pyc_scan_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_map_num_params": (i32, [vp]),
         "pyc_map_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
@@ -535,6 +537,13 @@ def launch_config(h, n, reduce=False):
     v, u, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     fn = getattr(load(), "pyc_%s_config" % _kind(reduce))
     _check(fn(h, int(n), ctypes.byref(v), ctypes.byref(u), ctypes.byref(b)))
+    return v.value, u.value, b.value
+
+
+def batched_config(h):
+    """(vec_bytes, unroll, block) of the handle's batched launches."""
+    v, u, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().pyc_reduce_batched_config(h, ctypes.byref(v), ctypes.byref(u), ctypes.byref(b)))
     return v.value, u.value, b.value
 
 

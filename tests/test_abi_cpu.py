@@ -237,3 +237,17 @@ def test_scan_create_validation():
         with pytest.raises(pyc.PycError) as e:
             pyc.pyc_scan_create(*args)
         assert e.value.status in (pyc.PYC_E_ARG, pyc.PYC_E_PARSE)
+
+
+def test_batched_config_default_and_fixed_options():
+    # no tuning has run for these handles: the default batched configuration
+    # (16-byte vectors, unroll 1, 256 threads), with fixed options taking over
+    spec = "float *x, float *y"
+    h = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i]+0.0f*%d" % os.getpid(), spec)
+    assert pyc.batched_config(h) == (16, 1, 256)
+    g = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i]", spec,
+                              {"vec_bytes": 32, "items_per_thread": 2, "block": 128})
+    assert pyc.batched_config(g) == (32, 2, 128)
+    assert pyc.load().pyc_reduce_batched_config(None, None, None, None) == pyc.PYC_E_ARG
+    pyc.pyc_reduce_destroy(h)
+    pyc.pyc_reduce_destroy(g)
