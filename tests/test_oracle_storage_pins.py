@@ -7,6 +7,7 @@ ties to even, written from the IEEE 754 definition of a binary format with p
 significand bits and exponent range [emin, emax]), from the binary16 format's
 boundary values, from closed forms, and from Python's unbounded integers.
 """
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -212,3 +213,64 @@ def test_map_u8_add_index_hand_values():
     x = rng.integers(0, 256, idx.size)
     got = storage.map_u8_add_index(x, idx, 20)
     assert all(int(g) == (int(a) + ((int(i) >> 20) % 256)) % 256 for g, a, i in zip(got, x, idx))
+
+
+# planted mistakes in the storage oracle: each must make one of the pins above fail
+def _f16_in_binary64(a, x16, b, y16):
+    x = np.asarray(x16, np.float16).astype(np.float64)
+    y = np.asarray(y16, np.float16).astype(np.float64)
+    return (a * x + b * y).astype(np.float16)
+
+
+def _f16_truncating(v):
+    # round toward zero instead of to nearest even
+    v = np.asarray(v, np.float64)
+    with np.errstate(over="ignore"):
+        r = v.astype(np.float16).astype(np.float64)
+    over = np.abs(r) > np.abs(v)
+    r[over] = np.nextafter(r[over].astype(np.float16), np.float16(0)).astype(np.float64)
+    return r.astype(np.float16)
+
+
+_MUTANTS = {
+    "binary16 map computed in binary64": ("lin_comb_f16", _f16_in_binary64),
+    "binary16 store truncates": ("round_f16", _f16_truncating),
+    "binary64 map sign": ("lin_comb_f64", lambda a, x, b, y: np.float64(a) * np.asarray(x)
+                          - np.float64(b) * np.asarray(y)),
+    "binary64 map contracted": ("lin_comb_f64", lambda a, x, b, y: (
+        np.longdouble(a) * np.asarray(x, np.longdouble)
+        + np.longdouble(b) * np.asarray(y, np.longdouble)).astype(np.float64)),
+    "integer map saturates": ("lin_comb_int", lambda a, x, b, y, bits: np.clip(
+        a * np.asarray(x, np.float64) + b * np.asarray(y, np.float64),
+        -2.0 ** (bits - 1), 2.0 ** (bits - 1) - 1).astype({32: np.int32, 64: np.int64}[bits])),
+    "promotion to binary32 first": ("add_f16_f64_to_f32", lambda x16, y64: (
+        np.asarray(x16, np.float16).astype(np.float32) + np.asarray(y64).astype(np.float32))),
+    "sum drops the last term": ("sum_exact", lambda t: (
+        math.fsum(np.asarray(t, np.float64).ravel()[:-1].tolist()),
+        math.fsum(np.abs(np.asarray(t, np.float64)).ravel().tolist()))),
+    "u8 map without the index": ("map_u8_add_index", lambda x, idx, shift: (
+        np.asarray(x, np.int64) & 255).astype(np.uint8)),
+    "min keeps the first element": ("min_value", lambda x, empty: (
+        np.asarray(x).ravel().tolist() or [empty])[0]),
+}
+
+_PINS = [test_round_f16_boundary_values, test_round_f16_random_against_rationals,
+         lambda: test_lin_comb_f16_against_rationals(0.1, 3.3),
+         test_lin_comb_f64_against_rationals,
+         lambda: test_lin_comb_int_wraps_like_twos_complement(32),
+         test_mixed_promotion_against_rationals, test_sum_exact_closed_form_and_sign,
+         test_sum_exact_against_rationals, test_map_u8_add_index_hand_values,
+         test_extrema_brute_force]
+
+
+@pytest.mark.parametrize("name", sorted(_MUTANTS))
+def test_pins_catch_planted_mistakes(name, monkeypatch):
+    fn, bad = _MUTANTS[name]
+    monkeypatch.setattr(storage, fn, bad)
+    failed = False
+    for pin in _PINS:
+        try:
+            pin()
+        except AssertionError:
+            failed = True
+    assert failed, "the pins did not catch: " + name
