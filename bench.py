@@ -246,11 +246,28 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
             pyc.pyc_reduce_launch(h, m, [x.data_ptr(), y.data_ptr()], None, out.data_ptr(),
                                   gs.cuda_stream)
     ms_g = _time_fn(torch, g.replay, 20) / 100
+    # cold: before each launch a 512 MiB write evicts x and y from L2; the events
+    # bracket the dot launch alone (median of 20)
+    flush = torch.empty(1 << 27, dtype=torch.float32, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cold = []
+    for r in range(23):
+        flush.fill_(float(r))
+        a.record()
+        f()
+        b.record()
+        torch.cuda.synchronize()
+        if r >= 3:
+            cold.append(a.elapsed_time(b))
+    ms_c = statistics.median(cold)
     res["dot_f32_n2^20"] = {"n": m, "us": round(ms * 1e3, 2),
                             "GB/s": round(8 * m / (ms * 1e-3) / 1e9, 1), "cache": "warm (fits L2)",
+                            "launches_per_s": round(1e3 / ms, 1),
                             "graph_us": round(ms_g * 1e3, 2),
+                            "cold_us": round(ms_c * 1e3, 2),
+                            "cold_GB/s": round(8 * m / (ms_c * 1e-3) / 1e9, 1),
                             "config": "vec%d_u%d_b%d" % pyc.launch_config(h, m, reduce=True)}
-    del g
+    del g, flush
     return res
 
 
@@ -522,12 +539,11 @@ def bench_batched(torch, pyc, stock, dev, reps=5):
     return res
 
 
-def bench_serving(torch, pyc, stock, dev, nreq=50000, rate=20000.0, budget=40 << 30):
-    """The request trace: Poisson arrivals (mean 20k/s), 60% map-reduce (dot) /
+def serving_trace(torch, pyc, stock, dev, nreq=50000, rate=20000.0):
+    """The request trace: Poisson arrivals (mean `rate`/s), 60% map-reduce (dot) /
     40% map (a*x+b*y), dtype uniform over {f32, bf16, i32}, sizes log-uniform in
-    [2^10, 2^26], inputs at random offsets of resident pools, 40 GB admission cap.
-    Open loop (arrivals as drawn) and closed loop (all queued at t=0), through the
-    serving loop and as one plain launch per request."""
+    [2^10, 2^26], inputs at random offsets of resident pools.  Returns (table,
+    arrival times in ns, algorithmic bytes, pools)."""
     from paper_1304_5553_gb300 import inputs
     P = 1 << 26
     x = inputs.uniform_f32(4, 0, P, -1.0, 1.0)
@@ -565,6 +581,14 @@ def bench_serving(torch, pyc, stock, dev, nreq=50000, rate=20000.0, budget=40 <<
         else:
             table.set(k, pyc.PYC_REQ_MAP, stock.create(maps[dt]), n, ptrs + [0], scal[dt])
             total_bytes += 3 * es * n
+    return table, arrival, total_bytes, pools
+
+
+def bench_serving(torch, pyc, stock, dev, nreq=50000, rate=20000.0, budget=40 << 30):
+    """The request trace (`serving_trace`) with a 40 GB admission cap.  Open loop
+    (arrivals as drawn) and closed loop (all queued at t=0), through the serving
+    loop and as one plain launch per request."""
+    table, arrival, total_bytes, pools = serving_trace(torch, pyc, stock, dev, nreq, rate)
     srv = pyc.pyc_server_create(budget)
     out = {"requests": nreq, "rate_per_s": rate, "budget_bytes": budget,
            "algorithmic_bytes": total_bytes}
@@ -750,6 +774,32 @@ def profile_batched(args):
                       "note": "profiling driver, not a bench value"}))
 
 
+def profile_serving(args):
+    """Profiling driver (not a bench line): the first `requests` requests of the
+    serving trace, replayed closed loop (all queued at t = 0) through the serving
+    loop: one warm-up replay, then `steps` replays, for an ncu launch list."""
+    import torch
+    from paper_1304_5553_gb300 import pyc, stock
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda")
+    table, _, total_bytes, pools = serving_trace(torch, pyc, stock, dev, args.requests)
+    srv = pyc.pyc_server_create(40 << 30)
+    try:
+        pyc.pyc_server_replay(srv, table, None, pyc.PYC_REPLAY_SERVER)
+        spans = []
+        for _ in range(args.steps):
+            res = pyc.pyc_server_replay(srv, table, None, pyc.PYC_REPLAY_SERVER)
+            assert all(r.status == pyc.PYC_OK for r in res)
+            spans.append((max(r.t_done_ns for r in res) - min(r.t_submit_ns for r in res)) / 1e9)
+    finally:
+        pyc.pyc_server_destroy(srv)
+    span = statistics.median(spans)
+    print(json.dumps({"profile_serving": args.requests, "closed_loop_reqs_per_s":
+                      round(args.requests / span, 1), "GB/s": round(total_bytes / span / 1e9, 1),
+                      "note": "profiling driver, not a bench value"}))
+    del pools
+
+
 def profile_cg(args):
     """Profiling driver (not a bench line): CG on the 5-point Laplacian of an
     nx x nx grid (binary32), a warm-up solve of 8 steps, then `steps` steps."""
@@ -930,6 +980,10 @@ def main():
                     help="profiling driver: the segmented dot (dot_f32 / dot_bf16) only")
     ap.add_argument("--segments", type=int, default=20000,
                     help="with --profile-batched: the first K segments of the segment table")
+    ap.add_argument("--profile-serving", action="store_true",
+                    help="profiling driver: closed-loop replays of the serving trace's first requests")
+    ap.add_argument("--requests", type=int, default=50000,
+                    help="with --profile-serving: the first K requests of the trace")
     ap.add_argument("--profile-cg", action="store_true",
                     help="profiling driver: CG steps on a Poisson matrix of 2^n_log2 rows")
     ap.add_argument("--lanes", type=int, default=None,
@@ -952,6 +1006,8 @@ def main():
         profile_scan(args)
     elif args.profile_batched:
         profile_batched(args)
+    elif args.profile_serving:
+        profile_serving(args)
     elif args.profile_cg:
         profile_cg(args)
     else:
