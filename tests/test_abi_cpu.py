@@ -197,6 +197,31 @@ def test_kernel_cache_memory_and_disk(tmp_path):
     assert d["compiled"] == 1 and d["disk_hits"] == 0
 
 
+def test_kernel_cache_checks_the_full_key(tmp_path):
+    # a cache file stored under one spec's hash but holding another spec's key
+    # text (what a hash collision would look like) is not loaded: the spec recompiles
+    env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
+    code = _CACHE_CHILD % ROOT
+
+    def run(stmt):
+        out = subprocess.run([sys.executable, "-c", code, stmt], env=env, capture_output=True,
+                             text=True, check=True).stdout
+        return json.loads(out.strip().splitlines()[-1])
+
+    run("z[i] = 5 * x[i]")
+    first = set(f for f in os.listdir(tmp_path) if f.endswith(".pyck"))
+    run("z[i] = 6 * x[i]")
+    second = set(f for f in os.listdir(tmp_path) if f.endswith(".pyck")) - first
+    assert len(first) == 1 and len(second) == 1
+    (a,), (b,) = first, second
+    data = open(os.path.join(tmp_path, a), "rb").read()
+    open(os.path.join(tmp_path, b), "wb").write(data)
+    r = run("z[i] = 6 * x[i]")
+    assert r["compiled"] == 1 and r["disk_hits"] == 0
+    # the other spec still loads its own file
+    assert run("z[i] = 5 * x[i]")["disk_hits"] == 1
+
+
 def test_front_end_params():
     k = pyc.ElementwiseKernel("float a, float *x, float b, float *y, float *z",
                               "z[i] = a*x[i] + b*y[i]", "linear_combination")
