@@ -186,8 +186,11 @@ int pyc_map_scalar_bytes(pyc_map_t h);
 const char* pyc_map_source(pyc_map_t h);
 
 /* Time the tuning candidates for n's size bucket on scratch buffers the library
- * allocates and frees, remember the fastest for the handle and persist it in the
- * tuning cache.  Synchronises the stream.  (Automated tuning, Sec. 3.3.1.) */
+ * allocates and frees (min(n, 2^28) elements per array, at most 6 GiB for all
+ * arrays together, halved while the device cannot hold them), remember the
+ * fastest for the handle and persist it in the tuning cache.  Synchronises the
+ * stream.  (Automated tuning, Sec. 3.3.1.)  pyc_reduce_autotune and
+ * pyc_scan_autotune size their scratch the same way. */
 pyc_status pyc_map_autotune(pyc_map_t h, int64_t n, pyc_stream_t stream);
 
 /* The launch configuration (vector bytes, unroll, block) a launch of n

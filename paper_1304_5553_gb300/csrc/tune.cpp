@@ -42,9 +42,11 @@ bool field(const std::string& line, const char* name, std::string* out) {
 
 struct Scratch {
   std::vector<CUdeviceptr> bufs;
-  ~Scratch() {
+  ~Scratch() { release(); }
+  void release() {
     for (auto b : bufs)
       if (b) drv().cuMemFree(b);
+    bufs.clear();
   }
   CUdeviceptr alloc(size_t bytes) {
     CUdeviceptr p;
@@ -86,17 +88,35 @@ double time_us(Launch&& launch, CUstream s, int reps) {
 template <class H, class Launch>
 void autotune(H* h, int64_t n, CUstream stream, bool reduce, Launch&& launch_one) {
   if (n <= 0) fail(PYC_E_ARG, "autotune needs n > 0");
-  // representative size: n itself, capped so scratch stays modest
-  int64_t nt = std::min<int64_t>(n, (int64_t)1 << 26);
+  // Representative size: n itself up to 2^28 elements (a variant's rank at a
+  // quarter of the size can differ from its rank at the size that runs), with
+  // the scratch arrays held to 6 GiB together, halved while the device cannot
+  // hold them (down to 2^20 elements).
+  const int64_t kMinTune = (int64_t)1 << 20;
+  const int64_t kScratchCap = (int64_t)6 << 30;
+  int64_t per_elem = 0;
+  for (auto& p : h->spec.params)
+    if (p.is_ptr) per_elem += type_info(p.dtype).bytes;
+  int64_t nt = std::min<int64_t>(n, (int64_t)1 << 28);
+  while (nt > kMinTune && per_elem * nt > kScratchCap) nt = (nt + 1) / 2;
   Scratch sc;
   std::vector<void*> ptrs(h->spec.num_ptrs ? h->spec.num_ptrs : 1, nullptr);
-  for (auto& p : h->spec.params)
-    if (p.is_ptr) {
-      size_t bytes = (size_t)nt * type_info(p.dtype).bytes + 256;
-      CUdeviceptr b = sc.alloc(bytes);
-      PYC_CU(drv().cuMemsetD8Async(b, 0, bytes, stream));
-      ptrs[p.ptr_slot] = reinterpret_cast<void*>(b);
+  for (;;) {
+    try {
+      for (auto& p : h->spec.params)
+        if (p.is_ptr) {
+          size_t bytes = (size_t)nt * type_info(p.dtype).bytes + 256;
+          CUdeviceptr b = sc.alloc(bytes);
+          PYC_CU(drv().cuMemsetD8Async(b, 0, bytes, stream));
+          ptrs[p.ptr_slot] = reinterpret_cast<void*>(b);
+        }
+      break;
+    } catch (const Error& e) {
+      if (e.status != PYC_E_NOMEM || nt <= kMinTune) throw;
+      sc.release();
+      nt = (nt + 1) / 2;
     }
+  }
   std::vector<unsigned char> scal(h->spec.scalar_bytes + 8, 0);
   CUdeviceptr out = sc.alloc(256);
   LaunchCfg best;
