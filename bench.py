@@ -864,11 +864,11 @@ def run_gpu(args):
     # CPU baseline first (rank 0, N = 1 only): the oracle on a bounded sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        n_s = 1 << 25
-        gbs, sec = cpu_oracle_maps(n_s)
+        n_s = N_MAP
+        gbs, sec = cpu_oracle_maps(n_s, steps=2)
         cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "the three maps over the first 2^25 elements of the same inputs "
-                         "(%.1f s on one host core)" % sec}
+               "sample": "the three maps over the same 2^%d-element inputs, twice "
+                         "(%.1f s per pass on one host core)" % (n_s.bit_length() - 1, sec)}
 
     names = [k for k in MAP_BYTES if not args.only or k in args.only.split(",")]
     with ClockSampler(local) as clk:
