@@ -276,3 +276,16 @@ def test_batched_config_default_and_fixed_options():
     assert pyc.load().pyc_reduce_batched_config(None, None, None, None) == pyc.PYC_E_ARG
     pyc.pyc_reduce_destroy(h)
     pyc.pyc_reduce_destroy(g)
+
+
+def test_no_alloc_tests_are_collected_last():
+    # the allocation-free entry point's GPU test file runs after every other
+    # GPU test, so a run that stops at the first failure has run the rest first
+    out = subprocess.run([sys.executable, "-m", "pytest", "--collect-only", "-q", "-m", "gpu",
+                          "-p", "no:cacheprovider", os.path.join(ROOT, "tests")],
+                         capture_output=True, text=True, cwd=ROOT).stdout
+    ids = [ln for ln in out.splitlines() if "::" in ln]
+    files = [ln.split("::")[0] for ln in ids]
+    assert files and files[-1].endswith("test_zz_no_alloc.py")
+    first = files.index(files[-1])
+    assert all(f.endswith("test_zz_no_alloc.py") for f in files[first:])
