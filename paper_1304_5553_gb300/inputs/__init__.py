@@ -11,6 +11,8 @@ Recipes used by the workloads (seed, stream):
   * int32 uniform on [-2^20, 2^20]
   * bf16 storage: the binary32 draw rounded to bfloat16 (round to nearest
     even, done by torch's CPU conversion)
+  * binary16 storage: the binary32 draw rounded to binary16 (round to nearest
+    even, numpy's conversion)
 """
 from __future__ import annotations
 
@@ -120,6 +122,13 @@ def to_bf16_values(x: np.ndarray) -> np.ndarray:
     import torch
     t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
     return t.to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def to_f16_values(x: np.ndarray) -> np.ndarray:
+    """binary32 draws rounded to binary16 (numpy's conversion, round to nearest
+    even), returned as a float16 array."""
+    with np.errstate(over="ignore"):
+        return np.ascontiguousarray(x, dtype=np.float32).astype(np.float16)
 
 
 # ------------------------------------------------------------------ recipes

@@ -50,3 +50,16 @@ def test_int_and_lengths():
     assert 0.45 < float((lens <= 1024).mean()) < 0.55  # median near 2^10
     gaps = inputs.exponential_f64(6, 0, 100000, 20000.0)
     assert abs(gaps.mean() * 20000.0 - 1.0) < 0.02
+
+
+def test_f16_values_round_to_nearest_even():
+    # binary16 format facts: ties to even at 1 + 2^-11 and at 2^-25 (half the
+    # smallest subnormal), the largest finite value 65504, overflow from 65520
+    v = np.array([1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, 2.0 ** -25, 3 * 2.0 ** -25, 65519.0, 65520.0],
+                 np.float32)
+    got = inputs.to_f16_values(v).astype(np.float64).tolist()
+    assert got == [1.0, 1 + 2.0 ** -9, 0.0, 2.0 ** -23, 65504.0, float("inf")]
+    x = inputs.uniform_f32(20, 0, 1000, -2.0, 2.0)
+    h = inputs.to_f16_values(x)
+    assert h.dtype == np.float16
+    assert np.all(np.abs(h.astype(np.float64) - x) <= 2.0 ** -11 * np.abs(x) + 2.0 ** -25)

@@ -54,7 +54,7 @@ def _dev(a, off=0):
 
 
 def _f16(seed, stream, n, lo=-2.0, hi=2.0):
-    return storage.round_f16(inputs.uniform_f32(seed, stream, n, lo, hi))
+    return inputs.to_f16_values(inputs.uniform_f32(seed, stream, n, lo, hi))
 
 
 def _f64(seed, stream, n, lo=-2.0, hi=2.0):
