@@ -289,3 +289,52 @@ def test_no_alloc_tests_are_collected_last():
     assert files and files[-1].endswith("test_zz_no_alloc.py")
     first = files.index(files[-1])
     assert all(f.endswith("test_zz_no_alloc.py") for f in files[first:])
+
+
+_FUZZ_CHILD = r'''
+import json, random, sys
+sys.path.insert(0, %r)
+from paper_1304_5553_gb300 import pyc
+rng = random.Random(1304)
+spec_tok = ["float", "int", "double", "__half", "unsigned", "long", "char", "const", "struct",
+            "__restrict__", "*", "**", ",", ";", "(", ")", "[", "]", "#", "x", "y", "i", "n",
+            "0", "a", "pyc_q", "void", "float *x", "int k"]
+stmt_tok = ["x[i]", "z[i]", "=", "+", "*", "/", "k", "i", "(", ")", ";", "[", "]", "1",
+            "2.5f", "if", "else", "{", "}", "#", "/*", "*/", "\"", "'", "?", ":", "return",
+            "->", ".", "x", "z", "+=", "<<", "sin(", "exp(", "n", "__syncthreads()", "\\"]
+counts = {}
+for _ in range(400):
+    s = " ".join(rng.choice(spec_tok) for _ in range(rng.randint(1, 6)))
+    try:
+        h = pyc.pyc_map_create(s, "0")
+        pyc.pyc_map_destroy(h)
+        st = 0
+    except pyc.PycError as e:
+        st = e.status
+    counts["spec%%d" %% st] = counts.get("spec%%d" %% st, 0) + 1
+for _ in range(120):
+    s = " ".join(rng.choice(stmt_tok) for _ in range(rng.randint(1, 8)))
+    try:
+        h = pyc.pyc_map_create("float *x, float *z, int k", s)
+        pyc.pyc_map_destroy(h)
+        st = 0
+    except pyc.PycError as e:
+        st = e.status
+    counts["stmt%%d" %% st] = counts.get("stmt%%d" %% st, 0) + 1
+print(json.dumps(counts))
+'''
+
+
+def test_random_specs_and_statements_never_crash(tmp_path):
+    # seeded random token soup for argument specs and statements: every create
+    # returns a status (accepted, parse error or compile error); none crashes
+    env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
+    p = subprocess.run([sys.executable, "-c", _FUZZ_CHILD % ROOT], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    counts = json.loads(p.stdout.strip().splitlines()[-1])
+    allowed = {pyc.PYC_OK, pyc.PYC_E_PARSE, pyc.PYC_E_COMPILE, pyc.PYC_E_ARG}
+    for k in counts:
+        assert int(k[4:]) in allowed, counts
+    assert sum(v for k, v in counts.items() if k.startswith("spec")) == 400
+    assert sum(v for k, v in counts.items() if k.startswith("stmt")) == 120
