@@ -321,13 +321,37 @@ for _ in range(120):
     except pyc.PycError as e:
         st = e.status
     counts["stmt%%d" %% st] = counts.get("stmt%%d" %% st, 0) + 1
+red_tok = ["a", "b", "+", "*", "?", ":", ">", "<", "(", ")", "0", "1", "INFINITY", "x[i]",
+           "y[i]", ";", "{", "#", "a>b", "i", "/*", "\"", "min(", "fmaxf(a,b)", ","]
+for _ in range(120):
+    parts = [" ".join(rng.choice(red_tok) for _ in range(rng.randint(1, 5))) for _ in range(3)]
+    try:
+        h = pyc.pyc_reduce_create(rng.choice([pyc.PYC_F32, pyc.PYC_I64, pyc.PYC_F64]), parts[0],
+                                  parts[1], parts[2], "float *x, float *y")
+        pyc.pyc_reduce_destroy(h)
+        st = 0
+    except pyc.PycError as e:
+        st = e.status
+    counts["red%%d" %% st] = counts.get("red%%d" %% st, 0) + 1
+for _ in range(60):
+    parts = [" ".join(rng.choice(red_tok + ["item", "prev_item", "y[i] ="])
+                      for _ in range(rng.randint(1, 5))) for _ in range(4)]
+    try:
+        h = pyc.pyc_scan_create(pyc.PYC_F32, parts[0], parts[1], parts[2], parts[3],
+                                "float *x, float *y")
+        pyc.pyc_scan_destroy(h)
+        st = 0
+    except pyc.PycError as e:
+        st = e.status
+    counts["scan%%d" %% st] = counts.get("scan%%d" %% st, 0) + 1
 print(json.dumps(counts))
 '''
 
 
 def test_random_specs_and_statements_never_crash(tmp_path):
-    # seeded random token soup for argument specs and statements: every create
-    # returns a status (accepted, parse error or compile error); none crashes
+    # seeded random token soup for argument specs, map statements, map-reduce and
+    # scan expressions: every create returns a status (accepted, parse error or
+    # compile error); none crashes
     env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
     p = subprocess.run([sys.executable, "-c", _FUZZ_CHILD % ROOT], env=env, capture_output=True,
                        text=True, timeout=600)
@@ -335,6 +359,8 @@ def test_random_specs_and_statements_never_crash(tmp_path):
     counts = json.loads(p.stdout.strip().splitlines()[-1])
     allowed = {pyc.PYC_OK, pyc.PYC_E_PARSE, pyc.PYC_E_COMPILE, pyc.PYC_E_ARG}
     for k in counts:
-        assert int(k[4:]) in allowed, counts
+        assert int(re.sub(r"\D", "", k)) in allowed, counts
     assert sum(v for k, v in counts.items() if k.startswith("spec")) == 400
     assert sum(v for k, v in counts.items() if k.startswith("stmt")) == 120
+    assert sum(v for k, v in counts.items() if k.startswith("red")) == 120
+    assert sum(v for k, v in counts.items() if k.startswith("scan")) == 60
