@@ -344,14 +344,27 @@ for _ in range(60):
     except pyc.PycError as e:
         st = e.status
     counts["scan%%d" %% st] = counts.get("scan%%d" %% st, 0) + 1
+expr_tok = ["(", ")", "(+", "(*", "(-", "(/", "(sin", "(exp", "(where", "(pow", "(f32", "(i64",
+            "(<", "(min", "$0", "$1", "$2", "%%2", "%%0", "$9", "1.5", "2", "-3", "1e400", "(neg",
+            "(floor", "(bogus", "))", "$", "%%", "(rsqrt"]
+for _ in range(150):
+    e = " ".join(rng.choice(expr_tok) for _ in range(rng.randint(1, 9)))
+    try:
+        h = pyc.pyc_expr_map_create(e, [pyc.PYC_F32, pyc.PYC_I32, pyc.PYC_F32], [1, 1, 0],
+                                    pyc.PYC_F32)
+        pyc.pyc_map_destroy(h)
+        st = 0
+    except pyc.PycError as err:
+        st = err.status
+    counts["expr%%d" %% st] = counts.get("expr%%d" %% st, 0) + 1
 print(json.dumps(counts))
 '''
 
 
 def test_random_specs_and_statements_never_crash(tmp_path):
     # seeded random token soup for argument specs, map statements, map-reduce and
-    # scan expressions: every create returns a status (accepted, parse error or
-    # compile error); none crashes
+    # scan expressions and fused array expressions: every create returns a status
+    # (accepted, parse, argument or compile error); none crashes
     env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
     p = subprocess.run([sys.executable, "-c", _FUZZ_CHILD % ROOT], env=env, capture_output=True,
                        text=True, timeout=600)
@@ -364,3 +377,4 @@ def test_random_specs_and_statements_never_crash(tmp_path):
     assert sum(v for k, v in counts.items() if k.startswith("stmt")) == 120
     assert sum(v for k, v in counts.items() if k.startswith("red")) == 120
     assert sum(v for k, v in counts.items() if k.startswith("scan")) == 60
+    assert sum(v for k, v in counts.items() if k.startswith("expr")) == 150
