@@ -378,3 +378,31 @@ def test_random_specs_and_statements_never_crash(tmp_path):
     assert sum(v for k, v in counts.items() if k.startswith("red")) == 120
     assert sum(v for k, v in counts.items() if k.startswith("scan")) == 60
     assert sum(v for k, v in counts.items() if k.startswith("expr")) == 150
+
+
+def test_plain_c_program_uses_the_header_and_library(tmp_path):
+    # the boundary is a C ABI: a C11 program compiles against include/pyc.h with
+    # strict warnings, links libpyc.so and makes the calls that need no GPU
+    from paper_1304_5553_gb300 import buildlib
+    src = os.path.join(ROOT, "tests", "c_abi", "abi_consumer.c")
+    lib = buildlib.pyc_lib_path()
+    pyc.load()
+    exe = str(tmp_path / "abi_consumer")
+    cc = os.environ.get("CC", "gcc")
+    p = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), src, "-o", exe,
+                        "-L", os.path.dirname(lib), "-lpyc",
+                        "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert p.returncode == 0, p.stderr
+    env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path / "cache"))
+    out = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    lines = out.stdout.splitlines()
+    assert lines[0].startswith("version pyc ")
+    assert "map params 5 scalar_bytes 8" in lines
+    assert "param a ptr 0 dtype %d off 0 slot -1" % pyc.PYC_F32 in lines
+    assert "param x ptr 1 dtype %d off -1 slot 0" % pyc.PYC_F32 in lines
+    assert "param z ptr 1 dtype %d off -1 slot 2" % pyc.PYC_F32 in lines
+    assert "source has kernel 1" in lines
+    assert "reduce_create 0 out_bytes 4" in lines
+    assert "bad spec %d null 1 msg 1" % pyc.PYC_E_PARSE in lines
