@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
+#include <future>
 #include <sstream>
 
 #include "common.h"
@@ -85,6 +86,9 @@ std::atomic<long long> g_compiled{0}, g_disk{0}, g_mem{0};
 
 std::mutex g_cache_mu;
 std::map<std::string, std::weak_ptr<Module>> g_mem_cache;
+// keys being loaded or compiled right now: a second thread asking for the same
+// key waits for the first one's result instead of compiling it again
+std::map<std::string, std::shared_future<std::shared_ptr<Module>>> g_inflight;
 // keep recently used modules alive even when no handle holds them; never
 // destroyed, so no driver call runs during static destruction at exit
 std::vector<std::shared_ptr<Module>>* g_recent = new std::vector<std::shared_ptr<Module>>();
@@ -193,6 +197,11 @@ std::string cache_dir() {
   return base + "/pyc";
 }
 
+namespace {
+std::shared_ptr<Module> load_or_compile(const std::string& key, const std::string& key_text,
+                                        const std::string& source, bool fmad);
+}  // namespace
+
 std::shared_ptr<Module> get_module(const std::string& source, bool fmad) {
   int maj = 0, mnr = 0;
   {
@@ -203,8 +212,9 @@ std::shared_ptr<Module> get_module(const std::string& source, bool fmad) {
   std::string key_text = std::string(kLibTag) + "|" + kArch + "|nvrtc" + std::to_string(maj) +
                          "." + std::to_string(mnr) + "|fmad=" + (fmad ? "1" : "0") + "\n" + source;
   std::string key = digest(key_text);
+  std::promise<std::shared_ptr<Module>> promise;
   {
-    std::lock_guard<std::mutex> lk(g_cache_mu);
+    std::unique_lock<std::mutex> lk(g_cache_mu);
     auto it = g_mem_cache.find(key);
     if (it != g_mem_cache.end()) {
       if (auto m = it->second.lock()) {
@@ -212,7 +222,41 @@ std::shared_ptr<Module> get_module(const std::string& source, bool fmad) {
         return m;
       }
     }
+    auto fl = g_inflight.find(key);
+    if (fl != g_inflight.end()) {
+      std::shared_future<std::shared_ptr<Module>> pending = fl->second;
+      lk.unlock();
+      ++g_mem;
+      return pending.get();  // the other thread's module, or its error rethrown
+    }
+    g_inflight.emplace(key, promise.get_future().share());
   }
+  try {
+    auto m = load_or_compile(key, key_text, source, fmad);
+    {
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      g_mem_cache[key] = m;
+      g_recent->push_back(m);
+      if (g_recent->size() > 64) g_recent->erase(g_recent->begin());
+      g_inflight.erase(key);
+    }
+    promise.set_value(m);
+    return m;
+  } catch (...) {
+    {
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      g_inflight.erase(key);
+    }
+    promise.set_exception(std::current_exception());
+    throw;
+  }
+}
+
+namespace {
+
+// Disk-cache lookup, else NVRTC compilation (written back to the disk cache).
+std::shared_ptr<Module> load_or_compile(const std::string& key, const std::string& key_text,
+                                        const std::string& source, bool fmad) {
   std::string dir = cache_dir();
   std::string path = dir.empty() ? "" : dir + "/" + key + ".pyck";
   std::string cubin;
@@ -239,13 +283,10 @@ std::shared_ptr<Module> get_module(const std::string& source, bool fmad) {
       std::rename(tmp.c_str(), path.c_str());  // atomic publish
     }
   }
-  auto m = std::make_shared<Module>(cubin);
-  std::lock_guard<std::mutex> lk(g_cache_mu);
-  g_mem_cache[key] = m;
-  g_recent->push_back(m);
-  if (g_recent->size() > 64) g_recent->erase(g_recent->begin());
-  return m;
+  return std::make_shared<Module>(cubin);
 }
+
+}  // namespace
 
 CacheStats cache_stats() {
   CacheStats s;

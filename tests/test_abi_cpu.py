@@ -406,3 +406,55 @@ def test_plain_c_program_uses_the_header_and_library(tmp_path):
     assert "source has kernel 1" in lines
     assert "reduce_create 0 out_bytes 4" in lines
     assert "bad spec %d null 1 msg 1" % pyc.PYC_E_PARSE in lines
+
+
+_THREADS_CHILD = r'''
+import json, sys, threading
+sys.path.insert(0, %r)
+from paper_1304_5553_gb300 import pyc
+specs = [("float *x, float *z", "z[i] = %%d * x[i] + 1" %% k) for k in range(6)]
+results, errors = {}, []
+
+def worker(t):
+    try:
+        for j in range(len(specs)):
+            spec, stmt = specs[(j + t) %% len(specs)]
+            h = pyc.pyc_map_create(spec, stmt)
+            results.setdefault(stmt, set()).add(pyc.pyc_map_source(h))
+            pyc.pyc_map_destroy(h)
+            r = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", stmt.split("= ")[1], spec)
+            pyc.pyc_reduce_destroy(r)
+        try:  # a spec that fails to compile: every thread gets the compile error
+            pyc.pyc_map_create("float *x, float *z", "z[i] = no_such_function(x[i])")
+            errors.append("compiled a bad spec")
+        except pyc.PycError as e:
+            if e.status != pyc.PYC_E_COMPILE or "no_such_function" not in str(e):
+                errors.append("wrong error: %%d %%s" %% (e.status, e))
+    except Exception as e:  # reported to the parent
+        errors.append(repr(e))
+
+ts = [threading.Thread(target=worker, args=(t,)) for t in range(8)]
+[t.start() for t in ts]
+[t.join() for t in ts]
+print(json.dumps({"errors": errors, "distinct_sources": {k: len(v) for k, v in results.items()},
+                  "stats": pyc.pyc_cache_stats()}))
+'''
+
+
+def test_concurrent_creates_from_eight_threads(tmp_path):
+    # eight host threads create the same six map and six map-reduce specs in
+    # different orders (the C calls run without the interpreter lock): no errors,
+    # one generated source per spec, and each of the twelve kernels compiled once
+    # (a thread that asks while another compiles the same source waits for it)
+    env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
+    p = subprocess.run([sys.executable, "-c", _THREADS_CHILD % ROOT], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    res = json.loads(p.stdout.strip().splitlines()[-1])
+    assert res["errors"] == []
+    assert len(res["distinct_sources"]) == 6
+    assert all(v == 1 for v in res["distinct_sources"].values())
+    assert res["stats"]["compiled"] == 12
+    # the twelve good kernels: 84 hits; the failing spec: a thread that asked while
+    # another compiled it counts a hit, one that asked later compiles (and fails) again
+    assert 8 * 12 - 12 <= res["stats"]["mem_hits"] <= 8 * 12 - 12 + 7
