@@ -30,7 +30,9 @@
  *     faults surface at the caller's next synchronisation.
  *   - Handles are safe to launch from several threads.  Creating a handle
  *     needs no GPU (parse, generate, compile); the first launch on a device
- *     loads the module there.
+ *     loads the module there.  Handles may be created from several threads at
+ *     once: a source that one thread is compiling is not compiled again by
+ *     another, which waits for the first one's module (or its error).
  */
 #ifndef PYC_H
 #define PYC_H
