@@ -245,6 +245,29 @@ pyc_status pyc_reduce_batched(pyc_reduce_t h, int64_t nseg, const int64_t* seg_o
                               void* const* ptrs, const void* scalars, void* d_out,
                               pyc_stream_t stream);
 
+/* Work plan of pyc_reduce_batched for a segment table, computed on the host
+ * with no GPU work (introspection and tests; the launch builds the same plan).
+ * Arguments as for pyc_reduce_batched (ptrs: the base arrays; they are not
+ * dereferenced).  The plan has one task per segment: segments of at most 2048
+ * elements first, in input order, reduced one warp each; then longer segments,
+ * longest first (ties in input order), cut into chunks of whole tiles.
+ *   task_info  NULL, or 6 int64 per task in plan order: segment index, length n,
+ *              vector head (elements before the first aligned vector; -1 when
+ *              the arrays share no alignment and the task runs element-wise),
+ *              chunk length (elements), number of chunks (0 for one-warp tasks),
+ *              first partial slot (used when it has more than one chunk).
+ *   items      NULL, or 4 int32 per work item: (task, chunk, count, 0); chunk >= 0
+ *              is one chunk of a long task (count 1); chunk = -1 is a bundle of
+ *              `count` one-warp tasks starting at task index `task`.
+ *   items_cap  capacity of items in work items (PYC_E_ARG if too small).
+ *   n_items, n_slots  NULL, or the number of work items and of partial slots.
+ * The configuration is the handle's batched one (pyc_reduce_batched_config).
+ * Errors as for pyc_reduce_batched. */
+pyc_status pyc_reduce_batched_plan(pyc_reduce_t h, int64_t nseg, const int64_t* seg_offsets,
+                                   void* const* ptrs, const void* scalars, int64_t* task_info,
+                                   int32_t* items, int64_t items_cap, int64_t* n_items,
+                                   int64_t* n_slots);
+
 /* Map-reduce launch that allocates nothing.  The paper has no counterpart.
  * For callers that cannot allocate device memory when they launch: programs
  * that reserve all device memory at start-up and must not allocate afterwards

@@ -290,6 +290,69 @@ void reduce_batched_autotune(pyc_reduce* h, int64_t nseg, const int64_t* off, vo
   tune_cache_store(*h, true, kBatchedBucket, best, best_us);
 }
 
+// Host-side view of the work plan pyc_reduce_batched builds for a segment
+// table: the same task construction as build_plan (tasks over each segment's
+// offset pointers) and the same work list writer, with a stand-in output base
+// so that each task record names its segment.  Nothing touches a GPU.
+void reduce_batched_plan(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const* ptrs,
+                         const void* scalars, int64_t* task_info, int32_t* items_out,
+                         int64_t items_cap, int64_t* n_items, int64_t* n_slots) {
+  char* const base = reinterpret_cast<char*>((uintptr_t)1 << 20);  // never written
+  check_batched_args(h, nseg, off, base);
+  if (n_items) *n_items = 0;
+  if (n_slots) *n_slots = 0;
+  if (nseg == 0) return;
+  if (h->spec.num_ptrs > 0 && !ptrs) fail(PYC_E_ARG, "ptrs is NULL but the spec declares arrays");
+  const LaunchCfg cfg = batched_cfg(*h, true);
+  const ArgSpec& spec = h->spec;
+  const ReduceGen& g = h->gen;
+  const size_t np = spec.num_ptrs ? spec.num_ptrs : 1;
+  std::vector<void*> tptrs((size_t)nseg * np, nullptr);
+  std::vector<ReduceTaskIn> in((size_t)nseg);
+  for (int64_t s = 0; s < nseg; ++s) {
+    void** tp = &tptrs[(size_t)s * np];
+    for (auto& p : spec.params)
+      if (p.is_ptr)
+        tp[p.ptr_slot] = static_cast<char*>(ptrs[p.ptr_slot]) + off[s] * type_info(p.dtype).bytes;
+    in[s] = {tp, scalars, off[s + 1] - off[s], base + s * g.out_bytes};
+  }
+  std::vector<unsigned char> tasks;
+  std::vector<ReduceItem> items;
+  const int64_t slots = write_reduce_work(h, cfg, in, tasks, items);
+  if (items_out && (int64_t)items.size() > items_cap)
+    fail(PYC_E_ARG, "items_cap " + std::to_string(items_cap) + " < " +
+                        std::to_string(items.size()) + " work items");
+  if (n_items) *n_items = (int64_t)items.size();
+  if (n_slots) *n_slots = slots;
+  if (items_out)
+    for (size_t k = 0; k < items.size(); ++k) {
+      items_out[4 * k] = items[k].task;
+      items_out[4 * k + 1] = items[k].chunk;
+      items_out[4 * k + 2] = items[k].count;
+      items_out[4 * k + 3] = 0;
+    }
+  if (task_info)
+    for (int64_t t = 0; t < nseg; ++t) {
+      const unsigned char* rec = &tasks[(size_t)t * g.task_bytes];
+      int64_t n, head, chunk;
+      char* out;
+      int32_t nchunks, slot0;
+      std::memcpy(&n, rec + g.task_off_n, 8);
+      std::memcpy(&head, rec + g.task_off_head, 8);
+      std::memcpy(&chunk, rec + g.task_off_chunk, 8);
+      std::memcpy(&out, rec + g.task_off_out, 8);
+      std::memcpy(&nchunks, rec + g.task_off_nchunks, 4);
+      std::memcpy(&slot0, rec + g.task_off_slot0, 4);
+      int64_t* ti = task_info + 6 * t;
+      ti[0] = (int64_t)((out - base) / g.out_bytes);
+      ti[1] = n;
+      ti[2] = head;
+      ti[3] = chunk;
+      ti[4] = nchunks;
+      ti[5] = slot0;
+    }
+}
+
 void free_plans(pyc_reduce* h) {
   std::lock_guard<std::mutex> lk(h->plan_mu);
   for (auto& p : h->plans) p->release();
@@ -297,3 +360,17 @@ void free_plans(pyc_reduce* h) {
 }
 
 }  // namespace pyc
+
+using namespace pyc;
+
+PYC_API pyc_status pyc_reduce_batched_plan(pyc_reduce_t h, int64_t nseg,
+                                           const int64_t* seg_offsets, void* const* ptrs,
+                                           const void* scalars, int64_t* task_info,
+                                           int32_t* items, int64_t items_cap, int64_t* n_items,
+                                           int64_t* n_slots) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    reduce_batched_plan(h, nseg, seg_offsets, ptrs, scalars, task_info, items, items_cap, n_items,
+                        n_slots);
+  });
+}

@@ -114,7 +114,7 @@ EXPORTED = [
     "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
     "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay", "pyc_map_launch_host",
     "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
-    "pyc_reduce_batched_config",
+    "pyc_reduce_batched_config", "pyc_reduce_batched_plan",
     "pyc_scan_create", "pyc_scan_launch", "pyc_scan_num_params", "pyc_scan_param",
     "pyc_scan_scalar_bytes", "pyc_scan_source", "pyc_scan_autotune", "pyc_scan_config", "pyc_scan_destroy",
     "pyc_scan_sync", "pyc_scan_launch_test", "pyc_expr_map_create", "pyc_expr_reduce_create",
@@ -154,6 +154,8 @@ def load(build_if_missing=True):
         "pyc_map_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_reduce_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_reduce_batched_config": (st, [vp] + [ctypes.POINTER(i32)] * 3),
+        "pyc_reduce_batched_plan": (st, [vp, i64, vp, ctypes.POINTER(vp), vp, vp, vp, i64,
+                                         ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "pyc_scan_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_map_num_params": (i32, [vp]),
         "pyc_map_param": (st, [vp, i32, ctypes.POINTER(pyc_param_info)]),
@@ -538,6 +540,26 @@ def launch_config(h, n, reduce=False):
     fn = getattr(load(), "pyc_%s_config" % _kind(reduce))
     _check(fn(h, int(n), ctypes.byref(v), ctypes.byref(u), ctypes.byref(b)))
     return v.value, u.value, b.value
+
+
+def batched_plan(h, seg_offsets, ptrs, scalars=None):
+    """Host-side work plan of pyc_reduce_batched: (task_info (nseg x 6 int64:
+    segment, n, head, chunk, nchunks, slot0), items (k x 4 int32: task, chunk,
+    count, 0), partial slots)."""
+    import numpy as np
+    off = np.ascontiguousarray(seg_offsets, dtype=np.int64)
+    nseg = off.size - 1
+    lib = load()
+    n_items, n_slots = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.pyc_reduce_batched_plan(h, nseg, off.ctypes.data, _ptr_array(ptrs), scalars,
+                                       None, None, 0, ctypes.byref(n_items),
+                                       ctypes.byref(n_slots)))
+    info = np.zeros((max(nseg, 0), 6), np.int64)
+    items = np.zeros((n_items.value, 4), np.int32)
+    _check(lib.pyc_reduce_batched_plan(h, nseg, off.ctypes.data, _ptr_array(ptrs), scalars,
+                                       info.ctypes.data, items.ctypes.data, n_items.value,
+                                       ctypes.byref(n_items), ctypes.byref(n_slots)))
+    return info, items, n_slots.value
 
 
 def batched_config(h):
