@@ -132,12 +132,18 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
 
 namespace {
 
-void check_batched_args(pyc_reduce* h, int64_t nseg, const int64_t* off, void* d_out) {
+// Everything that can be rejected before any GPU work: the plan's cache key and
+// the task records read ptrs[] and the scalar block, so NULLs stop here.
+void check_batched_args(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const* ptrs,
+                        const void* scalars, void* d_out) {
   if (nseg < 0) fail(PYC_E_ARG, "nseg must be >= 0");
   if (nseg > (int64_t)INT32_MAX / 2) fail(PYC_E_ARG, "too many segments");
   if (nseg == 0) return;
   if (!off) fail(PYC_E_ARG, "seg_offsets is NULL");
   if (!d_out) fail(PYC_E_ARG, "d_out is NULL");
+  if (h->spec.num_ptrs > 0 && !ptrs) fail(PYC_E_ARG, "ptrs is NULL but the spec declares arrays");
+  if (h->spec.scalar_bytes > 0 && !scalars)
+    fail(PYC_E_ARG, "scalars is NULL but the spec declares scalar parameters");
   if (reinterpret_cast<uintptr_t>(d_out) % (uintptr_t)std::min(h->gen.out_bytes, 8))
     fail(PYC_E_ARG, "d_out is not aligned to the result type");
   if (off[0] < 0) fail(PYC_E_ARG, "seg_offsets[0] must be >= 0");
@@ -174,7 +180,7 @@ LaunchCfg batched_cfg(HandleBase& h, bool reduce) {
 
 void reduce_batched(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const* ptrs,
                     const void* scalars, void* d_out, CUstream stream) {
-  check_batched_args(h, nseg, off, d_out);
+  check_batched_args(h, nseg, off, ptrs, scalars, d_out);
   if (nseg == 0) return;
   LaunchCfg cfg = batched_cfg(*h, true);
 
@@ -232,7 +238,7 @@ namespace pyc {
 // handle's batched configuration (also persisted in the tuning cache).
 void reduce_batched_autotune(pyc_reduce* h, int64_t nseg, const int64_t* off, void* const* ptrs,
                              const void* scalars, void* d_out, CUstream stream) {
-  check_batched_args(h, nseg, off, d_out);
+  check_batched_args(h, nseg, off, ptrs, scalars, d_out);
   if (nseg == 0) fail(PYC_E_ARG, "autotune needs nseg > 0");
   const Driver& d = drv();
   CUevent e0, e1;
@@ -298,11 +304,10 @@ void reduce_batched_plan(pyc_reduce* h, int64_t nseg, const int64_t* off, void* 
                          const void* scalars, int64_t* task_info, int32_t* items_out,
                          int64_t items_cap, int64_t* n_items, int64_t* n_slots) {
   char* const base = reinterpret_cast<char*>((uintptr_t)1 << 20);  // never written
-  check_batched_args(h, nseg, off, base);
+  check_batched_args(h, nseg, off, ptrs, scalars, base);
   if (n_items) *n_items = 0;
   if (n_slots) *n_slots = 0;
   if (nseg == 0) return;
-  if (h->spec.num_ptrs > 0 && !ptrs) fail(PYC_E_ARG, "ptrs is NULL but the spec declares arrays");
   const LaunchCfg cfg = batched_cfg(*h, true);
   const ArgSpec& spec = h->spec;
   const ReduceGen& g = h->gen;

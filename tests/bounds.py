@@ -1,4 +1,5 @@
-"""Error bounds used by the parity tests (derivations in the design doc).
+"""Error bounds used by the parity tests, each derived in its docstring from
+the rounding of the operations it covers.
 
 u = 2^-24 is the unit roundoff of binary32 (half an ulp at 1).
 """

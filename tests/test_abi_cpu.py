@@ -153,6 +153,31 @@ def test_batched_validation_before_any_gpu_work():
         pyc.pyc_reduce_destroy(h)
 
 
+def test_batched_null_arrays_and_scalars_are_argument_errors():
+    """A NULL ptrs (or scalar block) for a spec that declares arrays (scalars)
+    is PYC_E_ARG from the segmented calls and the plan call alike, before any
+    read of the missing table (the plan's cache key copies ptrs[])."""
+    import numpy as np
+    lib = pyc.load()
+    off = np.array([0, 7, 100], np.int64)
+    offp = off.ctypes.data_as(pyc.ctypes.POINTER(pyc.ctypes.c_int64))
+    h = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i]", "float *x, float *y")
+    hs = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "a*x[i]", "float a, float *x")
+    try:
+        for fn in (lib.pyc_reduce_batched, lib.pyc_reduce_batched_autotune):
+            assert fn(h, 2, offp, None, None, 1 << 22, None) == pyc.PYC_E_ARG
+            assert "ptrs is NULL" in pyc.pyc_last_error()
+            assert fn(hs, 2, offp, pyc._ptr_array([1 << 20]), None, 1 << 22, None) == pyc.PYC_E_ARG
+            assert "scalars is NULL" in pyc.pyc_last_error()
+        assert lib.pyc_reduce_batched_plan(h, 2, off.ctypes.data, None, None, None, None, 0,
+                                           None, None) == pyc.PYC_E_ARG
+        assert lib.pyc_reduce_batched_plan(hs, 2, off.ctypes.data, pyc._ptr_array([1 << 20]),
+                                           None, None, None, 0, None, None) == pyc.PYC_E_ARG
+    finally:
+        pyc.pyc_reduce_destroy(h)
+        pyc.pyc_reduce_destroy(hs)
+
+
 @pytest.mark.skipif(_has_gpu(), reason="checks the no-driver error path")
 def test_launch_without_driver_is_an_error():
     h = pyc.pyc_map_create("float *x", "x[i] = 1")
