@@ -280,15 +280,31 @@ pyc_status pyc_reduce_batched_plan(pyc_reduce_t h, int64_t nseg, const int64_t* 
  * which every GPU that loads the library holds until the process exits.  A
  * reduction whose chunk plan needs more partial bytes than that is rejected with
  * PYC_E_ARG (the planner caps a reduction at 4096 chunks, so none does today).
- * The first call on a device is its set-up: it looks up the scratch address and
- * loads the kernels there, which may allocate; make that first call before any
- * stream capture.  Later calls allocate nothing: no cudaMalloc, no cudaFree, no
- * allocating library routine.  All calls share the one scratch area and it keeps
- * what the last call left: each call clears the ticket itself, but calls that
- * overlap on the GPU (e.g. on two streams with no ordering between them) race
- * and give wrong results, so serialise them.  Errors as for pyc_reduce_launch. */
+ * Set-up happens on first use and may allocate: the first call in a context
+ * looks up the scratch address there (loading the library's own device module),
+ * and the first call of each handle in each context loads that handle's kernels
+ * and queries their occupancy.  So make one call of every handle you will use,
+ * in every context you will use it in, before any stream capture and before the
+ * point after which you may not allocate.  Later calls allocate nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  All calls in a
+ * context share its one scratch area, and it keeps what the last call left:
+ * each call clears the ticket itself, but calls that overlap on the GPU (e.g. on
+ * two streams with no ordering between them) race and give wrong results, so
+ * serialise them.  Errors as for pyc_reduce_launch. */
 pyc_status pyc_reduce_launch_static(pyc_reduce_t h, int64_t n, void* const* ptrs,
                                     const void* scalars, void* d_out, pyc_stream_t stream);
+
+/* The static scratch area of pyc_reduce_launch_static in the current context
+ * (the primary context of device $CUDA_DEVICE, default 0, if none is current):
+ * *d_addr = its device address there, *bytes = its size (65,792).  Either
+ * pointer may be NULL.  The first query in a context performs that context's
+ * address lookup (the same one the launch's set-up does); no kernel runs.
+ * Each context has its own area: the primary context and a context created
+ * with cuCtxCreate on the same device get different addresses.  Like all of the
+ * library's per-context state, entries are kept by context handle, so a context
+ * the library has used must not be destroyed and replaced while the process
+ * still calls the library.  Errors: PYC_E_ARG (both NULL), PYC_E_CUDA. */
+pyc_status pyc_reduce_static_scratch(void** d_addr, int64_t* bytes);
 
 /* Tune the batched launch (automated tuning, Sec. 3.3.1): time every vector
  * width x unroll x block candidate of the segmented reducer on this segment

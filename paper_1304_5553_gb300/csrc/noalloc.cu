@@ -14,6 +14,7 @@
 // and tuning.
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 
 #include "cudrv.h"
@@ -30,27 +31,29 @@ constexpr size_t kScratchBytes = kPartBytes + 256;
 // the device object; the device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char pyc_static_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
+// Scratch address per context.  The array's address is a property of the
+// module instance in a context, not of the device: two contexts on one device
+// (the primary one and one a caller created with cuCtxCreate) each hold their
+// own copy of the library's device module, so each gets its own entry.  Like
+// the library's other per-context state (modules, workspaces), entries are
+// keyed by the context handle.
 std::mutex g_mu;
-void* g_scratch[kMaxDevices] = {};
+std::map<CUcontext, void*> g_scratch;
 
-// Device address of the scratch area on the current device; the first call on
-// a device looks it up (this loads the library's own device module there).
-void* scratch_address() {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) pyc::fail(PYC_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) pyc::fail(PYC_E_CUDA, "device ordinal out of range");
+// Device address of the scratch area in `ctx`, which must be current; the first
+// call in a context looks it up (this loads the library's own device module
+// there).
+void* scratch_address(CUcontext ctx) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, pyc_static_scratch);
-    if (e != cudaSuccess || !p)
-      pyc::fail(PYC_E_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
-                                cudaGetErrorString(e));
-    g_scratch[dev] = p;
-  }
-  return g_scratch[dev];
+  auto it = g_scratch.find(ctx);
+  if (it != g_scratch.end()) return it->second;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, pyc_static_scratch);
+  if (e != cudaSuccess || !p)
+    pyc::fail(PYC_E_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
+                              cudaGetErrorString(e));
+  g_scratch.emplace(ctx, p);
+  return p;
 }
 
 int variant_index(const pyc::Variant& v) {
@@ -93,7 +96,7 @@ PYC_API pyc_status pyc_reduce_launch_static(pyc_reduce_t h, int64_t n, void* con
       fail(PYC_E_ARG, "d_out is not aligned to the result type");
     if (h->gen.acc_bytes > 16) fail(PYC_E_INTERNAL, "accumulator wider than the static slots");
     CUcontext ctx = ensure_context();
-    char* scratch = static_cast<char*>(scratch_address());
+    char* scratch = static_cast<char*>(scratch_address(ctx));
 
     std::lock_guard<std::mutex> lk(h->static_mu);
     setup_handle(h, ctx);
@@ -137,5 +140,13 @@ PYC_API pyc_status pyc_reduce_launch_static(pyc_reduce_t h, int64_t n, void* con
     void* params[] = {args, &n, &cp.head, &cp.chunk, &cp.nchunks, &part, &ticket, &d_out};
     PYC_CU(drv().cuLaunchKernel(h->static_fn[vi], (unsigned)cp.grid, 1, 1, (unsigned)cfg.block, 1,
                                 1, 0, s, params, nullptr));
+  });
+}
+
+PYC_API pyc_status pyc_reduce_static_scratch(void** d_addr, int64_t* bytes) {
+  return guarded([&] {
+    if (!d_addr && !bytes) fail(PYC_E_ARG, "d_addr and bytes are both NULL");
+    if (bytes) *bytes = (int64_t)kScratchBytes;
+    if (d_addr) *d_addr = scratch_address(ensure_context());
   });
 }

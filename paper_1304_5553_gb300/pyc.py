@@ -111,6 +111,7 @@ EXPORTED = [
     "pyc_reduce_create", "pyc_reduce_launch", "pyc_reduce_batched", "pyc_reduce_num_params",
     "pyc_reduce_param", "pyc_reduce_scalar_bytes", "pyc_reduce_out_bytes", "pyc_reduce_source",
     "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats", "pyc_reduce_launch_static",
+    "pyc_reduce_static_scratch",
     "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
     "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay", "pyc_map_launch_host",
     "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
@@ -169,6 +170,7 @@ def load(build_if_missing=True):
         "pyc_reduce_batched": (st, [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(vp), vp, vp,
                                     vp]),
         "pyc_reduce_launch_static": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, vp]),
+        "pyc_reduce_static_scratch": (st, [ctypes.POINTER(vp), ctypes.POINTER(i64)]),
         "pyc_scan_create": (st, [i32, cp, cp, cp, cp, cp, ctypes.POINTER(pyc_opts),
                                  ctypes.POINTER(vp)]),
         "pyc_scan_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp]),
@@ -314,6 +316,14 @@ def pyc_reduce_launch_static(h, n, ptrs, scalars, d_out, stream=None):
     """pyc_reduce_launch without any device allocation (static scratch area)."""
     _check(load().pyc_reduce_launch_static(h, int(n), _ptr_array(ptrs), scalars, d_out,
                                            _stream(stream)))
+
+
+def pyc_reduce_static_scratch():
+    """(device address, bytes) of pyc_reduce_launch_static's scratch area in the
+    current context; the first query in a context looks the address up there."""
+    a, b = ctypes.c_void_p(), ctypes.c_int64()
+    _check(load().pyc_reduce_static_scratch(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def pyc_reduce_batched(h, nseg, seg_offsets, ptrs, scalars, d_out, stream=None):

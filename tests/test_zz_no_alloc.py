@@ -92,3 +92,43 @@ def test_rejects_bad_arguments():
     with pytest.raises(pyc.PycError) as e:
         pyc.pyc_reduce_launch_static(h, 8, [x.data_ptr()], None, 0, _s())
     assert e.value.status == pyc.PYC_E_ARG
+
+
+def test_scratch_address_is_kept_per_context():
+    """The scratch address is looked up and kept per context: a second context
+    on the same device (as a caller's cuCtxCreate makes) gets its own area, and
+    the primary context keeps its first one.  Only the address lookup runs here
+    (pyc_reduce_static_scratch); no kernel is launched in the second context."""
+    import ctypes
+    cu = ctypes.CDLL("libcuda.so.1")
+    torch.zeros(1, device="cuda")  # the primary context is current
+    CU_POINTER_ATTRIBUTE_CONTEXT = 1
+
+    def owner(addr):
+        c = ctypes.c_void_p()
+        r = cu.cuPointerGetAttribute(ctypes.byref(c), CU_POINTER_ATTRIBUTE_CONTEXT,
+                                     ctypes.c_uint64(addr))
+        return c.value if r == 0 else None
+
+    cur = ctypes.c_void_p()
+    assert cu.cuCtxGetCurrent(ctypes.byref(cur)) == 0 and cur.value
+    primary = cur.value
+    a1, nbytes = pyc.pyc_reduce_static_scratch()
+    assert a1 and nbytes == 4096 * 16 + 256
+    assert owner(a1) in (primary, None)
+    dev = ctypes.c_int()
+    assert cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
+    ctx2 = ctypes.c_void_p()
+    assert cu.cuCtxCreate_v2(ctypes.byref(ctx2), 0, dev) == 0  # made current on this thread
+    try:
+        a2, _ = pyc.pyc_reduce_static_scratch()
+        assert a2 and a2 != a1  # one address space: the two areas cannot coincide
+        assert owner(a2) in (ctx2.value, None)
+        assert owner(a1) != owner(a2) or owner(a1) is None
+        assert pyc.pyc_reduce_static_scratch()[0] == a2
+    finally:
+        popped = ctypes.c_void_p()
+        assert cu.cuCtxPopCurrent_v2(ctypes.byref(popped)) == 0 and popped.value == ctx2.value
+        assert cu.cuCtxDestroy_v2(ctx2) == 0
+    assert cu.cuCtxGetCurrent(ctypes.byref(cur)) == 0 and cur.value == primary
+    assert pyc.pyc_reduce_static_scratch()[0] == a1
