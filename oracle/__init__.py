@@ -284,3 +284,58 @@ def exact_sum_f32(x):
 def exact_dot_f32(x, y):
     x, y = _f32(x), _f32(y)
     return float(_load().orc_exact_dot_f32(x.size, _ptr(x), _ptr(y)))
+
+
+# ------------------------------------------------------------------ sharded reductions
+# A map-reduce over [0, n) cut into contiguous shards.  Sec. 3.2.5 defines the
+# reduction by an associative reduce operation whose neutral element is an
+# identity, so the reduction of the whole range equals the operation applied,
+# in shard order, to the reductions of the shards.  A shard's partial is the
+# reductions above applied to the shard's own elements, with indices shifted by
+# the shard's first global index i0; combine_partials folds them in order.
+
+SHARD_KINDS = ("sum_i32_i64", "max_f32", "argmin_f32", "argmax_f32", "sum_f32", "dot_f32")
+_NO_INDEX = 2 ** 63 - 1  # index of the argmin / argmax neutral element
+
+
+def shard_partial(kind, arrays, i0):
+    """Partial of one shard: `arrays` hold the shard's elements, the first of
+    which is element i0 of the whole range.  sum_i32_i64: int; max_f32: float;
+    argmin_f32 / argmax_f32: (value, global index); sum_f32 / dot_f32: (binary64
+    sum, sum of |terms|)."""
+    if kind == "sum_i32_i64":
+        return sum_i32_i64(arrays[0])
+    if kind == "max_f32":
+        return max_f32(arrays[0])
+    if kind in ("argmin_f32", "argmax_f32"):
+        v, i = (argmin_f32 if kind == "argmin_f32" else argmax_f32)(arrays[0])
+        return v, (i if i == _NO_INDEX else i0 + i)
+    if kind == "sum_f32":
+        return sum_f32(arrays[0])
+    if kind == "dot_f32":
+        return dot_f32(arrays[0], arrays[1])
+    raise ValueError(kind)
+
+
+def combine_partials(kind, parts):
+    """Fold the shards' partials in shard order with the reduction's own
+    operation (an empty list gives the neutral element)."""
+    import math
+    if kind == "sum_i32_i64":
+        return sum(parts)
+    if kind == "max_f32":
+        m = -math.inf
+        for p in parts:
+            if p > m:
+                m = p
+        return m
+    if kind in ("argmin_f32", "argmax_f32"):
+        sign = 1.0 if kind == "argmin_f32" else -1.0
+        best = (sign * math.inf, _NO_INDEX)
+        for v, i in parts:
+            if sign * v < sign * best[0] or (v == best[0] and i < best[1]):
+                best = (v, i)
+        return best
+    if kind in ("sum_f32", "dot_f32"):
+        return math.fsum(p[0] for p in parts), sum(p[1] for p in parts)
+    raise ValueError(kind)
