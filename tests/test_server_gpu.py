@@ -233,3 +233,95 @@ def test_replay_server_and_direct_agree(pools):
         assert st["admitted_bytes"] == 0 and st["arena_in_use"] == 0
     finally:
         pyc.pyc_server_destroy(srv)
+
+
+def test_serving_config_mix_against_the_oracle():
+    """The serving workload's own mix and sizes (50,000-request config, here its
+    first 2,000 requests' recipe): Poisson arrivals at 20,000/s, 60 % dot / 40 %
+    a*x+b*y, dtype uniform over binary32 / bfloat16 / int32, sizes log-uniform in
+    [2^10, 2^26], inputs at random offsets of 2^26-element pools, a 40 GB cap.
+    Every request of at most 2^16 elements and one in 100 of the rest is checked
+    against the oracle (Sec. 3.2.4 / 3.2.5 define each request's result): map
+    outputs element by element -- bit-exact binary32 source-order evaluation for
+    binary32 and bfloat16 storage (rounded once on the store), exact for int32 --
+    and dots within the plain-sum bound (exact for int32).  The other maps write
+    into one shared sink per dtype that nothing reads."""
+    nreq, P = 2000, 1 << 26
+    x = inputs.uniform_f32(4, 0, P, -1.0, 1.0)
+    y = inputs.uniform_f32(4, 1, P, -1.0, 1.0)
+    xb, yb = inputs.to_bf16_values(x), inputs.to_bf16_values(y)
+    xi, yi = inputs.int_uniform_i32(4, 2, P), inputs.int_uniform_i32(4, 3, P)
+    host = {"f32": (x, y), "bf16": (xb, yb), "i32": (xi, yi)}
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "i32": torch.int32}
+    dev = {k: (torch.from_numpy(a).to(tdt[k]).cuda(), torch.from_numpy(b).to(tdt[k]).cuda())
+           for k, (a, b) in host.items()}
+    sink = {k: torch.empty(P, dtype=tdt[k], device="cuda") for k in host}
+    maps = {"f32": "lin_comb_f32", "bf16": "lin_comb_bf16", "i32": "lin_comb_i32"}
+    reds = {"f32": "dot_f32", "bf16": "dot_bf16", "i32": "dot_i32_i64"}
+    scal = {k: bytes(pyc.pack_scalars(stock.create(v), [3, -2] if k == "i32" else [A, B]))
+            for k, v in maps.items()}
+    u_kind = inputs.unit_f64(50, 0, nreq)
+    u_dt = inputs.unit_f64(50, 1, nreq)
+    sizes = inputs.loguniform_i64(50, 2, nreq, 10.0, 16.0, 1 << 10, 1 << 26)
+    u_off = inputs.unit_f64(50, 3, nreq)
+    arrival = np.cumsum(inputs.exponential_f64(50, 4, nreq, 20000.0) * 1e9).astype(np.int64)
+    table = pyc.RequestTable(nreq)
+    plan, outs = [], {}
+    for k in range(nreq):
+        dt = ["f32", "bf16", "i32"][min(2, int(u_dt[k] * 3))]
+        n = int(sizes[k])
+        off = int(u_off[k] * (P - n + 1))
+        a, b = dev[dt]
+        es = a.element_size()
+        ptrs = [a.data_ptr() + off * es, b.data_ptr() + off * es]
+        check = n <= (1 << 16) or k % 100 == 0
+        if u_kind[k] < 0.6:
+            table.set(k, pyc.PYC_REQ_REDUCE, stock.create(reds[dt]), n, ptrs)
+            plan.append((pyc.PYC_REQ_REDUCE, dt, n, off, check))
+        else:
+            if check:
+                outs[k] = torch.empty(n, dtype=tdt[dt], device="cuda")
+                z = outs[k].data_ptr()
+            else:
+                z = sink[dt].data_ptr() + off * es  # same alignment as the inputs
+            table.set(k, pyc.PYC_REQ_MAP, stock.create(maps[dt]), n, ptrs + [z], scal[dt])
+            plan.append((pyc.PYC_REQ_MAP, dt, n, off, check))
+    srv = pyc.pyc_server_create(40 << 30)
+    try:
+        res = pyc.pyc_server_replay(srv, table, arrival, pyc.PYC_REPLAY_SERVER)
+        torch.cuda.synchronize()
+        assert all(r.status == pyc.PYC_OK for r in res)
+        assert max(r.batch_size for r in res) > 1  # requests really shared launches
+        st = pyc.pyc_server_get_stats(srv)
+        assert st["peak_admitted_bytes"] <= 40 << 30 and st["admitted_bytes"] == 0
+    finally:
+        pyc.pyc_server_destroy(srv)
+    checked = {"map": 0, "reduce": 0, "elements": 0, "bf16_maps": 0, "big": 0}
+    for k, (kind, dt, n, off, check) in enumerate(plan):
+        if not check:
+            continue
+        a, b = host[dt][0][off:off + n], host[dt][1][off:off + n]
+        checked["elements"] += n
+        checked["big"] += n > (1 << 16)
+        if kind == pyc.PYC_REQ_MAP:
+            checked["map"] += 1
+            if dt == "i32":
+                want = (3 * a.astype(np.int64) - 2 * b.astype(np.int64)).astype(np.int32)
+                got = outs[k].cpu().numpy()
+            else:
+                want = oracle.map_lin_comb_f32ops(A, a, B, b, out_bf16=(dt == "bf16"))
+                got = outs[k].float().cpu().numpy()
+                checked["bf16_maps"] += dt == "bf16"
+            assert np.array_equal(got, want), (k, dt, n, off)
+        else:
+            checked["reduce"] += 1
+            raw = bytes(res[k].value)
+            if dt == "i32":
+                assert np.frombuffer(raw[:8], np.int64)[0] == oracle.dot_i32_i64(a, b), (k, n)
+            else:
+                ref, ab = oracle.dot_f32(a, b)
+                v = float(np.frombuffer(raw[:4], np.float32)[0])
+                assert abs(v - ref) <= plain_sum_bound(ab), (k, dt, n, v, ref)
+    print("serving mix: checked", checked)
+    assert checked["map"] > 200 and checked["reduce"] > 300 and checked["bf16_maps"] > 50
+    assert checked["big"] >= 10
