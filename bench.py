@@ -108,20 +108,23 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 
-def make_map_inputs(torch, dev, only=None):
+def make_map_inputs(torch, dev, only=None, offset=0):
+    """The maps' inputs: elements [offset, offset + N_MAP) of the seeded arrays
+    (one rank's shard of arrays of world * N_MAP elements under torchrun)."""
     from paper_1304_5553_gb300 import inputs
     n = N_MAP
     want = set(only.split(",")) if only else set(MAP_BYTES)
     host = {}
     if want & {"lin_comb_f32", "lin_comb_bf16"}:
-        x = inputs.uniform_f32(0, 0, n, -2.0, 2.0)
-        y = inputs.uniform_f32(0, 1, n, -2.0, 2.0)
+        x = inputs.uniform_f32(0, 0, n, -2.0, 2.0, offset=offset)
+        y = inputs.uniform_f32(0, 1, n, -2.0, 2.0, offset=offset)
         if "lin_comb_f32" in want:
             host["lin_comb_f32"] = [x, y]
         if "lin_comb_bf16" in want:
             host["lin_comb_bf16"] = [inputs.to_bf16_values(x), inputs.to_bf16_values(y)]
     if "gauss_sin_f32" in want:
-        host["gauss_sin_f32"] = [inputs.uniform_f32(1, s, n, -2.0, 2.0) for s in range(4)]
+        host["gauss_sin_f32"] = [inputs.uniform_f32(1, s, n, -2.0, 2.0, offset=offset)
+                                 for s in range(4)]
     d = {}
     for k, arrs in host.items():
         dt = torch.bfloat16 if k.endswith("bf16") else torch.float32
@@ -269,6 +272,33 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
                             "config": "vec%d_u%d_b%d" % pyc.launch_config(h, m, reduce=True)}
     del g, flush
     return res
+
+
+def bench_sharded_sum(torch, pyc, stock, dev, rank, world, dist, reps=10):
+    """Compensated binary32 sum over world * 2^28 elements, each rank holding a
+    2^28-element shard: shard record -> all-gather of 16-byte records (NCCL) ->
+    combine.  Time of the whole step (max over ranks)."""
+    from paper_1304_5553_gb300 import inputs
+    from paper_1304_5553_gb300.shard import ShardedReduce
+    n = N_MAP
+    x = torch.from_numpy(inputs.lognormal_signed_f32(0, 0, n, offset=rank * n)).to(dev)
+    out = torch.zeros(1, dtype=torch.float32, device=dev)
+    h = stock.create("sum_f32_comp")
+    sr = ShardedReduce(h, world * n, rank, world)
+    assert (sr.i0, sr.n) == (rank * n, n)
+    f = lambda: sr([x.data_ptr()], None, out.data_ptr())
+    for _ in range(3):
+        f()
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = max_over_ranks(_time_fn(torch, f, reps), dist, dev)
+    vals = [torch.zeros_like(out) for _ in range(world)]
+    dist.all_gather(vals, out)
+    same = all(float(v.item()) == float(out.item()) for v in vals)
+    del x
+    return {"n_total": world * n, "us": round(ms * 1e3, 2),
+            "GB/s": round(4 * world * n / (ms * 1e-3) / 1e9, 1),
+            "exchange": "all-gather of %d x 16 B" % world, "same_on_every_rank": same}
 
 
 def bench_scans(torch, pyc, stock, dev, reps=10):
@@ -621,8 +651,10 @@ def bench_serving(torch, pyc, stock, dev, nreq=50000, rate=20000.0, budget=40 <<
     return out
 
 
-def cpu_oracle_maps(n_sample, steps=1):
-    """The oracle (single-threaded C) on the three maps over n_sample elements."""
+def oracle_map_step(n_sample):
+    """The three maps' inputs over n_sample elements, generated once, and a
+    function that runs the oracle (single-threaded C) over them once and returns
+    the seconds it took."""
     import oracle
     from paper_1304_5553_gb300 import inputs
     x = inputs.uniform_f32(0, 0, n_sample, -2.0, 2.0)
@@ -630,12 +662,20 @@ def cpu_oracle_maps(n_sample, steps=1):
     bx, by = inputs.to_bf16_values(x), inputs.to_bf16_values(y)
     g = [inputs.uniform_f32(1, s, n_sample, -2.0, 2.0) for s in range(4)]
     oracle.map_lin_comb(A, x[:16], B, y[:16])  # load the library outside the timing
-    t = time.perf_counter()
-    for _ in range(steps):
+
+    def step():
+        t = time.perf_counter()
         oracle.map_lin_comb(A, x, B, y)
         oracle.map_lin_comb(A, bx, B, by, out_bf16=True)
         oracle.map_gauss_sin(*g)
-    sec = (time.perf_counter() - t) / steps
+        return time.perf_counter() - t
+    return step
+
+
+def cpu_oracle_maps(n_sample, steps=1):
+    """The oracle on the three maps over n_sample elements: (GB/s, seconds per pass)."""
+    step = oracle_map_step(n_sample)
+    sec = sum(step() for _ in range(steps)) / steps
     alg = sum(MAP_BYTES.values()) * n_sample
     return alg / sec / 1e9, sec
 
@@ -853,7 +893,8 @@ def run_gpu(args):
             dist.barrier()
 
     stock.compile_all()
-    host, d = make_map_inputs(torch, dev, args.only)
+    # each rank holds its own shard of the maps' arrays (world * 2^28 elements)
+    host, d = make_map_inputs(torch, dev, args.only, offset=rank * N_MAP)
     stream = torch.cuda.current_stream().cuda_stream
     launch = map_launchers(torch, pyc, stock, d, stream)
     if args.autotune == "on":
@@ -889,6 +930,8 @@ def run_gpu(args):
                for k in names}
 
     details = {"maps": kernels}
+    if world > 1:
+        details["sharded_sum"] = bench_sharded_sum(torch, pyc, stock, dev, rank, world, dist)
     e2e = None
     if rank == 0 and not args.quick:
         details["reductions"] = bench_reductions(torch, pyc, stock, dev)
@@ -911,7 +954,8 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
             "data": "synthetic (seeded uniform[-2,2))",
             "config": {"workload": WORKLOAD, "n": N_MAP, "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": ("sharded: rank r holds elements [r n, (r + 1) n) of "
+                                       "arrays of %d n" % world) if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4),
                          "traffic": measured_traffic(pyc, stock, dom, N_MAP),
@@ -927,34 +971,46 @@ def run_gpu(args):
 
 # ---------------------------------------------------------------- reference arm
 
-def run_reference(args):
+def run_reference(args, budget_s=170.0):
+    """The reference arm: the oracle on the host cores (rank 0 only) over the same
+    three maps.  Warm-up steps run at 2^20 elements; the timed steps run at the
+    bench's 2^28 whenever `steps` of them fit in about budget_s seconds (the
+    per-element cost measured in the warm-up), else at the largest power of two
+    that does."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_s = 1 << 20  # bounded sample per step
     import oracle
     oracle.build()
-    cpu_oracle_maps(1 << 12)
-    for _ in range(args.warmup):
-        cpu_oracle_maps(n_s)
+    warm = oracle_map_step(1 << 20)
+    per_elem = min(warm() for _ in range(max(1, args.warmup))) / (1 << 20)
+    n_s = N_MAP
+    while n_s > (1 << 20) and per_elem * n_s * args.steps > budget_s:
+        n_s //= 2
+    step = oracle_map_step(n_s)
     t = time.perf_counter()
-    secs = []
-    for _ in range(args.steps):
-        _, sec = cpu_oracle_maps(n_s)
-        secs.append(sec)
+    secs = [step() for _ in range(args.steps)]
     total = sum(secs)
     alg = sum(MAP_BYTES.values()) * n_s
     value = alg * args.steps / total / 1e9
+    full = n_s == N_MAP
+    config = {"workload": WORKLOAD, "n": N_MAP, "l2": "inputs larger than L2 (no flush)",
+              "parallelism": "single GPU"}
+    if not full:
+        config["sample_per_step"] = n_s
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded uniform[-2,2))",
-        "config": {"workload": WORKLOAD, "n": N_MAP, "sample_per_step": n_s},
+        "config": config,
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "each step: the three maps over 2^20 elements of the same "
-                                   "inputs (binary64 oracle, one host core)"},
+                         "sample": "each timed step: the three maps over 2^%d elements of the "
+                                   "same inputs (%s; binary64 oracle, one host core; warm-up "
+                                   "steps at 2^20)" % (n_s.bit_length() - 1,
+                                                       "the full workload" if full else
+                                                       "a sample, to bound the run")},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "wall_s": round(time.perf_counter() - t, 2),

@@ -105,6 +105,16 @@ typedef struct {
                            bit-for-bit against IEEE binary32 evaluation of the source. */
   const char* preamble; /* optional device code (helper functions, constants) placed
                            before the kernel; NULL = none */
+  int debug_bounds;     /* 1 = bounds-checked build (a debugging aid, slower): every
+                           array access the generated kernels make -- vector groups and
+                           single elements, in single, batched, sharded and served
+                           launches -- is checked against the array's index range and
+                           its access width; the first violation is recorded and the
+                           access skipped.  Read it with pyc_map_check_bounds /
+                           pyc_reduce_check_bounds (scans: pyc_scan_sync).  Also
+                           selected for every handle by $PYC_DEBUG_BOUNDS=1.  Accesses
+                           a statement makes itself other than name[i] are not
+                           checked. */
 } pyc_opts;
 
 /* Static description of one declared argument (for prepared invocation). */
@@ -179,6 +189,19 @@ pyc_status pyc_map_launch(pyc_map_t h, int64_t n, void* const* ptrs, const void*
 pyc_status pyc_map_launch_host(pyc_map_t h, int64_t n, void* const* host_ptrs,
                                const void* scalars);
 
+/* For a handle created with opts.debug_bounds (the stand-in for a memory
+ * checker, Sec. 3.1's automatic error checking carried into the kernels):
+ * synchronise the current context, then read and clear the first out-of-range
+ * or misaligned access recorded by the handle's kernels in that context since
+ * the last call.  PYC_OK if there was none; PYC_E_INTERNAL naming the access
+ * (kind, index or address, the range's end, block, thread) otherwise; PYC_E_ARG
+ * for a handle built without the checks.  Test hook: $PYC_DEBUG_BOUNDS_SHRINK=k
+ * at creation narrows every checked range by k elements at its top, so that a
+ * test can make the checks fire without any access leaving its array (the
+ * accesses they reject are skipped). */
+pyc_status pyc_map_check_bounds(pyc_map_t h);
+pyc_status pyc_reduce_check_bounds(pyc_reduce_t h);
+
 /* Number of declared parameters and their descriptions. */
 int pyc_map_num_params(pyc_map_t h);
 pyc_status pyc_map_param(pyc_map_t h, int idx, pyc_param_info* info);
@@ -230,6 +253,50 @@ pyc_status pyc_reduce_create(pyc_dtype out_dtype, const char* neutral, const cha
  * (n, tuning), independent of timing.  Errors as for pyc_map_launch. */
 pyc_status pyc_reduce_launch(pyc_reduce_t h, int64_t n, void* const* ptrs, const void* scalars,
                              void* d_out, pyc_stream_t stream);
+
+/* Sharded map-reduce: a range [0, n_total) cut into contiguous shards that live
+ * on different devices (one process each), reduced with one exchange step.
+ * Sec. 3.2.5 defines the reduction by an associative reduce expression and its
+ * neutral element; together they make the reduction of the whole range equal
+ * to the reduce expression applied, in shard order, to the reductions of the
+ * shards (the paper itself runs on one device).
+ *
+ * pyc_reduce_shard folds shard [i0, i0 + n) into one accumulator record of
+ * PYC_RECORD_BYTES (16) bytes at d_rec (device, 8-byte aligned):
+ *   ptrs     one device pointer per array parameter, pointing at the shard's
+ *            first element (global element i0); every array holds the shard's
+ *            n elements.  The map expression sees the global index i in
+ *            [i0, i0 + n) and n_total as n, so it may use i as a value and an
+ *            ARGMIN / ARGMAX record carries the global index.  Every array must
+ *            be accessed only as name[i] (else PYC_E_ARG): a shard holds no
+ *            other elements.
+ *   record   the shard's accumulator before its conversion to the result type:
+ *            bytes [0, acc) hold the accumulation type (binary32 for F32, BF16
+ *            and F16 results, the result type otherwise, pyc_argf32 for
+ *            ARGMIN / ARGMAX), the rest are zero; for a compensated F32 handle,
+ *            two binary64 values (hi, lo) whose sum is the shard's sum.  An empty
+ *            shard (n == 0) gives the neutral element.
+ * The launch, its chunk plan and its workspace are those of pyc_reduce_launch
+ * for n elements; records on one stream are serialised by the stream.
+ *
+ * pyc_reduce_combine folds k >= 0 records (d_recs: k consecutive records in
+ * shard order, device, 8-byte aligned) with the handle's reduce expression --
+ * for a compensated handle, a binary64 (hi, lo) sum -- in record order and then
+ * a fixed tree, converts once to the result type and writes one result to d_out
+ * (device), as pyc_reduce_launch would.  k == 0 writes the neutral element.  One
+ * launch of one CTA.  Integer sums, min / max and argmin / argmax give the same
+ * bits as pyc_reduce_launch over the whole range; floating-point sums are
+ * within the same bounds (another association order).  The exchange of
+ * records between processes is the caller's, e.g. an all-gather of 16 bytes
+ * per shard.
+ * Errors: PYC_E_ARG (bad range, a non-elementwise array, NULL or misaligned
+ * pointers), PYC_E_CUDA. */
+#define PYC_RECORD_BYTES 16
+pyc_status pyc_reduce_shard(pyc_reduce_t h, int64_t n_total, int64_t i0, int64_t n,
+                            void* const* ptrs, const void* scalars, void* d_rec,
+                            pyc_stream_t stream);
+pyc_status pyc_reduce_combine(pyc_reduce_t h, int64_t k, const void* d_recs, void* d_out,
+                              pyc_stream_t stream);
 
 /* Segmented map-reduce: nseg independent reductions in one persistent launch.
  *   seg_offsets  HOST array of nseg+1 non-decreasing element offsets; segment s
@@ -626,6 +693,31 @@ void pyc_server_destroy(pyc_server_t s);
 #define PYC_REPLAY_DIRECT 1
 pyc_status pyc_server_replay(pyc_server_t s, int64_t nreq, const pyc_request* reqs,
                              const int64_t* arrival_ns, int mode, pyc_result* results);
+
+/* ------------------------------------------------------------------ fault injection */
+
+/* Test hook (the paper has no counterpart; it stands in for failures that tests
+ * cannot cause on a shared GPU): make the library's own host-side steps fail on
+ * purpose, so that its error paths run -- Sec. 3.1's rule that every failure
+ * surfaces as an error, never as a crash or a silent wrong result.
+ *   PYC_INJECT_ALLOC     the next `value` system allocations the library makes
+ *                        (device cuMemAlloc, page-locked cuMemAllocHost, host-pool
+ *                        blocks) fail as the driver does when memory runs out:
+ *                        callers see PYC_E_NOMEM (a pool first returns its
+ *                        retained blocks and retries once).
+ *   PYC_INJECT_COMPILE   the next `value` run-time compilations fail with
+ *                        PYC_E_COMPILE (cache hits do not compile).
+ *   PYC_INJECT_STALL_MS  the next serving-loop scheduler to wake sleeps `value` ms
+ *                        before admitting requests (a late scheduler: deadlines
+ *                        run out, PYC_E_TIMEOUT).
+ * value = 0 clears the kind.  Nothing is injected into the GPU.  Process-wide;
+ * not for production use.  Errors: PYC_E_ARG (unknown kind, value < 0). */
+typedef enum {
+  PYC_INJECT_ALLOC = 0,
+  PYC_INJECT_COMPILE = 1,
+  PYC_INJECT_STALL_MS = 2
+} pyc_inject_kind;
+pyc_status pyc_test_inject(pyc_inject_kind what, int64_t value);
 
 /* ------------------------------------------------------------------ cache */
 

@@ -1,6 +1,7 @@
 // C ABI: map and map-reduce creation and launches (see include/pyc.h).
 #include <algorithm>
 #include <cctype>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -124,6 +125,50 @@ ChunkPlan plan_chunks(int64_t n, int64_t head, int64_t tile, int resident) {
   return p;
 }
 
+bool bounds_requested(const pyc_opts& o) {
+  if (o.debug_bounds) return true;
+  const char* e = std::getenv("PYC_DEBUG_BOUNDS");
+  return e && e[0] == '1';
+}
+
+std::string bounds_defines() {
+  std::string d = "#define PYC_BOUNDS 1\n";
+  if (const char* k = std::getenv("PYC_DEBUG_BOUNDS_SHRINK")) {
+    long long v = std::atoll(k);
+    if (v > 0) d += "#define PYC_BOUNDS_SHRINK " + std::to_string(v) + "LL\n";
+  }
+  return d;
+}
+
+void check_bounds_record(HandleBase& h) {
+  if (!h.bounds) fail(PYC_E_ARG, "the handle is not a bounds-checked build (opts.debug_bounds)");
+  const Driver& d = drv();
+  ensure_context();
+  PYC_CU(d.cuCtxSynchronize());
+  size_t bytes = 0;
+  CUdeviceptr rec = h.mod->global("pyc_bounds_rec", &bytes);
+  if (bytes != 32) fail(PYC_E_INTERNAL, "unexpected size of the bounds record");
+  unsigned long long r[4] = {0, 0, 0, 0};
+  PYC_CU(d.cuMemcpyDtoH(r, rec, sizeof(r)));
+  if (r[0] == 0) return;
+  const unsigned long long z[4] = {0, 0, 0, 0};
+  PYC_CU(d.cuMemcpyHtoD(rec, z, sizeof(z)));
+  static const char* what[] = {"?", "vector load", "vector store", "element load",
+                               "element store", "vector access"};
+  const unsigned code = r[0] < 6 ? (unsigned)r[0] : 0u;
+  std::string m = "bounds check: ";
+  m += what[code];
+  if (code == 5)
+    m += " at address " + std::to_string(r[1]) + " not aligned to " + std::to_string(r[2]) +
+         " bytes";
+  else
+    m += " at index " + std::to_string((long long)r[1]) + " outside the array's range (end " +
+         std::to_string((long long)r[2]) + ")";
+  m += " in " + h.tag + ", block " + std::to_string(r[3] >> 16) + ", thread " +
+       std::to_string(r[3] & 0xffff);
+  fail(PYC_E_INTERNAL, m);
+}
+
 namespace {
 
 void check_cfg(const LaunchCfg& c) {
@@ -152,6 +197,8 @@ void check_opts(const pyc_opts& o) {
 }
 
 void finish_handle(HandleBase& h, bool reduce) {
+  h.bounds = bounds_requested(h.opts);
+  if (h.bounds) h.source = bounds_defines() + h.source;
   h.min_bytes = lifted_min_bytes(h.spec);
   h.mod = get_module(h.source, h.opts.fmad != 0);
   h.tune_key = digest(h.source + (h.opts.fmad ? "|fmad" : ""));
@@ -195,9 +242,7 @@ void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
                               nullptr));
 }
 
-namespace {
-
-pyc_reduce::Workspace& workspace(pyc_reduce* h, CUstream stream) {
+pyc_reduce::Workspace& reduce_workspace(pyc_reduce* h, CUstream stream) {
   CUcontext ctx = ensure_context();
   std::lock_guard<std::mutex> lk(h->ws_mu);
   auto key = std::make_pair(ctx, stream);
@@ -213,8 +258,6 @@ pyc_reduce::Workspace& workspace(pyc_reduce* h, CUstream stream) {
   return h->ws.emplace(key, w).first->second;
 }
 
-}  // namespace
-
 void launch_reduce(pyc_reduce* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
                    const void* scalars, void* d_out, CUstream stream) {
   check_cfg(cfg);
@@ -228,7 +271,7 @@ void launch_reduce(pyc_reduce* h, const LaunchCfg& cfg, int64_t n, void* const* 
   int resident = resident_ctas(f, cfg.block);
   int64_t tile = (int64_t)cfg.block * (cfg.v.vec_bytes / h->min_bytes) * cfg.v.unroll;
   ChunkPlan cp = plan_chunks(n, head, tile, resident);
-  pyc_reduce::Workspace& w = workspace(h, stream);
+  pyc_reduce::Workspace& w = reduce_workspace(h, stream);
   void* params[] = {args.data(), &n, &cp.head, &cp.chunk, &cp.nchunks, &w.part, &w.ticket, &d_out};
   PYC_CU(drv().cuLaunchKernel(f, (unsigned)cp.grid, 1, 1, (unsigned)cfg.block, 1, 1, 0, stream,
                               params, nullptr));
@@ -270,6 +313,20 @@ PYC_API pyc_status pyc_map_launch(pyc_map_t h, int64_t n, void* const* ptrs, con
     if (!h) fail(PYC_E_ARG, "handle is NULL");
     LaunchCfg cfg = choose_cfg(*h, n, false);
     launch_map(h, cfg, n, ptrs, scalars, reinterpret_cast<CUstream>(stream));
+  });
+}
+
+PYC_API pyc_status pyc_map_check_bounds(pyc_map_t h) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    check_bounds_record(*h);
+  });
+}
+
+PYC_API pyc_status pyc_reduce_check_bounds(pyc_reduce_t h) {
+  return guarded([&] {
+    if (!h) fail(PYC_E_ARG, "handle is NULL");
+    check_bounds_record(*h);
   });
 }
 

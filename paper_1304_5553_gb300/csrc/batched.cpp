@@ -52,9 +52,6 @@ struct BatchPlan {
   }
 };
 
-namespace {
-
-// One private non-blocking stream per context, used only for graph capture.
 CUstream capture_stream() {
   static std::mutex mu;
   static std::map<CUcontext, CUstream> streams;
@@ -67,6 +64,8 @@ CUstream capture_stream() {
   streams[ctx] = s;
   return s;
 }
+
+namespace {
 
 std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t* off,
                                       void* const* ptrs, const void* scalars, void* d_out,

@@ -277,6 +277,49 @@ __device__ __forceinline__ void pyc_two_sum_d(const double a, const double b, do
   const double bp = s - a;
   e = (a - (s - bp)) + (b - bp);
 }
+// Bounds-checked build (PYC_BOUNDS defined by opts.debug_bounds): every access
+// the generated code makes to an array -- a vector group [idx, idx + cnt) or one
+// element -- is checked against the array's index range [lo, hi), and a vector
+// group's address against its access width; the first violation in the module
+// is recorded in pyc_bounds_rec (code, index, bound, block << 16 | thread) and
+// the access is skipped.  PYC_BOUNDS_SHRINK (a test hook) narrows every range
+// by that many elements at its top.  Without PYC_BOUNDS the checks are absent.
+#ifdef PYC_BOUNDS
+#ifndef PYC_BOUNDS_SHRINK
+#define PYC_BOUNDS_SHRINK 0
+#endif
+__device__ unsigned long long pyc_bounds_rec[4];
+__device__ __noinline__ bool pyc_bounds_fail(const long long idx, const long long bound,
+                                             const int code) {
+  if (atomicCAS(&pyc_bounds_rec[0], 0ull, (unsigned long long)code) == 0ull) {
+    pyc_bounds_rec[1] = (unsigned long long)idx;
+    pyc_bounds_rec[2] = (unsigned long long)bound;
+    pyc_bounds_rec[3] = ((unsigned long long)blockIdx.x << 16) | threadIdx.x;
+  }
+  return false;
+}
+#define PYC_IN(idx, cnt, lo, hi, code)                                                \
+  (((long long)(idx) >= (long long)(lo) &&                                              \
+    (long long)(idx) + (long long)(cnt) <= (long long)(hi) - PYC_BOUNDS_SHRINK) ||       \
+   pyc_bounds_fail((long long)(idx), (long long)(hi), (code)))
+#define PYC_ALIGNED(ptr, width, code)                                                  \
+  ((unsigned long long)(ptr) % (unsigned long long)(width) == 0ull ||                   \
+   pyc_bounds_fail((long long)(unsigned long long)(ptr), (long long)(width), (code)))
+#else
+#define PYC_IN(idx, cnt, lo, hi, code) true
+#define PYC_ALIGNED(ptr, width, code) true
+#endif
+
+// Arrival at a ticket shared by the CTAs of one launch (or one segment): an add
+// with release-acquire semantics at GPU scope.  The partials the arriving thread
+// stored before it are visible to whichever thread sees the last arrival, and
+// that thread sees every earlier arrival's partials; a CTA barrier then hands
+// the outcome (and that visibility) to the rest of its CTA.
+__device__ __forceinline__ unsigned pyc_ticket_arrive(unsigned* t) {
+  unsigned prev;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(t) : "memory");
+  return prev;
+}
 // ------------------------------------------------------------ end of prelude
 )PYC";
 
@@ -352,11 +395,13 @@ std::string group_io(const ArgSpec& spec, bool load) {
     if (!(p.is_ptr && p.lifted)) continue;
     if (load ? !p.read : !p.written) continue;
     int b = type_info(p.dtype).bytes;
+    o << "        if (PYC_IN(pyc_e0, E, pyc_lo, pyc_hi, " << (load ? 1 : 2) << ") && PYC_ALIGNED("
+      << p.name << " + pyc_e0, VB, 5)) ";
     if (load)
-      o << "        pyc_ldg<E * " << b << ", VB>(&pyc_r_" << p.name << "[pyc_u * E], " << p.name
+      o << "pyc_ldg<E * " << b << ", VB>(&pyc_r_" << p.name << "[pyc_u * E], " << p.name
         << " + pyc_e0);\n";
     else
-      o << "        pyc_stg<E * " << b << ", VB>(" << p.name << " + pyc_e0, &pyc_r_" << p.name
+      o << "pyc_stg<E * " << b << ", VB>(" << p.name << " + pyc_e0, &pyc_r_" << p.name
         << "[pyc_u * E]);\n";
   }
   return o.str();
@@ -379,8 +424,9 @@ std::string buf_load(const ArgSpec& spec, const char* prefix, const std::string&
     << "      const pyc_i64 pyc_e0 = (" << base << ") + (pyc_i64)pyc_u * pyc_step;\n";
   for (auto& p : spec.params)
     if (p.is_ptr && p.lifted && p.read)
-      o << "      pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&" << prefix << p.name
-        << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
+      o << "      if (PYC_IN(pyc_e0, E, pyc_lo, pyc_hi, 1) && PYC_ALIGNED(" << p.name
+        << " + pyc_e0, VB, 5)) pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&" << prefix
+        << p.name << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
   o << "    }\n";
   return o.str();
 }
@@ -396,8 +442,9 @@ std::string buf_load_used(const ArgSpec& spec, const char* prefix, const std::st
     if (code.find("pyc_r_" + p.name + " ") == std::string::npos &&
         code.find("pyc_r_" + p.name + "[") == std::string::npos)
       continue;
-    o << "      pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&" << prefix << p.name
-      << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
+    o << "      if (PYC_IN(pyc_e0, E, pyc_lo, pyc_hi, 1) && PYC_ALIGNED(" << p.name
+      << " + pyc_e0, VB, 5)) pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&" << prefix
+      << p.name << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
   }
   o << "    }\n";
   return o.str();
@@ -462,8 +509,9 @@ std::string group_loads_used(const ArgSpec& spec, const std::string& code) {
     if (code.find("pyc_r_" + p.name + " ") == std::string::npos &&
         code.find("pyc_r_" + p.name + "[") == std::string::npos)
       continue;
-    o << "        pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&pyc_r_" << p.name
-      << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
+    o << "        if (PYC_IN(pyc_e0, E, pyc_lo, pyc_hi, 1) && PYC_ALIGNED(" << p.name
+      << " + pyc_e0, VB, 5)) pyc_ldg<E * " << type_info(p.dtype).bytes << ", VB>(&pyc_r_"
+      << p.name << "[pyc_u * E], " << p.name << " + pyc_e0);\n";
   }
   return o.str();
 }
@@ -532,8 +580,12 @@ std::string scalar_io(const ArgSpec& spec, bool load) {
   std::ostringstream o;
   for (auto& p : spec.params) {
     if (!(p.is_ptr && p.lifted)) continue;
-    if (load && p.read) o << "      pyc_r_" << p.name << "[0] = " << p.name << "[i];\n";
-    if (!load && p.written) o << "      " << p.name << "[i] = pyc_r_" << p.name << "[0];\n";
+    if (load && p.read)
+      o << "      if (PYC_IN(i, 1, pyc_lo, pyc_hi, 3)) pyc_r_" << p.name << "[0] = " << p.name
+        << "[i];\n";
+    if (!load && p.written)
+      o << "      if (PYC_IN(i, 1, pyc_lo, pyc_hi, 4)) " << p.name << "[i] = pyc_r_" << p.name
+        << "[0];\n";
   }
   return o.str();
 }
@@ -557,7 +609,10 @@ __device__ __forceinline__ void pyc_map_body(const pyc_args& pyc_p, const pyc_i6
   constexpr int T = E * U;               // elements per thread per tile
 )PYC";
   o << aliases(spec, "pyc_p");
-  o << R"PYC(  const pyc_i64 pyc_step = (pyc_i64)blockDim.x * E;
+  o << R"PYC(  const pyc_i64 pyc_lo = 0, pyc_hi = n;  // every array holds n elements
+  (void)pyc_lo;
+  (void)pyc_hi;
+  const pyc_i64 pyc_step = (pyc_i64)blockDim.x * E;
   const pyc_i64 pyc_tile = pyc_step * U;
   // aligned body [h, h + nfull * tile) in whole tiles; head [0, h) and tail scalar
   const pyc_i64 pyc_h = pyc_head < 0 ? 0 : (pyc_head < n ? pyc_head : n);
@@ -609,6 +664,9 @@ __device__ __forceinline__ void pyc_map_span(const pyc_args& pyc_p, const pyc_i6
 )PYC";
   o << aliases(spec, "pyc_p");
   o << R"PYC(  (void)n;
+  const pyc_i64 pyc_lo = 0, pyc_hi = n;  // every array of the task holds n elements
+  (void)pyc_lo;
+  (void)pyc_hi;
   const pyc_i64 pyc_step = (pyc_i64)pyc_nthr * E;
   const pyc_i64 pyc_tile = pyc_step * U;
   const pyc_i64 pyc_nt = pyc_ve > pyc_vs ? (pyc_ve - pyc_vs) / pyc_tile : 0;
@@ -836,11 +894,12 @@ struct pyc_combine_op {
 
 // Fold [vs, ve) (vs aligned to VB for every lifted array) with vector groups,
 // plus the scalar range [ss, se), by a group of `nthr` threads (a CTA or a
-// warp); returns this thread's accumulator.
+// warp); returns this thread's accumulator.  [lo, hi) is the index range the
+// arrays hold (for the bounds-checked build).
 template <int VB, int U>
 __device__ __forceinline__ pyc_acc_t pyc_reduce_span(const pyc_args& pyc_p, const pyc_i64 n,
     const pyc_i64 pyc_vs, const pyc_i64 pyc_ve, const pyc_i64 pyc_ss, const pyc_i64 pyc_se,
-    const int pyc_tid, const int pyc_nthr) {
+    const int pyc_tid, const int pyc_nthr, const pyc_i64 pyc_lo, const pyc_i64 pyc_hi) {
   constexpr int E = VB / PYC_MIN_BYTES;
   constexpr int T = E * U;
   // independent accumulators: element position k folds into acc[k % A]
@@ -849,6 +908,8 @@ __device__ __forceinline__ pyc_acc_t pyc_reduce_span(const pyc_args& pyc_p, cons
 )PYC";
   o << aliases(spec, "pyc_p");
   o << R"PYC(  (void)n;
+  (void)pyc_lo;
+  (void)pyc_hi;
   pyc_acc_t pyc_acc[A];
 #pragma unroll
   for (int k = 0; k < A; ++k) pyc_acc[k] = pyc_neutral();
@@ -905,11 +966,11 @@ __device__ __forceinline__ pyc_acc_t pyc_chunk(const pyc_args& pyc_p, const pyc_
   if (head >= 0) {
     const pyc_i64 vs = head + c * chunk;
     const pyc_i64 ve = vs + chunk < n ? vs + chunk : n;
-    return pyc_reduce_span<VB, U>(pyc_p, n, vs, ve, 0, c == 0 ? head : 0, tid, nthr);
+    return pyc_reduce_span<VB, U>(pyc_p, n, vs, ve, 0, c == 0 ? head : 0, tid, nthr, 0, n);
   }
   const pyc_i64 ss = c * chunk;
   const pyc_i64 se = ss + chunk < n ? ss + chunk : n;
-  return pyc_reduce_span<VB, U>(pyc_p, n, 0, 0, ss, se, tid, nthr);
+  return pyc_reduce_span<VB, U>(pyc_p, n, 0, 0, ss, se, tid, nthr, 0, n);
 }
 
 )PYC";
@@ -948,6 +1009,65 @@ __device__ __forceinline__ pyc_out_t pyc_combine_partials(const pyc_acc_t* part,
 }
 )PYC";
   }
+  // accumulator record of a shard (sharded reductions): 16 bytes
+  if (kind == ReduceKind::Compensated) {
+    o << R"PYC(// Record of a shard: the binary64 pair (hi, lo) whose sum is the shard's sum.
+struct pyc_record { double hi; double lo; };
+__device__ __forceinline__ pyc_record pyc_record_partials(const pyc_acc_t* part, const int count) {
+  pyc_dd acc; acc.hi = 0.0; acc.lo = 0.0;
+  pyc_dd_op op;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    const pyc_acc_t p = pyc_ld_cg(part + j);
+    pyc_dd t; t.hi = (double)p.s; t.lo = (double)p.c;
+    acc = op(acc, t);
+  }
+  pyc_dd z; z.hi = 0.0; z.lo = 0.0;
+  acc = pyc_block_reduce(acc, op, z);
+  pyc_record r; r.hi = acc.hi; r.lo = acc.lo;
+  return r;
+}
+// Combine of k records in record order (then a fixed tree); one rounding.
+__device__ __forceinline__ pyc_out_t pyc_combine_records(const pyc_record* rec, const pyc_i64 k) {
+  pyc_dd acc; acc.hi = 0.0; acc.lo = 0.0;
+  pyc_dd_op op;
+  for (pyc_i64 j = threadIdx.x; j < k; j += blockDim.x) {
+    pyc_dd t; t.hi = rec[j].hi; t.lo = rec[j].lo;
+    acc = op(acc, t);
+  }
+  pyc_dd z; z.hi = 0.0; z.lo = 0.0;
+  acc = pyc_block_reduce(acc, op, z);
+  return __double2float_rn(acc.hi + acc.lo);
+}
+)PYC";
+  } else {
+    if (g.acc_bytes == 16)
+      o << "// Record of a shard: its accumulator, before conversion to the result type.\n"
+           "struct pyc_record { pyc_acc_t acc; };\n";
+    else
+      o << "// Record of a shard: its accumulator, before conversion to the result type.\n"
+           "struct pyc_record { pyc_acc_t acc; unsigned char pad[16 - sizeof(pyc_acc_t)]; };\n";
+    o << R"PYC(__device__ __forceinline__ pyc_record pyc_record_partials(const pyc_acc_t* part, const int count) {
+  pyc_acc_t acc = pyc_neutral();
+  for (int j = threadIdx.x; j < count; j += blockDim.x) acc = pyc_combine(acc, pyc_ld_cg(part + j));
+  acc = pyc_block_reduce(acc, pyc_combine_op(), pyc_neutral());
+  pyc_record r;
+  unsigned char* b = reinterpret_cast<unsigned char*>(&r);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) b[j] = 0;
+  r.acc = acc;
+  return r;
+}
+// Combine of k records with the reduce expression in record order (then a
+// fixed tree), converted to the result type once.
+__device__ __forceinline__ pyc_out_t pyc_combine_records(const pyc_record* rec, const pyc_i64 k) {
+  pyc_acc_t acc = pyc_neutral();
+  for (pyc_i64 j = threadIdx.x; j < k; j += blockDim.x) acc = pyc_combine(acc, rec[j].acc);
+  acc = pyc_block_reduce(acc, pyc_combine_op(), pyc_neutral());
+  return pyc_finalize(acc);
+}
+)PYC";
+  }
+  o << "static_assert(sizeof(pyc_record) == 16, \"record size\");\n";
   o << R"PYC(
 // Single reduction: CTAs take chunks c = blockIdx.x, blockIdx.x + gridDim.x, ...;
 // the last CTA to arrive combines the partials and resets the ticket.
@@ -961,15 +1081,56 @@ __device__ __forceinline__ void pyc_reduce_body(const pyc_args& pyc_p, const pyc
     v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
     if (threadIdx.x == 0) part[c] = v;
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) pyc_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+  // thread 0 stored every partial of this CTA; its arrival publishes them
+  if (threadIdx.x == 0) pyc_last = pyc_ticket_arrive(ticket) == gridDim.x - 1 ? 1u : 0u;
   __syncthreads();
   if (!pyc_last) return;
-  __threadfence();
   const pyc_out_t r = pyc_combine_partials(part, (int)nchunks);
   if (threadIdx.x == 0) {
     *out = r;
+    *ticket = 0u;
+  }
+}
+
+// Sharded reduction: one shard [base, base + len) of a range of length n that
+// is partitioned across devices.  The argument struct's array pointers are
+// offset by -base elements, so element i of the shard's arrays is addressed as
+// name[i] with the global index i, which the map expression (and an argmin's
+// index) sees; chunk c starts at base + head + c * chunk.  The last CTA
+// combines the partials into the shard's record instead of the result.
+template <int VB, int U>
+__device__ __forceinline__ pyc_acc_t pyc_chunk_at(const pyc_args& pyc_p, const pyc_i64 n,
+    const pyc_i64 base, const pyc_i64 len, const pyc_i64 head, const pyc_i64 chunk,
+    const pyc_i64 c, const int tid, const int nthr) {
+  const pyc_i64 end = base + len;
+  if (head >= 0) {
+    const pyc_i64 vs = base + head + c * chunk;
+    const pyc_i64 ve = vs + chunk < end ? vs + chunk : end;
+    return pyc_reduce_span<VB, U>(pyc_p, n, vs, ve, base, c == 0 ? base + head : base, tid, nthr,
+                                  base, end);
+  }
+  const pyc_i64 ss = base + c * chunk;
+  const pyc_i64 se = ss + chunk < end ? ss + chunk : end;
+  return pyc_reduce_span<VB, U>(pyc_p, n, 0, 0, ss, se, tid, nthr, base, end);
+}
+template <int VB, int U>
+__device__ __forceinline__ void pyc_shard_body(const pyc_args& pyc_p, const pyc_i64 n,
+    const pyc_i64 base, const pyc_i64 len, const pyc_i64 head, const pyc_i64 chunk,
+    const pyc_i64 nchunks, pyc_acc_t* __restrict__ part, unsigned* __restrict__ ticket,
+    pyc_record* __restrict__ rec) {
+  __shared__ unsigned pyc_last;
+  for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    pyc_acc_t v = pyc_chunk_at<VB, U>(pyc_p, n, base, len, head, chunk, c, threadIdx.x, blockDim.x);
+    v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
+    if (threadIdx.x == 0) part[c] = v;
+  }
+  // thread 0 stored every partial of this CTA; its arrival publishes them
+  if (threadIdx.x == 0) pyc_last = pyc_ticket_arrive(ticket) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!pyc_last) return;
+  const pyc_record r = pyc_record_partials(part, (int)nchunks);
+  if (threadIdx.x == 0) {
+    *rec = r;
     *ticket = 0u;
   }
 }
@@ -1060,12 +1221,23 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
          "const pyc_i64 nchunks, pyc_acc_t* part, unsigned* ticket, pyc_out_t* out) {\n"
       << "  pyc_reduce_body<" << v.vec_bytes << ", " << v.unroll
       << ">(pyc_p, n, head, chunk, nchunks, part, ticket, out);\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rshard_" << tag << "_" << sfx
+      << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 base, const pyc_i64 len, "
+         "const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 nchunks, pyc_acc_t* part, "
+         "unsigned* ticket, pyc_record* rec) {\n"
+      << "  pyc_shard_body<" << v.vec_bytes << ", " << v.unroll
+      << ">(pyc_p, n, base, len, head, chunk, nchunks, part, ticket, rec);\n}\n";
     o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rbatch_" << tag << "_" << sfx
       << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
          "unsigned* tickets, unsigned* ctl) {\n"
       << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll
       << ">(tasks, items, nitems, part, tickets, ctl);\n}\n";
   }
+  if (emit_kernels)
+    o << "extern \"C\" __global__ void __launch_bounds__(" << kCombineBlock << ") pyc_rcomb_" << tag
+      << "(const pyc_record* rec, const pyc_i64 k, pyc_out_t* out) {\n"
+         "  const pyc_out_t r = pyc_combine_records(rec, k);\n"
+         "  if (threadIdx.x == 0) *out = r;\n}\n";
   g.source = o.str();
   return g;
 }

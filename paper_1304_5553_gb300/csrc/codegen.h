@@ -38,6 +38,11 @@ MapGen generate_map(const ArgSpec& spec, const std::string& stmt_rewritten,
 
 enum class ReduceKind { Plain, Arg, Compensated };
 
+// Threads of the one CTA that combines the records of a sharded reduction.
+constexpr int kCombineBlock = 256;
+// Bytes of one shard record (the accumulator before the final conversion).
+constexpr int kRecordBytes = 16;
+
 struct ReduceGen {
   std::string source;
   int acc_bytes = 0;

@@ -1,11 +1,28 @@
-// Thread-local error text and element-type tables.
+// Thread-local error text, element-type tables and the injected-failure
+// counters of pyc_test_inject.
 #include "common.h"
+
+#include <atomic>
 
 namespace pyc {
 
 namespace {
 thread_local std::string t_last_error;
+std::atomic<int64_t> g_inject[3];  // pending failures by pyc_inject_kind
+
+int64_t take_one(std::atomic<int64_t>& c, bool all) {
+  int64_t v = c.load();
+  while (v > 0)
+    if (c.compare_exchange_weak(v, all ? 0 : v - 1)) return all ? v : 1;
+  return 0;
 }
+}  // namespace
+
+bool take_injected(pyc_inject_kind k) {
+  return (int)k >= 0 && (int)k < 2 && take_one(g_inject[(int)k], false) > 0;
+}
+
+int64_t take_injected_stall_ms() { return take_one(g_inject[PYC_INJECT_STALL_MS], true); }
 
 void set_last_error(const std::string& m) { t_last_error = m; }
 void clear_last_error() { t_last_error.clear(); }
@@ -42,3 +59,11 @@ bool is_float_type(pyc_dtype t) {
 PYC_API const char* pyc_last_error(void) { return pyc::t_last_error.c_str(); }
 
 PYC_API const char* pyc_version(void) { return "pyc 0.1 (sm_103a)"; }
+
+PYC_API pyc_status pyc_test_inject(pyc_inject_kind what, int64_t value) {
+  return pyc::guarded([&] {
+    if ((int)what < 0 || (int)what > 2) pyc::fail(PYC_E_ARG, "unknown injection kind");
+    if (value < 0) pyc::fail(PYC_E_ARG, "value must be >= 0");
+    pyc::g_inject[(int)what].store(value);
+  });
+}

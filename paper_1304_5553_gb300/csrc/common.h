@@ -52,4 +52,10 @@ struct TypeInfo {
 const TypeInfo& type_info(pyc_dtype t);
 bool is_float_type(pyc_dtype t);
 
+// Failures injected by pyc_test_inject (host side only): take_injected
+// consumes one pending failure of the kind and says whether there was one;
+// take_injected_stall_ms consumes the pending scheduler stall (0 if none).
+bool take_injected(pyc_inject_kind k);
+int64_t take_injected_stall_ms();
+
 }  // namespace pyc

@@ -27,6 +27,22 @@ std::once_flag g_once;
 #define PYC_XSTR(x) PYC_STR(x)
 #define PYC_STR(x) #x
 
+// The driver's allocation entry points, called through these wrappers so that
+// pyc_test_inject can make the next allocations fail as the driver does when
+// memory runs out.
+decltype(&::cuMemAlloc) g_real_mem_alloc = nullptr;
+decltype(&::cuMemAllocHost) g_real_mem_alloc_host = nullptr;
+
+CUresult CUDAAPI mem_alloc_or_injected(CUdeviceptr* p, size_t bytes) {
+  if (take_injected(PYC_INJECT_ALLOC)) return CUDA_ERROR_OUT_OF_MEMORY;
+  return g_real_mem_alloc(p, bytes);
+}
+
+CUresult CUDAAPI mem_alloc_host_or_injected(void** p, size_t bytes) {
+  if (take_injected(PYC_INJECT_ALLOC)) return CUDA_ERROR_OUT_OF_MEMORY;
+  return g_real_mem_alloc_host(p, bytes);
+}
+
 void load_driver() {
   void* h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_GLOBAL);
   if (!h) h = dlopen("libcuda.so", RTLD_NOW | RTLD_GLOBAL);
@@ -47,6 +63,10 @@ void load_driver() {
     g_load_error = "CUDA driver lacks entry points: " + missing;
     return;
   }
+  g_real_mem_alloc = d.cuMemAlloc;
+  g_real_mem_alloc_host = d.cuMemAllocHost;
+  d.cuMemAlloc = &mem_alloc_or_injected;
+  d.cuMemAllocHost = &mem_alloc_host_or_injected;
   CUresult r = d.cuInit(0);
   if (r != CUDA_SUCCESS) {
     const char* s = nullptr;

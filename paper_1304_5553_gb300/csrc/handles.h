@@ -49,6 +49,7 @@ struct HandleBase {
   std::string tune_key;  // digest of the source: key of the persistent tuning cache
   std::vector<std::string> param_names;  // stable storage for pyc_param_info.name
   std::string tag;                       // kernel-name tag of this spec
+  bool bounds = false;                   // bounds-checked build (opts.debug_bounds)
   // Kernel function name, e.g. kname("pyc_map", v) = "pyc_map_<tag>_v16_u4".
   std::string kname(const char* kind, const Variant& v) const {
     return std::string(kind) + "_" + tag + "_" + variant_suffix(v);
@@ -93,6 +94,15 @@ struct pyc_reduce : pyc::HandleBase {
 
 namespace pyc {
 
+// Bounds-checked builds: whether opts (or $PYC_DEBUG_BOUNDS=1) ask for one, and
+// the defines placed before the generated source of such a build.
+bool bounds_requested(const pyc_opts& o);
+std::string bounds_defines();
+// Synchronise the context, then read and clear the first recorded violation of
+// a checked handle's module in the current context: returns normally if there
+// was none, else fails with PYC_E_INTERNAL describing it.
+void check_bounds_record(HandleBase& h);
+
 // Maximum number of chunks of one reduction (bounds the partial workspace).
 constexpr int64_t kMaxChunks = 4096;
 
@@ -122,6 +132,10 @@ struct ChunkPlan {
 };
 ChunkPlan plan_chunks(int64_t n, int64_t head, int64_t tile, int resident);
 
+// The handle's workspace (partials + ticket) for the current context and
+// `stream`, allocated and zeroed by its first use.
+pyc_reduce::Workspace& reduce_workspace(pyc_reduce* h, CUstream stream);
+
 // Enqueue one reduction (used by pyc_reduce_launch and the tuner).
 void launch_reduce(pyc_reduce* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
                    const void* scalars, void* d_out, CUstream stream);
@@ -131,10 +145,17 @@ void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
 
 // Times every (variant, block) candidate of a handle with `launch_one` on
 // scratch buffers for n's size bucket and keeps the fastest (tune.cpp).
+// launch_one(cfg, n, ptrs, scalars, out, stream) enqueues one launch on stream.
+// With graph_timing, kernels shorter than ~40 us are timed as replays of a CUDA
+// graph of 20 launches (on the context's private capture stream), so that the
+// host's per-launch latency is not part of the sample.
 using TuneLaunch = std::function<void(const LaunchCfg&, int64_t, void* const*, const void*,
-                                      CUdeviceptr)>;
+                                      CUdeviceptr, CUstream)>;
 void autotune_generic(HandleBase& h, int64_t n, CUstream stream, bool reduce,
-                      const TuneLaunch& launch_one);
+                      const TuneLaunch& launch_one, bool graph_timing = false);
+
+// One private non-blocking stream per context, used for graph capture.
+CUstream capture_stream();
 
 // Persistent tuning cache (JSON lines in the kernel cache directory).
 void tune_cache_load(HandleBase& h, bool reduce);

@@ -146,6 +146,8 @@ bool unpack_record(const std::string& r, const std::string& key_text, std::strin
 }
 
 std::string compile_nvrtc(const std::string& source, bool fmad) {
+  if (take_injected(PYC_INJECT_COMPILE))
+    fail(PYC_E_COMPILE, "compilation failed: injected by pyc_test_inject (no compiler log)");
   const Nvrtc& nv = nvrtc();
   nvrtcProgram prog;
   nvrtcResult r = nv.create(&prog, source.c_str(), "pyc_kernel.cu", 0, nullptr, nullptr);
@@ -305,6 +307,24 @@ Module::~Module() {
     } catch (...) {
     }
   }
+}
+
+CUdeviceptr Module::global(const std::string& name, size_t* bytes) {
+  CUcontext ctx = ensure_context();
+  std::lock_guard<std::mutex> lk(mu_);
+  auto it = loaded_.find(ctx);
+  CUmodule mod;
+  if (it == loaded_.end()) {
+    PYC_CU(drv().cuModuleLoadData(&mod, cubin_.data()));
+    loaded_[ctx] = mod;
+  } else {
+    mod = it->second;
+  }
+  CUdeviceptr p = 0;
+  size_t b = 0;
+  PYC_CU(drv().cuModuleGetGlobal(&p, &b, mod, name.c_str()));
+  if (bytes) *bytes = b;
+  return p;
 }
 
 CUfunction Module::function(const std::string& name) {

@@ -21,6 +21,9 @@ class Module {
   ~Module();
   // Function `name` in the current context (loads the module on first use).
   CUfunction function(const std::string& name);
+  // Device address and size of the module-scope variable `name` in the current
+  // context (loads the module on first use).
+  CUdeviceptr global(const std::string& name, size_t* bytes);
   const std::string& cubin() const { return cubin_; }
 
  private:

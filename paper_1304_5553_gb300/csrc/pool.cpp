@@ -54,6 +54,10 @@ bool uses_cuda(const pyc_pool* p) { return p->kind != PYC_POOL_HOST; }
 void* system_alloc(pyc_pool* p, int64_t bytes, bool* oom) {
   *oom = false;
   if (p->kind == PYC_POOL_HOST) {
+    if (take_injected(PYC_INJECT_ALLOC)) {  // (device kinds: in the driver wrapper)
+      *oom = true;
+      return nullptr;
+    }
     void* q = std::aligned_alloc(256, (size_t)((bytes + 255) / 256 * 256));
     *oom = q == nullptr;
     return q;

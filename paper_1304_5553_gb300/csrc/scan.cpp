@@ -172,9 +172,12 @@ PYC_API pyc_status pyc_scan_create(pyc_dtype dtype, const char* neutral, const c
       fail(PYC_E_ARG, "opts.items_per_thread must be 0, 1, 2 or 4");
     h->preamble = h->opts.preamble ? h->opts.preamble : "";
     h->opts.preamble = nullptr;
-    // PYC_CHECK_BOUNDS=1: build the bounds-checked kernel (debugging aid)
+    // opts.debug_bounds, PYC_DEBUG_BOUNDS=1 or PYC_CHECK_BOUNDS=1: the scan's own
+    // bounds-checked build (debugging aid)
+    bool checked = bounds_requested(h->opts);
     if (const char* c = std::getenv("PYC_CHECK_BOUNDS"))
-      if (c[0] == '1') h->preamble = "#define PYC_CHECK 1\n" + h->preamble;
+      if (c[0] == '1') checked = true;
+    if (checked) h->preamble = "#define PYC_CHECK 1\n" + h->preamble;
     h->dtype = dtype;
     h->name = "scan";
     h->spec = parse_argspec(argspec);
@@ -241,7 +244,7 @@ PYC_API pyc_status pyc_scan_autotune(pyc_scan_t h, int64_t n, pyc_stream_t strea
     CUstream s = reinterpret_cast<CUstream>(stream);
     autotune_generic(*h, n, s, true,
                      [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc,
-                         CUdeviceptr) { launch_scan(h, c, nt, p, sc, s); });
+                         CUdeviceptr, CUstream) { launch_scan(h, c, nt, p, sc, s); });
   });
 }
 

@@ -341,6 +341,12 @@ void scheduler(pyc_server* s) {
     }
     notify();
     if (s->stop && s->queue.empty() && s->admitted.empty() && s->inflight.empty()) break;
+    // an injected stall (pyc_test_inject): the scheduler is late to admit
+    if (const int64_t ms = take_injected_stall_ms()) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::milliseconds(ms));
+      lk.lock();
+    }
     // 2. admission in arrival order
     const int64_t t = now_ns();
     while (!s->queue.empty() && !s->stop) {

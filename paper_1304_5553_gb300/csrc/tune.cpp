@@ -85,8 +85,58 @@ double time_us(Launch&& launch, CUstream s, int reps) {
   return best;
 }
 
+// Device time of one launch, from replays of a CUDA graph of `reps` launches
+// captured on the context's private stream (best of 3 replays).  The first
+// launch runs outside the capture, so per-stream set-up (a reduction's
+// workspace) is done before it.
+template <class Launch>
+double time_graph_us(Launch&& launch, int reps) {
+  const Driver& d = drv();
+  CUstream cs = capture_stream();
+  launch(cs);
+  PYC_CU(d.cuStreamSynchronize(cs));
+  struct Res {
+    CUgraph g = nullptr;
+    CUgraphExec ge = nullptr;
+    CUevent e0 = nullptr, e1 = nullptr;
+    ~Res() {
+      const Driver& d = drv();
+      if (ge) d.cuGraphExecDestroy(ge);
+      if (g) d.cuGraphDestroy(g);
+      if (e0) d.cuEventDestroy(e0);
+      if (e1) d.cuEventDestroy(e1);
+    }
+  } r;
+  PYC_CU(d.cuStreamBeginCapture(cs, CU_STREAM_CAPTURE_MODE_THREAD_LOCAL));
+  try {
+    for (int k = 0; k < reps; ++k) launch(cs);
+  } catch (...) {
+    CUgraph t = nullptr;
+    d.cuStreamEndCapture(cs, &t);
+    if (t) d.cuGraphDestroy(t);
+    throw;
+  }
+  PYC_CU(d.cuStreamEndCapture(cs, &r.g));
+  PYC_CU(d.cuGraphInstantiateWithFlags(&r.ge, r.g, 0));
+  PYC_CU(d.cuEventCreate(&r.e0, CU_EVENT_DEFAULT));
+  PYC_CU(d.cuEventCreate(&r.e1, CU_EVENT_DEFAULT));
+  PYC_CU(d.cuGraphLaunch(r.ge, cs));
+  double best = 1e30;
+  for (int k = 0; k < 3; ++k) {
+    PYC_CU(d.cuEventRecord(r.e0, cs));
+    PYC_CU(d.cuGraphLaunch(r.ge, cs));
+    PYC_CU(d.cuEventRecord(r.e1, cs));
+    PYC_CU(d.cuEventSynchronize(r.e1));
+    float ms = 0;
+    PYC_CU(d.cuEventElapsedTime(&ms, r.e0, r.e1));
+    best = std::min(best, (double)ms * 1000.0 / reps);
+  }
+  return best;
+}
+
 template <class H, class Launch>
-void autotune(H* h, int64_t n, CUstream stream, bool reduce, Launch&& launch_one) {
+void autotune(H* h, int64_t n, CUstream stream, bool reduce, Launch&& launch_one,
+              bool graph_timing) {
   if (n <= 0) fail(PYC_E_ARG, "autotune needs n > 0");
   // Representative size: n itself up to 2^28 elements (a variant's rank at a
   // quarter of the size can differ from its rank at the size that runs), with
@@ -130,7 +180,12 @@ void autotune(H* h, int64_t n, CUstream stream, bool reduce, Launch&& launch_one
       LaunchCfg c;
       c.v = v;
       c.block = b;
-      double us = time_us([&] { launch_one(c, nt, ptrs.data(), scal.data(), out); }, stream, 5);
+      double us =
+          time_us([&] { launch_one(c, nt, ptrs.data(), scal.data(), out, stream); }, stream, 5);
+      // short kernels: a single launch's sample includes the host's launch latency
+      if (graph_timing && us < 40.0)
+        us = time_graph_us(
+            [&](CUstream cs) { launch_one(c, nt, ptrs.data(), scal.data(), out, cs); }, 20);
       if (std::getenv("PYC_TUNE_LOG"))
         std::fprintf(stderr, "pyc tune %s %s n=%lld vec=%d unroll=%d block=%d %.2f us\n",
                      reduce ? "reduce" : "map", h->tag.c_str(), (long long)nt, v.vec_bytes,
@@ -152,8 +207,8 @@ void autotune(H* h, int64_t n, CUstream stream, bool reduce, Launch&& launch_one
 }  // namespace
 
 void autotune_generic(HandleBase& h, int64_t n, CUstream stream, bool reduce,
-                      const TuneLaunch& launch_one) {
-  autotune(&h, n, stream, reduce, launch_one);
+                      const TuneLaunch& launch_one, bool graph_timing) {
+  autotune(&h, n, stream, reduce, launch_one, graph_timing);
 }
 
 void tune_cache_load(HandleBase& h, bool reduce) {
@@ -246,9 +301,9 @@ PYC_API pyc_status pyc_map_autotune(pyc_map_t h, int64_t n, pyc_stream_t stream)
     if (!h) fail(PYC_E_ARG, "handle is NULL");
     CUstream s = reinterpret_cast<CUstream>(stream);
     autotune(h, n, s, false,
-             [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc, CUdeviceptr) {
-               launch_map(h, c, nt, p, sc, s);
-             });
+             [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc, CUdeviceptr,
+                 CUstream ls) { launch_map(h, c, nt, p, sc, ls); },
+             true);
   });
 }
 
@@ -257,8 +312,8 @@ PYC_API pyc_status pyc_reduce_autotune(pyc_reduce_t h, int64_t n, pyc_stream_t s
     if (!h) fail(PYC_E_ARG, "handle is NULL");
     CUstream s = reinterpret_cast<CUstream>(stream);
     autotune(h, n, s, true,
-             [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc, CUdeviceptr out) {
-               launch_reduce(h, c, nt, p, sc, reinterpret_cast<void*>(out), s);
-             });
+             [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc, CUdeviceptr out,
+                 CUstream ls) { launch_reduce(h, c, nt, p, sc, reinterpret_cast<void*>(out), ls); },
+             true);
   });
 }

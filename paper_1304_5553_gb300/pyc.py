@@ -43,7 +43,8 @@ class PycError(RuntimeError):
 class pyc_opts(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("vec_bytes", ctypes.c_int),
                 ("items_per_thread", ctypes.c_int), ("compensated", ctypes.c_int),
-                ("fmad", ctypes.c_int), ("preamble", ctypes.c_char_p)]
+                ("fmad", ctypes.c_int), ("preamble", ctypes.c_char_p),
+                ("debug_bounds", ctypes.c_int)]
 
 
 class pyc_param_info(ctypes.Structure):
@@ -111,7 +112,8 @@ EXPORTED = [
     "pyc_reduce_create", "pyc_reduce_launch", "pyc_reduce_batched", "pyc_reduce_num_params",
     "pyc_reduce_param", "pyc_reduce_scalar_bytes", "pyc_reduce_out_bytes", "pyc_reduce_source",
     "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats", "pyc_reduce_launch_static",
-    "pyc_reduce_static_scratch",
+    "pyc_reduce_static_scratch", "pyc_reduce_shard", "pyc_reduce_combine",
+    "pyc_map_check_bounds", "pyc_reduce_check_bounds", "pyc_test_inject",
     "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
     "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay", "pyc_map_launch_host",
     "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
@@ -171,6 +173,11 @@ def load(build_if_missing=True):
                                     vp]),
         "pyc_reduce_launch_static": (st, [vp, i64, ctypes.POINTER(vp), vp, vp, vp]),
         "pyc_reduce_static_scratch": (st, [ctypes.POINTER(vp), ctypes.POINTER(i64)]),
+        "pyc_reduce_shard": (st, [vp, i64, i64, i64, ctypes.POINTER(vp), vp, vp, vp]),
+        "pyc_reduce_combine": (st, [vp, i64, vp, vp, vp]),
+        "pyc_map_check_bounds": (st, [vp]),
+        "pyc_test_inject": (st, [i32, i64]),
+        "pyc_reduce_check_bounds": (st, [vp]),
         "pyc_scan_create": (st, [i32, cp, cp, cp, cp, cp, ctypes.POINTER(pyc_opts),
                                  ctypes.POINTER(vp)]),
         "pyc_scan_launch": (st, [vp, i64, ctypes.POINTER(vp), vp, vp]),
@@ -316,6 +323,39 @@ def pyc_reduce_launch_static(h, n, ptrs, scalars, d_out, stream=None):
     """pyc_reduce_launch without any device allocation (static scratch area)."""
     _check(load().pyc_reduce_launch_static(h, int(n), _ptr_array(ptrs), scalars, d_out,
                                            _stream(stream)))
+
+
+PYC_RECORD_BYTES = 16
+
+
+def pyc_reduce_shard(h, n_total, i0, n, ptrs, scalars, d_rec, stream=None):
+    """Fold shard [i0, i0 + n) of [0, n_total) into a 16-byte record at d_rec."""
+    _check(load().pyc_reduce_shard(h, int(n_total), int(i0), int(n), _ptr_array(ptrs), scalars,
+                                   d_rec, _stream(stream)))
+
+
+def pyc_reduce_combine(h, k, d_recs, d_out, stream=None):
+    """Fold k consecutive 16-byte records into the result at d_out."""
+    _check(load().pyc_reduce_combine(h, int(k), d_recs, d_out, _stream(stream)))
+
+
+PYC_INJECT_ALLOC, PYC_INJECT_COMPILE, PYC_INJECT_STALL_MS = 0, 1, 2
+
+
+def pyc_test_inject(what, value):
+    """Test hook: make the next `value` allocations / compilations fail, or the
+    next scheduler wake-up sleep `value` ms (value 0 clears)."""
+    _check(load().pyc_test_inject(int(what), int(value)))
+
+
+def pyc_map_check_bounds(h):
+    """Raise PycError(PYC_E_INTERNAL) if the checked map recorded a violation."""
+    _check(load().pyc_map_check_bounds(h))
+
+
+def pyc_reduce_check_bounds(h):
+    """Raise PycError(PYC_E_INTERNAL) if the checked map-reduce recorded a violation."""
+    _check(load().pyc_reduce_check_bounds(h))
 
 
 def pyc_reduce_static_scratch():

@@ -483,3 +483,53 @@ def test_concurrent_creates_from_eight_threads(tmp_path):
     # the twelve good kernels: 84 hits; the failing spec: a thread that asked while
     # another compiled it counts a hit, one that asked later compiles (and fails) again
     assert 8 * 12 - 12 <= res["stats"]["mem_hits"] <= 8 * 12 - 12 + 7
+
+
+def test_shard_and_combine_argument_errors_need_no_gpu():
+    """pyc_reduce_shard / pyc_reduce_combine reject bad ranges, NULL or
+    misaligned records and non-elementwise arrays before any GPU work."""
+    lib = pyc.load()
+    E = pyc.PYC_E_ARG
+    h = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i]", "float *x, float *y")
+    hs = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i+1]-x[i]", "float *x")
+    p = pyc._ptr_array([1 << 20, 1 << 21])
+    rec = 1 << 22
+    try:
+        for n_total, i0, n in ((-1, 0, 0), (10, -1, 1), (10, 0, -1), (10, 8, 3), (10, 11, 0),
+                               (2 ** 62, 2 ** 62, 2 ** 62)):
+            assert lib.pyc_reduce_shard(h, n_total, i0, n, p, None, rec, None) == E
+            assert "exceeds" in pyc.pyc_last_error() or ">= 0" in pyc.pyc_last_error()
+        assert lib.pyc_reduce_shard(h, 10, 0, 10, p, None, None, None) == E
+        assert lib.pyc_reduce_shard(h, 10, 0, 10, p, None, rec + 4, None) == E
+        assert lib.pyc_reduce_shard(hs, 10, 0, 10, p, None, rec, None) == E
+        assert "a shard holds only its own elements" in pyc.pyc_last_error()
+        assert lib.pyc_reduce_shard(h, 10, 0, 10, pyc._ptr_array([0, 1 << 21]), None, rec,
+                                    None) == E
+        assert lib.pyc_reduce_shard(None, 10, 0, 10, p, None, rec, None) == E
+        assert lib.pyc_reduce_combine(h, -1, rec, rec, None) == E
+        assert lib.pyc_reduce_combine(h, 2, None, rec, None) == E
+        assert lib.pyc_reduce_combine(h, 2, rec + 4, rec, None) == E
+        assert lib.pyc_reduce_combine(h, 2, rec, None, None) == E
+        assert lib.pyc_reduce_combine(h, 2, rec, rec + 2, None) == E
+        assert lib.pyc_reduce_combine(None, 2, rec, rec, None) == E
+    finally:
+        pyc.pyc_reduce_destroy(h)
+        pyc.pyc_reduce_destroy(hs)
+
+
+def test_shard_and_combine_kernels_are_generated():
+    """Every map-reduce module holds the shard kernel in all six variants and
+    one combine kernel, with the 16-byte record layout asserted in the source."""
+    for out, kw in ((pyc.PYC_F32, {}), (pyc.PYC_F32, {"compensated": 1}),
+                    (pyc.PYC_ARGMIN_F32, {}), (pyc.PYC_I64, {}), (pyc.PYC_BF16, {})):
+        if out == pyc.PYC_ARGMIN_F32:
+            h = pyc.pyc_reduce_create(out, None, None, "x[i]", "float *x")
+        elif out == pyc.PYC_I64:
+            h = pyc.pyc_reduce_create(out, "0", "a+b", "(long long)x[i]", "int *x")
+        else:
+            h = pyc.pyc_reduce_create(out, "0", "a+b", "x[i]", "float *x", kw)
+        src = pyc.pyc_reduce_source(h)
+        assert src.count("__global__ void __launch_bounds__(512) pyc_rshard_") == 6
+        assert src.count("pyc_rcomb_") == 1
+        assert 'static_assert(sizeof(pyc_record) == 16, "record size")' in src
+        pyc.pyc_reduce_destroy(h)
