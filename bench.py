@@ -249,26 +249,33 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
             pyc.pyc_reduce_launch(h, m, [x.data_ptr(), y.data_ptr()], None, out.data_ptr(),
                                   gs.cuda_stream)
     ms_g = _time_fn(torch, g.replay, 20) / 100
-    # cold: before each launch a 512 MiB write evicts x and y from L2; the events
-    # bracket the dot launch alone (median of 20)
+    # cold: before each launch a 512 MiB write evicts x and y from L2 (and leaves
+    # L2 full of dirty lines that the dot's misses must write back); the events
+    # bracket the dot launch alone (median of 20).  Beside it, cold after a
+    # 512 MiB read (L2 holds only clean lines of other data).
     flush = torch.empty(1 << 27, dtype=torch.float32, device=dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cold = []
-    for r in range(23):
-        flush.fill_(float(r))
+    cold, clean = [], []
+    for r in range(46):
+        if r % 2 == 0:
+            flush.fill_(float(r))
+        else:
+            flush.sum()
         a.record()
         f()
         b.record()
         torch.cuda.synchronize()
-        if r >= 3:
-            cold.append(a.elapsed_time(b))
+        if r >= 6:
+            (cold if r % 2 == 0 else clean).append(a.elapsed_time(b))
     ms_c = statistics.median(cold)
+    ms_cc = statistics.median(clean)
     res["dot_f32_n2^20"] = {"n": m, "us": round(ms * 1e3, 2),
                             "GB/s": round(8 * m / (ms * 1e-3) / 1e9, 1), "cache": "warm (fits L2)",
                             "launches_per_s": round(1e3 / ms, 1),
                             "graph_us": round(ms_g * 1e3, 2),
                             "cold_us": round(ms_c * 1e3, 2),
                             "cold_GB/s": round(8 * m / (ms_c * 1e-3) / 1e9, 1),
+                            "cold_after_read_flush_us": round(ms_cc * 1e3, 2),
                             "config": "vec%d_u%d_b%d" % pyc.launch_config(h, m, reduce=True)}
     del g, flush
     return res
@@ -559,7 +566,7 @@ def bench_batched(torch, pyc, stock, dev, reps=5):
                                                        y.data_ptr() + int(off[k]) * es],
                                       None, out.data_ptr() + 4 * k, s)
         ms_p = _time_fn(torch, per_seg, 1, warmup=1)
-        res[name] = {"config": "vec%d_u%d_b%d" % pyc.batched_config(h),
+        res[name] = {"config": pyc.batched_config_name(h),
                      "batched_ms": round(ms_b, 3), "per_segment_launches_ms": round(ms_p, 3),
                      "speedup": round(ms_p / ms_b, 2),
                      "batched_GB/s": round(bpe * total / (ms_b * 1e-3) / 1e9, 1),
@@ -805,7 +812,7 @@ def profile_batched(args):
     ptrs = [x.data_ptr(), y.data_ptr()]
     if args.autotune == "on" and not opts:
         pyc.pyc_reduce_batched_autotune(h, lens.size, off, ptrs, None, out.data_ptr(), s)
-    print("config vec%d_u%d_b%d" % pyc.batched_config(h), file=sys.stderr)
+    print("config " + pyc.batched_config_name(h), file=sys.stderr)
     f = lambda: pyc.pyc_reduce_batched(h, lens.size, off, ptrs, None, out.data_ptr(), s)
     ms = _time_fn(torch, f, args.steps, warmup=args.warmup)
     bpe = x.element_size() * 2

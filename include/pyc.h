@@ -374,7 +374,8 @@ pyc_status pyc_reduce_launch_static(pyc_reduce_t h, int64_t n, void* const* ptrs
 pyc_status pyc_reduce_static_scratch(void** d_addr, int64_t* bytes);
 
 /* Tune the batched launch (automated tuning, Sec. 3.3.1): time every vector
- * width x unroll x block candidate of the segmented reducer on this segment
+ * width x unroll x block candidate of the segmented reducer, and the
+ * register-lean build of the 16-byte variants at each block, on this segment
  * table (same arguments as pyc_reduce_batched; d_out receives results), keep the
  * fastest for the handle's batched launches -- pyc_reduce_batched and the
  * server's map-reduce batches -- and persist it in the tuning cache.
@@ -394,9 +395,13 @@ pyc_status pyc_reduce_config(pyc_reduce_t h, int64_t n, int* vec_bytes, int* unr
 /* Launch configuration (vector bytes, unroll, block size) of the handle's
  * batched launches (pyc_reduce_batched and the server's map-reduce batches):
  * the tuned one after pyc_reduce_batched_autotune, else the default, with any
- * fixed pyc_opts fields applied.  Any output pointer may be NULL.  Sec. 3.3.1
- * (the kept variants).  PYC_E_ARG for a NULL handle. */
-pyc_status pyc_reduce_batched_config(pyc_reduce_t h, int* vec_bytes, int* unroll, int* block);
+ * fixed pyc_opts fields applied.  *reg_cap is 0 for the regular build of the
+ * kernel, or the register cap of its register-lean build (16-byte variants: at
+ * most 80 registers a thread, so more CTAs fit on an SM; one of the tuner's
+ * candidates; a configuration fixed by pyc_opts fields is the regular build).  Any output pointer may be NULL.  Sec. 3.3.1 (the kept
+ * variants).  PYC_E_ARG for a NULL handle. */
+pyc_status pyc_reduce_batched_config(pyc_reduce_t h, int* vec_bytes, int* unroll, int* block,
+                                     int* reg_cap);
 void pyc_reduce_destroy(pyc_reduce_t h);
 
 /* ------------------------------------------------------------------ scan */

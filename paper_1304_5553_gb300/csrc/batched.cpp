@@ -107,7 +107,7 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
     PYC_CU(d.cuMemcpyHtoD(plan->items, items.data(), items.size() * sizeof(ReduceItem)));
   PYC_CU(d.cuMemsetD8(plan->tickets, 0, b_tickets + b_ctl));
 
-  plan->f = h->mod->function(h->kname("pyc_rbatch", cfg.v));
+  plan->f = h->mod->function(h->rbatch_name(cfg));
   int resident = resident_ctas(plan->f, cfg.block);
   plan->grid = std::max(1, std::min(resident, plan->nitems));
 
@@ -174,6 +174,11 @@ LaunchCfg batched_cfg(HandleBase& h, bool reduce) {
   if (h.opts.block) c.block = h.opts.block;
   if (h.opts.vec_bytes) c.v.vec_bytes = h.opts.vec_bytes;
   if (h.opts.items_per_thread) c.v.unroll = h.opts.items_per_thread;
+  // a configuration fixed by options is the regular build; only 16-byte
+  // reductions have a lean one
+  if (!reduce || c.v.vec_bytes != 16 || h.opts.block || h.opts.vec_bytes ||
+      h.opts.items_per_thread)
+    c.lean = 0;
   return c;
 }
 
@@ -249,11 +254,16 @@ void reduce_batched_autotune(pyc_reduce* h, int64_t nseg, const int64_t* off, vo
     for (const Variant& v : all_variants()) {
       if (h->opts.vec_bytes && v.vec_bytes != h->opts.vec_bytes) continue;
       if (h->opts.items_per_thread && v.unroll != h->opts.items_per_thread) continue;
-      for (int b : {128, 256, 512}) {
+      static const int kBlocks[3] = {128, 256, 512};
+      for (int lb = 0; lb < 6; ++lb) {
+        const int b = kBlocks[lb % 3];
+        const int lean = lb / 3;
+        if (lean && v.vec_bytes != 16) continue;  // only the 16-byte variants have it
         if (h->opts.block && b != h->opts.block) continue;
         LaunchCfg c;
         c.v = v;
         c.block = b;
+        c.lean = lean;
         std::unique_ptr<BatchPlan> plan = build_plan(h, nseg, off, ptrs, scalars, d_out, c);
         double us = 1e30;
         try {
@@ -273,8 +283,8 @@ void reduce_batched_autotune(pyc_reduce* h, int64_t nseg, const int64_t* off, vo
         }
         plan->release();
         if (std::getenv("PYC_TUNE_LOG"))
-          std::fprintf(stderr, "pyc tune batched %s nseg=%lld vec=%d unroll=%d block=%d %.2f us\n",
-                       h->tag.c_str(), (long long)nseg, v.vec_bytes, v.unroll, b, us);
+          std::fprintf(stderr, "pyc tune batched %s nseg=%lld vec=%d unroll=%d block=%d lean=%d %.2f us\n",
+                       h->tag.c_str(), (long long)nseg, v.vec_bytes, v.unroll, b, lean, us);
         if (us < best_us) {
           best_us = us;
           best = c;

@@ -1156,7 +1156,9 @@ struct pyc_item {
 )PYC";
   o << "static_assert(sizeof(pyc_task) == " << g.task_bytes << ", \"task layout\");\n";
   o << R"PYC(
-template <int VB, int U>
+// WU: unroll of the one-warp tasks (at most 2048 elements; the register-lean
+// build uses 1 there).
+template <int VB, int U, int WU>
 __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ tasks,
     const pyc_item* __restrict__ items, const int nitems, pyc_acc_t* __restrict__ part,
     unsigned* __restrict__ tickets, unsigned* __restrict__ ctl) {
@@ -1173,7 +1175,7 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
       const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
       if (w < I.count) {
         const pyc_task& T = tasks[I.task + w];
-        pyc_acc_t v = pyc_chunk<VB, U>(T.args, T.n, T.head, T.chunk, 0, lane, 32);
+        pyc_acc_t v = pyc_chunk<VB, WU>(T.args, T.n, T.head, T.chunk, 0, lane, 32);
         v = pyc_warp_reduce(v, pyc_combine_op());
         if (lane == 0) *T.out = pyc_finalize(v);
       }
@@ -1230,8 +1232,17 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
     o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rbatch_" << tag << "_" << sfx
       << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
          "unsigned* tickets, unsigned* ctl) {\n"
-      << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll
+      << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll << ", " << v.unroll
       << ">(tasks, items, nitems, part, tickets, ctl);\n}\n";
+    // register-lean build of the 16-byte variants (a tuning candidate): at most
+    // kLeanRegs registers, so more CTAs -- and more loads in flight -- per SM
+    if (v.vec_bytes == 16)
+      o << "extern \"C\" __global__ void __maxnreg__(" << kLeanRegs << ") pyc_rbatch_" << tag << "_"
+        << sfx << "_r" << kLeanRegs
+        << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
+           "unsigned* tickets, unsigned* ctl) {\n"
+        << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll
+        << ", 1>(tasks, items, nitems, part, tickets, ctl);\n}\n";
   }
   if (emit_kernels)
     o << "extern \"C\" __global__ void __launch_bounds__(" << kCombineBlock << ") pyc_rcomb_" << tag
@@ -1253,6 +1264,50 @@ ScanGen generate_scan(const ArgSpec& spec, pyc_dtype dtype, const std::string& n
   g.stage_elem_bytes = stage_elem_bytes(spec);
   std::ostringstream o;
   o << core.source;
+  // The scan of one step's rows with the output statement, then the vector
+  // stores of the written arrays: shared by both forms of sweep 2.
+  const std::string scan_rows = std::string(R"PYC(#pragma unroll
+    for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
+      pyc_acc_t pyc_l[E];
+#pragma unroll
+      for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
+        const int pyc_k = pyc_u * E + pyc_e;
+        const pyc_i64 i = pyc_gb + (pyc_i64)pyc_u * (32 * E) + pyc_e;
+        (void)i;
+        pyc_acc_t pyc_x = pyc_neutral();
+        if (!RAG || i < te) pyc_x = (pyc_acc_t)()PYC") + input_expr + R"PYC();
+        pyc_l[pyc_e] = pyc_e == 0 ? pyc_x : pyc_combine(pyc_l[pyc_e - 1], pyc_x);
+      }
+      const pyc_acc_t pyc_in = pyc_warp_incl_scan(pyc_l[E - 1]);
+      pyc_acc_t pyc_ex = pyc_shfl_up(pyc_in, 1);
+      if (lane == 0) pyc_ex = pyc_neutral();
+      const pyc_acc_t pyc_p0 = pyc_combine(pyc_run, pyc_ex);
+#pragma unroll
+      for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
+        const int pyc_k = pyc_u * E + pyc_e;
+        const pyc_i64 i = pyc_gb + (pyc_i64)pyc_u * (32 * E) + pyc_e;
+        (void)i;
+        const pyc_acc_t item = pyc_combine(pyc_p0, pyc_l[pyc_e]);
+        const pyc_acc_t prev_item = pyc_e == 0 ? pyc_p0 : pyc_combine(pyc_p0, pyc_l[pyc_e - 1]);
+        (void)item;
+        (void)prev_item;
+        if (!RAG || i < te) {
+          { )PYC" + output_stmt + R"PYC( ; }
+          if constexpr (RAG) {
+            if (PYC_OK(S, i, 1, S.n, 23, t)) {
+)PYC" + scalar_stores_k(spec) + R"PYC(            }
+          }
+        }
+      }
+      pyc_run = pyc_combine(pyc_run, pyc_shfl_idx(pyc_in, 31));
+    }
+    if constexpr (!RAG) {
+#pragma unroll
+      for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
+        const pyc_i64 pyc_e0 = pyc_gb + (pyc_i64)pyc_u * (32 * E);
+        if (PYC_OK(S, pyc_e0, E, S.n, 24, t)) {
+)PYC" + with_policy(group_io(spec, false), "pyc_pd") + "        }\n      }\n    }\n";
+
   o << R"PYC(
 // ------------------------------------------------------------------ scan
 template <typename T>
@@ -1610,56 +1665,8 @@ __device__ __forceinline__ void pyc_sweep2(const pyc_args& pyc_p, const pyc_scan
 )PYC";
   o << "        if (PYC_OK(S, pyc_e0, E, S.n, 22, t)) {\n"
     << with_policy(group_io(spec, true), "pyc_pd") << "        }\n";
-  o << R"PYC(      }
-    }
-#pragma unroll
-    for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
-      pyc_acc_t pyc_l[E];
-#pragma unroll
-      for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
-        const int pyc_k = pyc_u * E + pyc_e;
-        const pyc_i64 i = pyc_gb + (pyc_i64)pyc_u * (32 * E) + pyc_e;
-        (void)i;
-        pyc_acc_t pyc_x = pyc_neutral();
-        if (!RAG || i < te) pyc_x = (pyc_acc_t)()PYC" << input_expr << R"PYC();
-        pyc_l[pyc_e] = pyc_e == 0 ? pyc_x : pyc_combine(pyc_l[pyc_e - 1], pyc_x);
-      }
-      const pyc_acc_t pyc_in = pyc_warp_incl_scan(pyc_l[E - 1]);
-      pyc_acc_t pyc_ex = pyc_shfl_up(pyc_in, 1);
-      if (lane == 0) pyc_ex = pyc_neutral();
-      const pyc_acc_t pyc_p0 = pyc_combine(pyc_run, pyc_ex);
-#pragma unroll
-      for (int pyc_e = 0; pyc_e < E; ++pyc_e) {
-        const int pyc_k = pyc_u * E + pyc_e;
-        const pyc_i64 i = pyc_gb + (pyc_i64)pyc_u * (32 * E) + pyc_e;
-        (void)i;
-        const pyc_acc_t item = pyc_combine(pyc_p0, pyc_l[pyc_e]);
-        const pyc_acc_t prev_item = pyc_e == 0 ? pyc_p0 : pyc_combine(pyc_p0, pyc_l[pyc_e - 1]);
-        (void)item;
-        (void)prev_item;
-        if (!RAG || i < te) {
-          { )PYC" << output_stmt << R"PYC( ; }
-          if constexpr (RAG) {
-            if (PYC_OK(S, i, 1, S.n, 23, t)) {
-)PYC";
-  o << scalar_stores_k(spec);
-  o << R"PYC(            }
-          }
-        }
-      }
-      pyc_run = pyc_combine(pyc_run, pyc_shfl_idx(pyc_in, 31));
-    }
-    if constexpr (!RAG) {
-#pragma unroll
-      for (int pyc_u = 0; pyc_u < RU; ++pyc_u) {
-        const pyc_i64 pyc_e0 = pyc_gb + (pyc_i64)pyc_u * (32 * E);
-)PYC";
-  o << "        if (PYC_OK(S, pyc_e0, E, S.n, 24, t)) {\n"
-    << with_policy(group_io(spec, false), "pyc_pd") << "        }\n";
-  o << R"PYC(      }
-    }
-  }
-}
+  o << "      }\n    }\n" << scan_rows << "  }\n}\n";
+  o << R"PYC(
 
 // Tile t: [ts, te), row groups per warp, and whether it is ragged.  Order: the
 // scalar head (if head > 0), nfull vector tiles of `groups` row groups, one of
@@ -1712,6 +1719,60 @@ __device__ __forceinline__ pyc_tinfo pyc_tile_info(const pyc_scan_params& S, con
   o << prefetch_used(spec, input_expr);
   o << "  (void)ts; (void)te; (void)tid; (void)nt;\n}\n";
   o << R"PYC(
+// The look-back warp of a CTA (warp nw): for each tile the compute warps fold
+// (slot k & 1), scan the warp aggregates, find the tile's exclusive prefix,
+// publish its inclusive prefix and hand back the prefix of each compute warp's
+// rows.  false if a wait ran out.
+__device__ __forceinline__ bool pyc_lookback_warp(const pyc_scan_params& S, const int nw,
+    const int lane, pyc_acc_t (*pyc_tot)[32], pyc_acc_t (*pyc_off)[32], pyc_i64* pyc_tq,
+    unsigned long long* pyc_ma, unsigned long long* pyc_mp, unsigned long long* err) {
+  for (int k = 0;; ++k) {
+    const int sl = k & 1;
+    const unsigned ph = (unsigned)(k >> 1) & 1u;
+    if (!pyc_mbar_wait(&pyc_ma[sl], ph, err)) return false;
+    const pyc_i64 t = pyc_tq[sl];
+    if (t >= S.ntiles || !PYC_OK(S, t, 0, S.ntiles, 41, t)) return true;
+    pyc_acc_t s = lane < nw ? pyc_tot[sl][lane] : pyc_neutral();
+    s = pyc_warp_incl_scan(s);
+    const pyc_acc_t agg = pyc_shfl_idx(s, nw - 1);  // (all lanes: a warp-wide shuffle)
+    pyc_acc_t ex = pyc_neutral();
+    if (t > 0) {
+      ex = pyc_lookback(S, t);
+      if (lane == 0) pyc_publish(S, t, 2u, pyc_combine(ex, agg));
+    }
+    pyc_acc_t o = pyc_shfl_up(s, 1);
+    if (lane == 0) o = pyc_neutral();
+    if (lane < nw) pyc_off[sl][lane] = pyc_combine(ex, o);
+    __syncwarp();
+    if (lane == 0) pyc_mbar_arrive(&pyc_mp[sl]);
+  }
+}
+
+// A compute warp stores its aggregate `a` of tile t; the last of the nw warps to
+// do so publishes the tile's aggregate at once (its inclusive prefix for tile
+// 0), so that later tiles need not wait for this CTA's look-back warp.
+__device__ __forceinline__ void pyc_store_aggregate(const pyc_scan_params& S, const pyc_i64 t,
+    const int nw, const int w, const int lane, const pyc_acc_t a, pyc_acc_t* tot,
+    unsigned* cnt) {
+  unsigned last = 0u;
+  if (lane == 0) {
+    tot[w] = a;
+    __threadfence_block();
+    last = atomicAdd(cnt, 1u) == (unsigned)nw - 1u ? 1u : 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence_block();
+    pyc_acc_t s = lane < nw ? tot[lane] : pyc_neutral();
+    s = pyc_warp_incl_scan(s);
+    const pyc_acc_t agg = pyc_shfl_idx(s, nw - 1);
+    if (lane == 0) {
+      pyc_publish(S, t, t == 0 ? 2u : 1u, agg);
+      *cnt = 0u;
+    }
+  }
+}
+
 // Persistent single-pass scan with a look-back warp.  The CTA has nw compute
 // warps and one look-back warp (the last).  Iteration k of the compute warps:
 // take tile k, sweep 1 over it, publish its aggregate and hand the warp
@@ -1750,26 +1811,7 @@ __device__ __forceinline__ void pyc_scan_body(const pyc_args& pyc_p, const pyc_s
   }
   __syncthreads();
   if (w == nw) {
-    for (int k = 0;; ++k) {
-      const int sl = k & 1;
-      const unsigned ph = (unsigned)(k >> 1) & 1u;
-      if (!pyc_mbar_wait(&pyc_ma[sl], ph, err)) return;
-      const pyc_i64 t = pyc_tq[sl];
-      if (t >= S.ntiles || !PYC_OK(S, t, 0, S.ntiles, 41, t)) break;
-      pyc_acc_t s = lane < nw ? pyc_tot[sl][lane] : pyc_neutral();
-      s = pyc_warp_incl_scan(s);
-      const pyc_acc_t agg = pyc_shfl_idx(s, nw - 1);  // (all lanes: a warp-wide shuffle)
-      pyc_acc_t ex = pyc_neutral();
-      if (t > 0) {
-        ex = pyc_lookback(S, t);
-        if (lane == 0) pyc_publish(S, t, 2u, pyc_combine(ex, agg));
-      }
-      pyc_acc_t o = pyc_shfl_up(s, 1);
-      if (lane == 0) o = pyc_neutral();
-      if (lane < nw) pyc_off[sl][lane] = pyc_combine(ex, o);
-      __syncwarp();
-      if (lane == 0) pyc_mbar_arrive(&pyc_mp[sl]);
-    }
+    if (!pyc_lookback_warp(S, nw, lane, pyc_tot, pyc_off, pyc_tq, pyc_ma, pyc_mp, err)) return;
   } else {
     pyc_i64 tprev = -1;
     for (int k = 0;; ++k) {
@@ -1788,26 +1830,7 @@ __device__ __forceinline__ void pyc_scan_body(const pyc_args& pyc_p, const pyc_s
         const pyc_acc_t a =
             I.rag ? pyc_sweep1<VB, U, true>(pyc_p, S, t, I.ts, I.te, I.g, w, lane)
                   : pyc_sweep1<VB, U, false>(pyc_p, S, t, I.ts, I.te, I.g, w, lane);
-        unsigned last = 0u;
-        if (lane == 0) {
-          pyc_tot[sl][w] = a;
-          __threadfence_block();
-          last = atomicAdd(&pyc_cnt[sl], 1u) == (unsigned)nw - 1u ? 1u : 0u;
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-          // every aggregate of the tile is stored: publish the tile's at once
-          // (its inclusive prefix for tile 0), so that later tiles need not wait
-          // for this CTA's look-back warp
-          __threadfence_block();
-          pyc_acc_t s = lane < nw ? pyc_tot[sl][lane] : pyc_neutral();
-          s = pyc_warp_incl_scan(s);
-          const pyc_acc_t agg = pyc_shfl_idx(s, nw - 1);
-          if (lane == 0) {
-            pyc_publish(S, t, t == 0 ? 2u : 1u, agg);
-            pyc_cnt[sl] = 0u;
-          }
-        }
+        pyc_store_aggregate(S, t, nw, w, lane, a, pyc_tot[sl], &pyc_cnt[sl]);
       }
       __syncwarp();
       if (lane == 0) pyc_mbar_arrive(&pyc_ma[sl]);

@@ -38,6 +38,10 @@ MapGen generate_map(const ArgSpec& spec, const std::string& stmt_rewritten,
 
 enum class ReduceKind { Plain, Arg, Compensated };
 
+// Register cap of the register-lean batched reduction kernels (16-byte
+// variants, suffix _r<kLeanRegs>): with it a CTA of 512 threads still fits.
+constexpr int kLeanRegs = 80;
+
 // Threads of the one CTA that combines the records of a sharded reduction.
 constexpr int kCombineBlock = 256;
 // Bytes of one shard record (the accumulator before the final conversion).

@@ -23,6 +23,7 @@ namespace pyc {
 struct LaunchCfg {
   Variant v{16, 4};
   int block = 256;
+  int lean = 0;  // batched reductions: 1 = the register-lean build (16-byte variants)
 };
 
 // Size buckets for tuning: bucket b holds n with bit length in [2b, 2b+1].
@@ -53,6 +54,10 @@ struct HandleBase {
   // Kernel function name, e.g. kname("pyc_map", v) = "pyc_map_<tag>_v16_u4".
   std::string kname(const char* kind, const Variant& v) const {
     return std::string(kind) + "_" + tag + "_" + variant_suffix(v);
+  }
+  // Batched reduction kernel of a configuration (the lean build's suffix included).
+  std::string rbatch_name(const LaunchCfg& c) const {
+    return kname("pyc_rbatch", c.v) + (c.lean ? "_r" + std::to_string(kLeanRegs) : "");
   }
 };
 

@@ -231,6 +231,8 @@ void tune_cache_load(HandleBase& h, bool reduce) {
     c.v.vec_bytes = std::atoi(vb.c_str());
     c.v.unroll = std::atoi(u.c_str());
     c.block = std::atoi(blk.c_str());
+    std::string ln;
+    c.lean = field(line, "lean", &ln) && ln == "1" && c.v.vec_bytes == 16 ? 1 : 0;
     bool ok = (c.v.vec_bytes == 16 || c.v.vec_bytes == 32) &&
               (c.v.unroll == 1 || c.v.unroll == 2 || c.v.unroll == 4) && c.block >= 32 &&
               c.block <= 512 && c.block % 32 == 0;
@@ -252,7 +254,8 @@ void tune_cache_store(const HandleBase& h, bool reduce, int bucket, const Launch
   std::ostringstream o;
   o << "{\"key\":\"" << h.tune_key << "\",\"kind\":\"" << (reduce ? "reduce" : "map")
     << "\",\"bucket\":" << bucket << ",\"vec_bytes\":" << c.v.vec_bytes
-    << ",\"unroll\":" << c.v.unroll << ",\"block\":" << c.block << ",\"us\":" << us
+    << ",\"unroll\":" << c.v.unroll << ",\"block\":" << c.block << ",\"lean\":" << c.lean
+    << ",\"us\":" << us
     << ",\"device\":\"" << dev << "\"}\n";
   std::lock_guard<std::mutex> flk(g_file_mu);
   std::ofstream f(path, std::ios::app);
@@ -286,13 +289,14 @@ PYC_API pyc_status pyc_reduce_config(pyc_reduce_t h, int64_t n, int* vec_bytes, 
 }
 
 PYC_API pyc_status pyc_reduce_batched_config(pyc_reduce_t h, int* vec_bytes, int* unroll,
-                                             int* block) {
+                                             int* block, int* reg_cap) {
   return guarded([&] {
     if (!h) fail(PYC_E_ARG, "handle is NULL");
     LaunchCfg c = batched_cfg(*h, true);
     if (vec_bytes) *vec_bytes = c.v.vec_bytes;
     if (unroll) *unroll = c.v.unroll;
     if (block) *block = c.block;
+    if (reg_cap) *reg_cap = c.lean ? kLeanRegs : 0;
   });
 }
 

@@ -156,7 +156,7 @@ def load(build_if_missing=True):
         "pyc_map_launch_host": (st, [vp, i64, ctypes.POINTER(vp), vp]),
         "pyc_map_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
         "pyc_reduce_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
-        "pyc_reduce_batched_config": (st, [vp] + [ctypes.POINTER(i32)] * 3),
+        "pyc_reduce_batched_config": (st, [vp] + [ctypes.POINTER(i32)] * 4),
         "pyc_reduce_batched_plan": (st, [vp, i64, vp, ctypes.POINTER(vp), vp, vp, vp, i64,
                                          ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "pyc_scan_config": (st, [vp, i64] + [ctypes.POINTER(i32)] * 3),
@@ -614,9 +614,22 @@ def batched_plan(h, seg_offsets, ptrs, scalars=None):
 
 def batched_config(h):
     """(vec_bytes, unroll, block) of the handle's batched launches."""
-    v, u, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(load().pyc_reduce_batched_config(h, ctypes.byref(v), ctypes.byref(u), ctypes.byref(b)))
-    return v.value, u.value, b.value
+    return batched_config_full(h)[:3]
+
+
+def batched_config_full(h):
+    """(vec_bytes, unroll, block, reg_cap) of the handle's batched launches;
+    reg_cap 0 = the regular build, else the register cap of the lean build."""
+    v, u, b, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().pyc_reduce_batched_config(h, ctypes.byref(v), ctypes.byref(u), ctypes.byref(b),
+                                            ctypes.byref(r)))
+    return v.value, u.value, b.value, r.value
+
+
+def batched_config_name(h):
+    """The batched configuration as text, e.g. vec16_u2_b128_r80."""
+    v, u, b, r = batched_config_full(h)
+    return "vec%d_u%d_b%d" % (v, u, b) + ("_r%d" % r if r else "")
 
 
 def pyc_cache_stats():

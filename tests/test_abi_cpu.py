@@ -298,7 +298,7 @@ def test_batched_config_default_and_fixed_options():
     g = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i]", spec,
                               {"vec_bytes": 32, "items_per_thread": 2, "block": 128})
     assert pyc.batched_config(g) == (32, 2, 128)
-    assert pyc.load().pyc_reduce_batched_config(None, None, None, None) == pyc.PYC_E_ARG
+    assert pyc.load().pyc_reduce_batched_config(None, None, None, None, None) == pyc.PYC_E_ARG
     pyc.pyc_reduce_destroy(h)
     pyc.pyc_reduce_destroy(g)
 

@@ -86,11 +86,14 @@ def test_unaligned_base_pointers_and_variants():
             assert np.all(np.abs(out.cpu().numpy() - ref) <= plain_sum_bound(ab))
 
 
+@pytest.mark.parametrize("tuned", [False, True])
 @pytest.mark.parametrize("bf16", [False, True])
-def test_config_20000_segments(bf16):
+def test_config_20000_segments(bf16, tuned):
     """20,000 segments, lengths log-uniform in [1, 2^20]; graph replay gives the
     same bits; every segment within the plain-sum bound of the oracle; integer-free
-    cross-check against one launch per segment."""
+    cross-check against one launch per segment.  `tuned`: after the batched
+    autotuner has run on the table, as the benchmark does, so that the
+    configuration it times (on GB300 the register-lean build) is the one checked."""
     lens = inputs.segment_lengths()
     off = _offsets(lens)
     total = int(off[-1])
@@ -103,6 +106,12 @@ def test_config_20000_segments(bf16):
     else:
         dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
     name = "dot_bf16" if bf16 else "dot_f32"
+    if tuned:
+        h = stock.create(name)
+        o = torch.zeros(len(lens), device="cuda")
+        pyc.pyc_reduce_batched_autotune(h, len(lens), off, [dx.data_ptr(), dy.data_ptr()], None,
+                                        o.data_ptr(), _s())
+        print("tuned batched configuration:", pyc.batched_config_name(h))
     out, h, _ = _batched(name, off, [dx, dy])
     first = out.clone()
     pyc.pyc_reduce_batched(h, len(lens), off, [dx.data_ptr(), dy.data_ptr()], None,
