@@ -418,8 +418,15 @@ PYC_API pyc_status pyc_reduce_create(pyc_dtype out_dtype, const char* neutral,
                              ordered);
     h->source = h->gen.source;
     finish_handle(*h, true);
+    h->source_ext = (h->bounds ? bounds_defines() : std::string()) + h->gen.source_ext;
     *out = h.release();
   });
+}
+
+pyc::Module& pyc_reduce::ext() {
+  std::lock_guard<std::mutex> lk(ext_mu);
+  if (!mod_ext) mod_ext = pyc::get_module(source_ext, opts.fmad != 0);
+  return *mod_ext;
 }
 
 PYC_API pyc_status pyc_reduce_launch(pyc_reduce_t h, int64_t n, void* const* ptrs,

@@ -107,7 +107,7 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
     PYC_CU(d.cuMemcpyHtoD(plan->items, items.data(), items.size() * sizeof(ReduceItem)));
   PYC_CU(d.cuMemsetD8(plan->tickets, 0, b_tickets + b_ctl));
 
-  plan->f = h->mod->function(h->rbatch_name(cfg));
+  plan->f = h->batched_module(cfg).function(h->rbatch_name(cfg));
   int resident = resident_ctas(plan->f, cfg.block);
   plan->grid = std::max(1, std::min(resident, plan->nitems));
 

@@ -1215,41 +1215,49 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
 }
 
 )PYC";
+  // Entry points: the main module holds the single and batched reductions; the
+  // extra module, compiled on first use, the sharded reduction, the combine of
+  // shard records and the register-lean batched builds.
+  std::ostringstream m, x;
   for (auto& v : all_variants()) {
-    if (!emit_kernels) break;
     std::string sfx = variant_suffix(v);
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_reduce_" << tag << "_" << sfx
+    m << "extern \"C\" __global__ void __launch_bounds__(512) pyc_reduce_" << tag << "_" << sfx
       << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
          "const pyc_i64 nchunks, pyc_acc_t* part, unsigned* ticket, pyc_out_t* out) {\n"
       << "  pyc_reduce_body<" << v.vec_bytes << ", " << v.unroll
       << ">(pyc_p, n, head, chunk, nchunks, part, ticket, out);\n}\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rshard_" << tag << "_" << sfx
+    m << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rbatch_" << tag << "_" << sfx
+      << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
+         "unsigned* tickets, unsigned* ctl) {\n"
+      << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll << ", " << v.unroll
+      << ">(tasks, items, nitems, part, tickets, ctl);\n}\n";
+    x << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rshard_" << tag << "_" << sfx
       << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 base, const pyc_i64 len, "
          "const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 nchunks, pyc_acc_t* part, "
          "unsigned* ticket, pyc_record* rec) {\n"
       << "  pyc_shard_body<" << v.vec_bytes << ", " << v.unroll
       << ">(pyc_p, n, base, len, head, chunk, nchunks, part, ticket, rec);\n}\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rbatch_" << tag << "_" << sfx
-      << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
-         "unsigned* tickets, unsigned* ctl) {\n"
-      << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll << ", " << v.unroll
-      << ">(tasks, items, nitems, part, tickets, ctl);\n}\n";
     // register-lean build of the 16-byte variants (a tuning candidate): at most
     // kLeanRegs registers, so more CTAs -- and more loads in flight -- per SM
     if (v.vec_bytes == 16)
-      o << "extern \"C\" __global__ void __maxnreg__(" << kLeanRegs << ") pyc_rbatch_" << tag << "_"
+      x << "extern \"C\" __global__ void __maxnreg__(" << kLeanRegs << ") pyc_rbatch_" << tag << "_"
         << sfx << "_r" << kLeanRegs
         << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
            "unsigned* tickets, unsigned* ctl) {\n"
         << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll
         << ", 1>(tasks, items, nitems, part, tickets, ctl);\n}\n";
   }
-  if (emit_kernels)
-    o << "extern \"C\" __global__ void __launch_bounds__(" << kCombineBlock << ") pyc_rcomb_" << tag
-      << "(const pyc_record* rec, const pyc_i64 k, pyc_out_t* out) {\n"
-         "  const pyc_out_t r = pyc_combine_records(rec, k);\n"
-         "  if (threadIdx.x == 0) *out = r;\n}\n";
-  g.source = o.str();
+  x << "extern \"C\" __global__ void __launch_bounds__(" << kCombineBlock << ") pyc_rcomb_" << tag
+    << "(const pyc_record* rec, const pyc_i64 k, pyc_out_t* out) {\n"
+       "  const pyc_out_t r = pyc_combine_records(rec, k);\n"
+       "  if (threadIdx.x == 0) *out = r;\n}\n";
+  const std::string common = o.str();
+  if (emit_kernels) {
+    g.source = common + m.str();
+    g.source_ext = common + x.str();
+  } else {
+    g.source = common;
+  }
   return g;
 }
 

@@ -48,7 +48,8 @@ constexpr int kCombineBlock = 256;
 constexpr int kRecordBytes = 16;
 
 struct ReduceGen {
-  std::string source;
+  std::string source;      // main module: single and batched reductions
+  std::string source_ext;  // extra module: sharded reduction, record combine, lean batched
   int acc_bytes = 0;
   int out_bytes = 0;
   int task_bytes = 0;       // size of one batched task record

@@ -89,6 +89,14 @@ struct pyc_reduce : pyc::HandleBase {
   std::map<std::pair<CUcontext, CUstream>, Workspace> ws;
   std::mutex plan_mu;
   std::vector<std::unique_ptr<pyc::BatchPlan>> plans;  // most recent last
+  // The extra module (sharded reduction, record combine, register-lean batched
+  // kernels), compiled on first use: most handles never need it.
+  std::string source_ext;
+  std::mutex ext_mu;
+  std::shared_ptr<pyc::Module> mod_ext;
+  pyc::Module& ext();
+  // Module holding the batched kernel of a configuration.
+  pyc::Module& batched_module(const pyc::LaunchCfg& c) { return c.lean ? ext() : *mod; }
   // Set-up of pyc_reduce_launch_static for the context it was last called in:
   // kernel handles of every variant and resident CTAs per (variant, block / 32).
   std::mutex static_mu;

@@ -260,7 +260,7 @@ void launch_batch(pyc_server* s, Batch& b) {
     if (!items.empty())
       std::memcpy(sl.host + tasks.size(), items.data(), items.size() * sizeof(ReduceItem));
     nitems = (int)items.size();
-    f = h->mod->function(h->rbatch_name(cfg));
+    f = h->batched_module(cfg).function(h->rbatch_name(cfg));
     b.res_host_off = L.host_res;
     b.out_bytes = h->gen.out_bytes;
   } else {

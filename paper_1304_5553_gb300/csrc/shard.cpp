@@ -49,7 +49,7 @@ void reduce_shard(pyc_reduce* h, int64_t n_total, int64_t i0, int64_t n, void* c
       adj[p.ptr_slot] = reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(ptrs[p.ptr_slot]) -
                                                 (uintptr_t)i0 * type_info(p.dtype).bytes);
   std::vector<unsigned char> args = pack_args(spec, adj.data(), scalars);
-  CUfunction f = h->mod->function(h->kname("pyc_rshard", cfg.v));
+  CUfunction f = h->ext().function(h->kname("pyc_rshard", cfg.v));
   int resident = resident_ctas(f, cfg.block);
   int64_t tile = (int64_t)cfg.block * (cfg.v.vec_bytes / h->min_bytes) * cfg.v.unroll;
   ChunkPlan cp = plan_chunks(n, head, tile, resident);
@@ -66,8 +66,9 @@ void reduce_combine(pyc_reduce* h, int64_t k, const void* d_recs, void* d_out, C
   if (!d_out) fail(PYC_E_ARG, "d_out is NULL");
   if (reinterpret_cast<uintptr_t>(d_out) % (uintptr_t)std::min(h->gen.out_bytes, 8))
     fail(PYC_E_ARG, "d_out is not aligned to the result type");
+  Module& m = h->ext();  // compiled (or loaded from the cache) before any GPU work
   ensure_context();
-  CUfunction f = h->mod->function("pyc_rcomb_" + h->tag);
+  CUfunction f = m.function("pyc_rcomb_" + h->tag);
   void* params[] = {&d_recs, &k, &d_out};
   PYC_CU(drv().cuLaunchKernel(f, 1, 1, 1, (unsigned)kCombineBlock, 1, 1, 0, stream, params,
                               nullptr));

@@ -8,6 +8,9 @@ order with the handle's reduce expression (``pyc_reduce_combine``).  The
 exchange is the one collective of the path; maps and segmented batches shard
 with none.
 
+Segmented batches shard by whole segments (:func:`segment_bounds`, balanced by
+elements) and need no exchange at all.
+
 The three steps are methods of :class:`ShardedReduce` so that each can be
 checked on its own: ``partial`` and ``combine`` are C-ABI calls on the GPU,
 ``exchange`` is a plain ``torch.distributed`` all-gather (NCCL between GPUs,
@@ -24,6 +27,32 @@ def shard_bounds(n_total: int, world: int) -> list:
     if world < 1 or n_total < 0:
         raise ValueError("need world >= 1 and n_total >= 0")
     return [(n_total * r) // world for r in range(world + 1)]
+
+
+def segment_bounds(seg_offsets, world: int) -> list:
+    """Split a segment table across ranks for pyc_reduce_batched with no
+    exchange: rank r takes the whole segments [b[r], b[r + 1]) (b[0] = 0,
+    b[world] = nseg), the cut after segment s placed where the elements before
+    it come closest to r / world of the total, so that ranks get about equal
+    bytes; a rank may get no segment.  Each rank reduces its segments into its
+    own results; nothing is combined."""
+    import numpy as np
+    off = np.asarray(seg_offsets, dtype=np.int64)
+    if off.ndim != 1 or off.size < 1 or world < 1:
+        raise ValueError("need seg_offsets of nseg + 1 entries and world >= 1")
+    nseg = off.size - 1
+    start = off - off[0]
+    total = int(start[-1])
+    b = [0]
+    for r in range(1, world):
+        target = total * r / world
+        # the segment boundary nearest the target, never before the previous cut
+        k = int(np.searchsorted(start, target, side="left"))
+        if k > 0 and k <= nseg and abs(start[k - 1] - target) <= abs(start[min(k, nseg)] - target):
+            k -= 1
+        b.append(max(b[-1], min(k, nseg)))
+    b.append(nseg)
+    return b
 
 
 class ShardedReduce:

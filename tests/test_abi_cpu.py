@@ -518,8 +518,9 @@ def test_shard_and_combine_argument_errors_need_no_gpu():
 
 
 def test_shard_and_combine_kernels_are_generated():
-    """Every map-reduce module holds the shard kernel in all six variants and
-    one combine kernel, with the 16-byte record layout asserted in the source."""
+    """A map-reduce's main module holds the single and batched reductions; the
+    shard kernels (six variants), the record combine and the register-lean
+    batched builds are in its extra module, compiled on first use."""
     for out, kw in ((pyc.PYC_F32, {}), (pyc.PYC_F32, {"compensated": 1}),
                     (pyc.PYC_ARGMIN_F32, {}), (pyc.PYC_I64, {}), (pyc.PYC_BF16, {})):
         if out == pyc.PYC_ARGMIN_F32:
@@ -529,7 +530,36 @@ def test_shard_and_combine_kernels_are_generated():
         else:
             h = pyc.pyc_reduce_create(out, "0", "a+b", "x[i]", "float *x", kw)
         src = pyc.pyc_reduce_source(h)
-        assert src.count("__global__ void __launch_bounds__(512) pyc_rshard_") == 6
-        assert src.count("pyc_rcomb_") == 1
+        assert src.count("__global__ void __launch_bounds__(512) pyc_reduce_") == 6
+        assert src.count("__global__ void __launch_bounds__(512) pyc_rbatch_") == 6
+        assert "pyc_rshard_" not in src.split("pyc_shard_body")[-1] and "_r80(" not in src
         assert 'static_assert(sizeof(pyc_record) == 16, "record size")' in src
         pyc.pyc_reduce_destroy(h)
+
+
+_EXT_CHILD = r"""
+import json, sys
+sys.path.insert(0, %r)
+from paper_1304_5553_gb300 import pyc
+lib = pyc.load()
+h = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i] + 0.5f", "float *x, float *y")
+c0 = pyc.pyc_cache_stats()["compiled"]
+st = []
+for _ in range(2):
+    st.append(lib.pyc_reduce_shard(h, 100, 0, 100, pyc._ptr_array([1 << 20, 1 << 21]), None,
+                                   1 << 22, None))
+c1 = pyc.pyc_cache_stats()["compiled"]
+print(json.dumps({"c0": c0, "c1": c1, "st": st}))
+"""
+
+
+@pytest.mark.skipif(_has_gpu(), reason="checks the compile-then-no-driver path")
+def test_extra_module_is_compiled_on_first_use(tmp_path):
+    env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
+    out = subprocess.run([sys.executable, "-c", _EXT_CHILD % ROOT], env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    assert r["c0"] == 1            # creation compiled the main module only
+    assert r["c1"] == 2            # the first shard call compiled the extra module, once
+    assert r["st"] == [pyc.PYC_E_CUDA, pyc.PYC_E_CUDA]  # then needed a GPU

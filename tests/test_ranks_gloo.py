@@ -191,3 +191,71 @@ def test_shard_bounds_partition():
             assert min(lens) >= 0 and max(lens) - min(lens) <= 1
     with pytest.raises(ValueError):
         shard_bounds(5, 0)
+
+
+def test_segment_bounds_balance_and_cover():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from paper_1304_5553_gb300 import inputs
+    from paper_1304_5553_gb300.shard import segment_bounds
+    lens = inputs.segment_lengths()  # the 20,000-segment table
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    for world in (1, 2, 3, 8):
+        b = segment_bounds(off, world)
+        assert b[0] == 0 and b[-1] == lens.size and all(b[r] <= b[r + 1] for r in range(world))
+        per = [int(off[b[r + 1]] - off[b[r]]) for r in range(world)]
+        assert sum(per) == int(off[-1])
+        # each cut is within one segment (at most 2^20 elements) of its target
+        assert max(per) - min(per) <= 2 * (1 << 20)
+    assert segment_bounds(np.array([0, 5]), 3) in ([0, 0, 1, 1], [0, 1, 1, 1], [0, 0, 0, 1])
+    assert segment_bounds(np.array([7]), 2) == [0, 0, 0]
+
+
+def _segment_worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1304_5553_gb300 import inputs
+    from paper_1304_5553_gb300.shard import segment_bounds
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        lens = inputs.segment_lengths(nseg=300, seed=44, max_log2=12)
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        x = inputs.uniform_f32(44, 0, int(off[-1]), -1.0, 1.0)
+        y = inputs.uniform_f32(44, 1, int(off[-1]), -1.0, 1.0)
+        b = segment_bounds(off, world)
+        s0, s1 = b[rank], b[rank + 1]
+        # this rank's part of the table and arrays (what it would hold on its GPU);
+        # the oracle stands in for pyc_reduce_batched
+        mine = off[s0:s1 + 1] - off[s0]
+        lo, hi = int(off[s0]), int(off[s1])
+        vals, _ = oracle.dot_segments_f32(mine, x[lo:hi], y[lo:hi])
+        out[rank] = (s0, s1, vals.tolist())
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_segmented_batch_shards_without_exchange():
+    """Each rank reduces its own whole segments; together the ranks' results are
+    the unsharded table's, segment for segment (world size 3)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    from paper_1304_5553_gb300 import inputs
+    world = 3
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_segment_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    lens = inputs.segment_lengths(nseg=300, seed=44, max_log2=12)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    x = inputs.uniform_f32(44, 0, int(off[-1]), -1.0, 1.0)
+    y = inputs.uniform_f32(44, 1, int(off[-1]), -1.0, 1.0)
+    whole, _ = oracle.dot_segments_f32(off, x, y)
+    got = np.concatenate([np.array(res[r][2]) for r in range(world)])
+    assert [res[r][0] for r in range(world)] == sorted(res[r][0] for r in range(world))
+    assert got.size == lens.size and np.array_equal(got, whole)
