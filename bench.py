@@ -253,22 +253,31 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
     # L2 full of dirty lines that the dot's misses must write back); the events
     # bracket the dot launch alone (median of 20).  Beside it, cold after a
     # 512 MiB read (L2 holds only clean lines of other data).
+    # Beside them, the same measurement of a one-CTA map over 32 elements: what
+    # any launch costs right after the flush (its code and launch state come
+    # from DRAM too), the floor under the dot's cold time.
     flush = torch.empty(1 << 27, dtype=torch.float32, device=dev)
+    tiny = pyc.pyc_map_create("float *x", "x[i] = 1.0f")
+    tz = torch.empty(32, dtype=torch.float32, device=dev)
+    ft = lambda: pyc.pyc_map_launch(tiny, 32, [tz.data_ptr()], None, s)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cold, clean = [], []
-    for r in range(46):
-        if r % 2 == 0:
-            flush.fill_(float(r))
-        else:
+    cold, clean, floor = [], [], []
+    for r in range(69):
+        k = r % 3
+        if k == 1:
             flush.sum()
+        else:
+            flush.fill_(float(r))
         a.record()
-        f()
+        (ft if k == 2 else f)()
         b.record()
         torch.cuda.synchronize()
-        if r >= 6:
-            (cold if r % 2 == 0 else clean).append(a.elapsed_time(b))
+        if r >= 9:
+            (cold, clean, floor)[k].append(a.elapsed_time(b))
     ms_c = statistics.median(cold)
     ms_cc = statistics.median(clean)
+    ms_floor = statistics.median(floor)
+    pyc.pyc_map_destroy(tiny)
     res["dot_f32_n2^20"] = {"n": m, "us": round(ms * 1e3, 2),
                             "GB/s": round(8 * m / (ms * 1e-3) / 1e9, 1), "cache": "warm (fits L2)",
                             "launches_per_s": round(1e3 / ms, 1),
@@ -276,6 +285,7 @@ def bench_reductions(torch, pyc, stock, dev, reps=20):
                             "cold_us": round(ms_c * 1e3, 2),
                             "cold_GB/s": round(8 * m / (ms_c * 1e-3) / 1e9, 1),
                             "cold_after_read_flush_us": round(ms_cc * 1e3, 2),
+                            "cold_launch_floor_us": round(ms_floor * 1e3, 2),
                             "config": "vec%d_u%d_b%d" % pyc.launch_config(h, m, reduce=True)}
     del g, flush
     return res

@@ -158,6 +158,7 @@ def test_lin_comb_full_size(bf16):
         dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
     dz = torch.empty_like(dx)
     h = stock.create("lin_comb_bf16" if bf16 else "lin_comb_f32")
+    pyc.pyc_map_autotune(h, n, _stream())  # as the benchmark does before timing
     pyc.pyc_map_launch(h, n, [dx.data_ptr(), dy.data_ptr(), dz.data_ptr()],
                        pyc.pack_scalars(h, [A, B]), _stream())
     torch.cuda.synchronize()
@@ -183,11 +184,14 @@ def test_lin_comb_full_size(bf16):
 
 
 def test_gauss_sin_full_size_sampled():
+    """n = 2^28 in the launch configuration the benchmark times (tuned first):
+    sampled elements and both ends within the derived bound."""
     n = 1 << 28
     arrs = [inputs.uniform_f32(1, s, n, -2.0, 2.0) for s in range(4)]
     dev = [torch.from_numpy(a).cuda() for a in arrs]
     dz = torch.empty_like(dev[0])
     h = stock.create("gauss_sin_f32")
+    pyc.pyc_map_autotune(h, n, _stream())
     pyc.pyc_map_launch(h, n, [d.data_ptr() for d in dev] + [dz.data_ptr()], None, _stream())
     torch.cuda.synchronize()
     z = dz.cpu().numpy()

@@ -167,11 +167,15 @@ def test_every_variant(vec, unroll, block):
 
 
 def test_dot_small_config():
-    """Listing 3b at n = 2^20, uniform[-1,1) from seed 0 (streams 0 and 1)."""
+    """Listing 3b at n = 2^20, uniform[-1,1) from seed 0 (streams 0 and 1), in
+    the default and in the tuned configuration the benchmark times."""
     n = 1 << 20
     x = inputs.uniform_f32(0, 0, n, -1.0, 1.0)
     y = inputs.uniform_f32(0, 1, n, -1.0, 1.0)
     ref, ab = oracle.dot_f32(x, y)
+    r = _reduce("dot_f32", [x, y])
+    assert abs(r - ref) <= plain_sum_bound(ab)
+    pyc.pyc_reduce_autotune(stock.create("dot_f32"), n, _s())
     r = _reduce("dot_f32", [x, y])
     assert abs(r - ref) <= plain_sum_bound(ab)
     bx = inputs.to_bf16_values(x)
@@ -184,8 +188,11 @@ def test_dot_small_config():
 
 def test_full_size_reductions():
     """n = 2^28: plain vs compensated binary32 sums of lognormal(0,3) values with
-    random sign, int32 -> int64 sum (bit-exact), max and argmin (bit-exact)."""
+    random sign, int32 -> int64 sum (bit-exact), max and argmin (bit-exact), each
+    in the launch configuration the benchmark times (tuned first)."""
     n = 1 << 28
+    for name in ("sum_f32", "sum_f32_comp", "max_f32", "sum_i32_i64", "argmin_f32"):
+        pyc.pyc_reduce_autotune(stock.create(name), n, _s())
     x = inputs.lognormal_signed_f32(0, 0, n)
     dx = torch.from_numpy(x).cuda()
     exact = oracle.exact_sum_f32(x)

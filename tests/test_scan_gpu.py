@@ -98,8 +98,12 @@ def test_in_place_scan():
 
 
 def test_full_size_scan_sampled():
-    """n = 2^28 binary32 prefix sums: every 4096th element and the last 4096."""
+    """n = 2^28 binary32 prefix sums: every 4096th element and the last 4096;
+    int32 -> int64 exclusive sums, every element.  Both in the launch
+    configuration the benchmark times (tuned first)."""
     n = 1 << 28
+    for name in ("cumsum_f32", "cumsum_excl_i32_i64"):
+        pyc.pyc_scan_autotune(stock.create(name), n, _s())
     x = inputs.uniform_f32(35, 0, n, -1.0, 1.0)
     y = _scan("cumsum_f32", x)
     ref, ab = oracle.scan_sum_f32(x)
