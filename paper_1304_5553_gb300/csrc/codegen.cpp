@@ -999,11 +999,30 @@ __device__ __forceinline__ pyc_out_t pyc_combine_partials(const pyc_acc_t* part,
   acc = pyc_block_reduce(acc, op, z);
   return __double2float_rn(acc.hi + acc.lo);
 }
+// The same for count <= 1 partials held by thread 0 in v (the same arithmetic).
+__device__ __forceinline__ pyc_out_t pyc_combine_partials_reg(const pyc_acc_t v, const int count) {
+  pyc_dd acc; acc.hi = 0.0; acc.lo = 0.0;
+  pyc_dd_op op;
+  if ((int)threadIdx.x < count) {
+    pyc_dd t; t.hi = (double)v.s; t.lo = (double)v.c;
+    acc = op(acc, t);
+  }
+  pyc_dd z; z.hi = 0.0; z.lo = 0.0;
+  acc = pyc_block_reduce(acc, op, z);
+  return __double2float_rn(acc.hi + acc.lo);
+}
 )PYC";
   } else {
     o << R"PYC(__device__ __forceinline__ pyc_out_t pyc_combine_partials(const pyc_acc_t* part, const int count) {
   pyc_acc_t acc = pyc_neutral();
   for (int j = threadIdx.x; j < count; j += blockDim.x) acc = pyc_combine(acc, pyc_ld_cg(part + j));
+  acc = pyc_block_reduce(acc, pyc_combine_op(), pyc_neutral());
+  return pyc_finalize(acc);
+}
+// The same for count <= 1 partials held by thread 0 in v (the same arithmetic).
+__device__ __forceinline__ pyc_out_t pyc_combine_partials_reg(const pyc_acc_t v, const int count) {
+  pyc_acc_t acc = pyc_neutral();
+  if ((int)threadIdx.x < count) acc = pyc_combine(acc, v);
   acc = pyc_block_reduce(acc, pyc_combine_op(), pyc_neutral());
   return pyc_finalize(acc);
 }
@@ -1070,12 +1089,25 @@ __device__ __forceinline__ pyc_out_t pyc_combine_records(const pyc_record* rec, 
   o << "static_assert(sizeof(pyc_record) == 16, \"record size\");\n";
   o << R"PYC(
 // Single reduction: CTAs take chunks c = blockIdx.x, blockIdx.x + gridDim.x, ...;
-// the last CTA to arrive combines the partials and resets the ticket.
+// the last CTA to arrive combines the partials and resets the ticket.  A launch
+// of one CTA with at most one chunk (n up to one tile) skips both.
 template <int VB, int U>
 __device__ __forceinline__ void pyc_reduce_body(const pyc_args& pyc_p, const pyc_i64 n,
     const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 nchunks,
     pyc_acc_t* __restrict__ part, unsigned* __restrict__ ticket, pyc_out_t* __restrict__ out) {
   __shared__ unsigned pyc_last;
+  if (gridDim.x == 1 && nchunks <= 1) {
+    // one CTA and at most one chunk: its partial is the only one, so it is
+    // combined where it is, with no partial slot, ticket or second read
+    pyc_acc_t v = pyc_neutral();
+    if (nchunks == 1) {
+      v = pyc_chunk<VB, U>(pyc_p, n, head, chunk, 0, threadIdx.x, blockDim.x);
+      v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
+    }
+    const pyc_out_t r = pyc_combine_partials_reg(v, (int)nchunks);
+    if (threadIdx.x == 0) *out = r;
+    return;
+  }
   for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     pyc_acc_t v = pyc_chunk<VB, U>(pyc_p, n, head, chunk, c, threadIdx.x, blockDim.x);
     v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());

@@ -187,3 +187,20 @@ def test_full_size_two_shards():
     d = torch.from_numpy(xa).cuda()
     _, out = _sharded(h_arg, [d], [0, cut, n])
     assert (_f32(out), _i64(out, 8)) == oracle.argmin_f32(xa)
+
+
+def test_a_thousand_shards(data):
+    """1,000 uneven shards (some empty): the combine folds more records than it
+    has threads (256), still exactly for integer sums and argmin, and within the
+    compensated bound for the compensated sum."""
+    rng = np.random.default_rng(77)
+    cuts = [0] + sorted(int(c) for c in rng.integers(0, N + 1, 999)) + [N]
+    d = data["d"]
+    _, out = _sharded("sum_i32_i64", [d["xi"]], cuts)
+    assert _i64(out) == oracle.sum_i32_i64(data["xi"])
+    xa = _extremes(data["xu"], cuts, -2.5)
+    _, out = _sharded("argmin_f32", [torch.from_numpy(xa).cuda()], cuts)
+    assert (_f32(out), _i64(out, 8)) == oracle.argmin_f32(xa)
+    _, out = _sharded("sum_f32_comp", [d["x"]], cuts)
+    ex = oracle.exact_sum_f32(data["x"])
+    assert abs(_f32(out) - ex) <= compensated_sum_bound(ex, oracle.sum_f32(data["x"])[1])
