@@ -47,12 +47,14 @@ int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 
 // Row groups per warp in a vector tile.  A tile is read twice (fold, then
 // scan), the second time from L2, and a CTA holds two tiles' input and one
-// tile's output at a time, so one tile's input is kept to 3/16 of L2 over the
-// resident CTAs; within that, tiles are made as large as possible (fewer
-// look-backs) while leaving at least four tiles per CTA.
+// tile's output at a time, so one tile's input is kept to 5/32 of L2 over the
+// resident CTAs (of 4/32, 5/32 and 6/32, the fastest for the int32 -> int64
+// scan and as fast as 6/32 for the binary32 scans); within that, tiles are made
+// as large as possible (fewer look-backs) while leaving at least four tiles per
+// CTA.
 int scan_groups(int64_t n, int64_t base, int resident, int elem_bytes, int64_t l2_bytes) {
   int64_t want = n / (4 * (int64_t)resident);
-  if (elem_bytes > 0) want = std::min<int64_t>(want, l2_bytes * 3 / 16 / resident / elem_bytes);
+  if (elem_bytes > 0) want = std::min<int64_t>(want, l2_bytes * 5 / 32 / resident / elem_bytes);
   return (int)std::max<int64_t>(1, std::min<int64_t>(64, want / base));
 }
 
