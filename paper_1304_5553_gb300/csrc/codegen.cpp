@@ -1096,22 +1096,20 @@ __device__ __forceinline__ void pyc_reduce_body(const pyc_args& pyc_p, const pyc
     const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 nchunks,
     pyc_acc_t* __restrict__ part, unsigned* __restrict__ ticket, pyc_out_t* __restrict__ out) {
   __shared__ unsigned pyc_last;
-  if (gridDim.x == 1 && nchunks <= 1) {
-    // one CTA and at most one chunk: its partial is the only one, so it is
-    // combined where it is, with no partial slot, ticket or second read
-    pyc_acc_t v = pyc_neutral();
-    if (nchunks == 1) {
-      v = pyc_chunk<VB, U>(pyc_p, n, head, chunk, 0, threadIdx.x, blockDim.x);
-      v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
-    }
-    const pyc_out_t r = pyc_combine_partials_reg(v, (int)nchunks);
-    if (threadIdx.x == 0) *out = r;
-    return;
-  }
+  // one CTA and at most one chunk: its partial is the only one, so it is
+  // combined where it is, with no partial slot, ticket or second read
+  const bool pyc_solo = gridDim.x == 1 && nchunks <= 1;
+  pyc_acc_t pyc_v1 = pyc_neutral();
   for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     pyc_acc_t v = pyc_chunk<VB, U>(pyc_p, n, head, chunk, c, threadIdx.x, blockDim.x);
     v = pyc_block_reduce(v, pyc_combine_op(), pyc_neutral());
-    if (threadIdx.x == 0) part[c] = v;
+    if (pyc_solo) pyc_v1 = v;
+    else if (threadIdx.x == 0) part[c] = v;
+  }
+  if (pyc_solo) {
+    const pyc_out_t r = pyc_combine_partials_reg(pyc_v1, (int)nchunks);
+    if (threadIdx.x == 0) *out = r;
+    return;
   }
   // thread 0 stored every partial of this CTA; its arrival publishes them
   if (threadIdx.x == 0) pyc_last = pyc_ticket_arrive(ticket) == gridDim.x - 1 ? 1u : 0u;
