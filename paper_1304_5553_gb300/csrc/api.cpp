@@ -140,19 +140,27 @@ std::string bounds_defines() {
   return d;
 }
 
-void check_bounds_record(HandleBase& h) {
+void check_bounds_record(HandleBase& h, pyc::Module* extra) {
   if (!h.bounds) fail(PYC_E_ARG, "the handle is not a bounds-checked build (opts.debug_bounds)");
   const Driver& d = drv();
   ensure_context();
   PYC_CU(d.cuCtxSynchronize());
-  size_t bytes = 0;
-  CUdeviceptr rec = h.mod->global("pyc_bounds_rec", &bytes);
-  if (bytes != 32) fail(PYC_E_INTERNAL, "unexpected size of the bounds record");
+  // every unit holds a record of its own: read them all, clear those that are set
   unsigned long long r[4] = {0, 0, 0, 0};
-  PYC_CU(d.cuMemcpyDtoH(r, rec, sizeof(r)));
+  for (pyc::Module* m : {h.mod.get(), extra}) {
+    if (!m) continue;
+    size_t bytes = 0;
+    for (CUdeviceptr rec : m->globals("pyc_bounds_rec", &bytes)) {
+      if (bytes != 32) fail(PYC_E_INTERNAL, "unexpected size of the bounds record");
+      unsigned long long q[4] = {0, 0, 0, 0};
+      PYC_CU(d.cuMemcpyDtoH(q, rec, sizeof(q)));
+      if (q[0] == 0) continue;
+      if (r[0] == 0) std::memcpy(r, q, sizeof(r));
+      const unsigned long long z[4] = {0, 0, 0, 0};
+      PYC_CU(d.cuMemcpyHtoD(rec, z, sizeof(z)));
+    }
+  }
   if (r[0] == 0) return;
-  const unsigned long long z[4] = {0, 0, 0, 0};
-  PYC_CU(d.cuMemcpyHtoD(rec, z, sizeof(z)));
   static const char* what[] = {"?", "vector load", "vector store", "element load",
                                "element store", "vector access"};
   const unsigned code = r[0] < 6 ? (unsigned)r[0] : 0u;
@@ -326,7 +334,12 @@ PYC_API pyc_status pyc_map_check_bounds(pyc_map_t h) {
 PYC_API pyc_status pyc_reduce_check_bounds(pyc_reduce_t h) {
   return guarded([&] {
     if (!h) fail(PYC_E_ARG, "handle is NULL");
-    check_bounds_record(*h);
+    std::shared_ptr<pyc::Module> ext;
+    {
+      std::lock_guard<std::mutex> lk(h->ext_mu);
+      ext = h->mod_ext;
+    }
+    check_bounds_record(*h, ext.get());
   });
 }
 

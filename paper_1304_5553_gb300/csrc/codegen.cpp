@@ -19,6 +19,7 @@
 //    (chunks of large segments) and warp bundles (one small segment per warp);
 //    a per-segment ticket lets the last chunk of each segment finish it.
 #include "codegen.h"
+#include "kcache.h"
 
 #include <sstream>
 
@@ -762,10 +763,13 @@ __device__ __forceinline__ void pyc_map_batched_body(const pyc_mtask* __restrict
   g.task_off_chunk = off + 16;
   g.task_bytes = off + 24;
   o << "static_assert(sizeof(pyc_mtask) == " << g.task_bytes << ", \"task layout\");\n";
+  // one compilation unit per kernel (kUnitMark): NVRTC compiles them in parallel
   for (auto& v : all_variants()) {
+    o << kUnitMark;
     o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_map_" << tag << "_"
       << variant_suffix(v) << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 pyc_head) {\n"
       << "  pyc_map_body<" << v.vec_bytes << ", " << v.unroll << ">(pyc_p, n, pyc_head);\n}\n";
+    o << kUnitMark;
     o << "extern \"C\" __global__ void __launch_bounds__(512) pyc_mbatch_" << tag << "_"
       << variant_suffix(v)
       << "(const pyc_mtask* tasks, const pyc_mitem* items, const int nitems, unsigned* ctl) {\n"
@@ -1247,20 +1251,24 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
 )PYC";
   // Entry points: the main module holds the single and batched reductions; the
   // extra module, compiled on first use, the sharded reduction, the combine of
-  // shard records and the register-lean batched builds.
+  // shard records and the register-lean batched builds.  One compilation unit
+  // per kernel (kUnitMark): NVRTC compiles them in parallel.
   std::ostringstream m, x;
   for (auto& v : all_variants()) {
     std::string sfx = variant_suffix(v);
+    m << kUnitMark;
     m << "extern \"C\" __global__ void __launch_bounds__(512) pyc_reduce_" << tag << "_" << sfx
       << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 head, const pyc_i64 chunk, "
          "const pyc_i64 nchunks, pyc_acc_t* part, unsigned* ticket, pyc_out_t* out) {\n"
       << "  pyc_reduce_body<" << v.vec_bytes << ", " << v.unroll
       << ">(pyc_p, n, head, chunk, nchunks, part, ticket, out);\n}\n";
+    m << kUnitMark;
     m << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rbatch_" << tag << "_" << sfx
       << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
          "unsigned* tickets, unsigned* ctl) {\n"
       << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll << ", " << v.unroll
       << ">(tasks, items, nitems, part, tickets, ctl);\n}\n";
+    x << kUnitMark;
     x << "extern \"C\" __global__ void __launch_bounds__(512) pyc_rshard_" << tag << "_" << sfx
       << "(const pyc_args pyc_p, const pyc_i64 n, const pyc_i64 base, const pyc_i64 len, "
          "const pyc_i64 head, const pyc_i64 chunk, const pyc_i64 nchunks, pyc_acc_t* part, "
@@ -1270,13 +1278,15 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
     // register-lean build of the 16-byte variants (a tuning candidate): at most
     // kLeanRegs registers, so more CTAs -- and more loads in flight -- per SM
     if (v.vec_bytes == 16)
-      x << "extern \"C\" __global__ void __maxnreg__(" << kLeanRegs << ") pyc_rbatch_" << tag << "_"
+      x << kUnitMark
+        << "extern \"C\" __global__ void __maxnreg__(" << kLeanRegs << ") pyc_rbatch_" << tag << "_"
         << sfx << "_r" << kLeanRegs
         << "(const pyc_task* tasks, const pyc_item* items, const int nitems, pyc_acc_t* part, "
            "unsigned* tickets, unsigned* ctl) {\n"
         << "  pyc_batched_body<" << v.vec_bytes << ", " << v.unroll
         << ", 1>(tasks, items, nitems, part, tickets, ctl);\n}\n";
   }
+  x << kUnitMark;
   x << "extern \"C\" __global__ void __launch_bounds__(" << kCombineBlock << ") pyc_rcomb_" << tag
     << "(const pyc_record* rec, const pyc_i64 k, pyc_out_t* out) {\n"
        "  const pyc_out_t r = pyc_combine_records(rec, k);\n"
@@ -1896,8 +1906,10 @@ __device__ __forceinline__ void pyc_scan_body(const pyc_args& pyc_p, const pyc_s
 }
 
 )PYC";
+  // one compilation unit per kernel (kUnitMark): NVRTC compiles them in parallel
   for (auto& v : all_variants()) {
     std::string sfx = variant_suffix(v);
+    o << kUnitMark;
     o << "extern \"C\" __global__ void __launch_bounds__(544) pyc_scan_" << tag << "_" << sfx
       << "(const pyc_args pyc_p, const pyc_scan_params S) {\n"
       << "  pyc_scan_body<" << v.vec_bytes << ", " << v.unroll << ">(pyc_p, S);\n}\n";

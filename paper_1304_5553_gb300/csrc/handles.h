@@ -111,10 +111,12 @@ namespace pyc {
 // the defines placed before the generated source of such a build.
 bool bounds_requested(const pyc_opts& o);
 std::string bounds_defines();
-// Synchronise the context, then read and clear the first recorded violation of
-// a checked handle's module in the current context: returns normally if there
-// was none, else fails with PYC_E_INTERNAL describing it.
-void check_bounds_record(HandleBase& h);
+// Synchronise the context, then read and clear the violations recorded by a
+// checked handle's kernels in the current context -- every unit of its module
+// and of `extra` (a map-reduce handle's second module, if compiled): returns
+// normally if there were none, else fails with PYC_E_INTERNAL describing the
+// first one found.
+void check_bounds_record(HandleBase& h, pyc::Module* extra = nullptr);
 
 // Maximum number of chunks of one reduction (bounds the partial workspace).
 constexpr int64_t kMaxChunks = 4096;

@@ -12,6 +12,7 @@
 #include <fstream>
 #include <future>
 #include <sstream>
+#include <thread>
 
 #include "common.h"
 #include "cudrv.h"
@@ -94,7 +95,7 @@ std::map<std::string, std::shared_future<std::shared_ptr<Module>>> g_inflight;
 std::vector<std::shared_ptr<Module>>* g_recent = new std::vector<std::shared_ptr<Module>>();
 
 const char* kArch = "sm_103a";
-const char* kLibTag = "pyc-0.1-t1";
+const char* kLibTag = "pyc-0.1-t2";
 
 std::string read_file(const std::string& path, bool* ok) {
   std::ifstream f(path, std::ios::binary);
@@ -116,33 +117,67 @@ void mkdirs(const std::string& path) {
   }
 }
 
-// On-disk record: magic, key text length + text, cubin length + bytes.  The
-// full key text (source + options) is compared on read, so a hash collision
-// can never return the wrong binary.
-std::string pack_record(const std::string& key_text, const std::string& cubin) {
-  std::string r = "PYCK1\n";
+// On-disk record: magic, key text length + text, number of units, then each
+// unit's cubin length + bytes.  The full key text (source + options) is
+// compared on read, so a hash collision can never return the wrong binary.
+std::string pack_record(const std::string& key_text, const std::vector<std::string>& cubins) {
+  std::string r = "PYCK2\n";
   r += std::to_string(key_text.size()) + "\n" + key_text;
-  r += std::to_string(cubin.size()) + "\n" + cubin;
+  r += std::to_string(cubins.size()) + "\n";
+  for (const auto& c : cubins) r += std::to_string(c.size()) + "\n" + c;
   return r;
 }
 
-bool unpack_record(const std::string& r, const std::string& key_text, std::string* cubin) {
-  if (r.compare(0, 6, "PYCK1\n") != 0) return false;
+bool unpack_record(const std::string& r, const std::string& key_text,
+                   std::vector<std::string>* cubins) {
+  if (r.compare(0, 6, "PYCK2\n") != 0) return false;
   size_t p = 6;
-  size_t nl = r.find('\n', p);
-  if (nl == std::string::npos) return false;
-  size_t klen = std::strtoull(r.c_str() + p, nullptr, 10);
-  p = nl + 1;
-  if (p + klen > r.size() || r.compare(p, klen, key_text) != 0 || klen != key_text.size())
+  auto number = [&](size_t* v) {
+    const size_t nl = r.find('\n', p);
+    if (nl == std::string::npos || nl == p || nl - p > 19) return false;
+    for (size_t q = p; q < nl; ++q)
+      if (r[q] < '0' || r[q] > '9') return false;
+    *v = std::strtoull(r.c_str() + p, nullptr, 10);
+    p = nl + 1;
+    return true;
+  };
+  size_t klen = 0, count = 0;
+  if (!number(&klen) || klen != key_text.size() || p + klen > r.size() ||
+      r.compare(p, klen, key_text) != 0)
     return false;
   p += klen;
-  nl = r.find('\n', p);
-  if (nl == std::string::npos) return false;
-  size_t clen = std::strtoull(r.c_str() + p, nullptr, 10);
-  p = nl + 1;
-  if (p + clen != r.size()) return false;
-  *cubin = r.substr(p, clen);
+  if (!number(&count) || count == 0 || count > 1024) return false;
+  std::vector<std::string> out;
+  for (size_t u = 0; u < count; ++u) {
+    size_t clen = 0;
+    if (!number(&clen) || clen > r.size() - p) return false;
+    out.push_back(r.substr(p, clen));
+    p += clen;
+  }
+  if (p != r.size()) return false;
+  *cubins = std::move(out);
   return true;
+}
+
+// The units of `source` (see kUnitMark): each unit's full text and its own part.
+void split_units(const std::string& source, std::vector<std::string>* text,
+                 std::vector<std::string>* own) {
+  const std::string mark = kUnitMark;
+  size_t p = source.find(mark);
+  if (p == std::string::npos) {
+    text->push_back(source);
+    own->push_back(source);
+    return;
+  }
+  const std::string common = source.substr(0, p);
+  while (p != std::string::npos) {
+    const size_t b = p + mark.size();
+    const size_t e = source.find(mark, b);
+    std::string mine = source.substr(b, e == std::string::npos ? std::string::npos : e - b);
+    text->push_back(common + mine);
+    own->push_back(std::move(mine));
+    p = e;
+  }
 }
 
 std::string compile_nvrtc(const std::string& source, bool fmad) {
@@ -171,6 +206,37 @@ std::string compile_nvrtc(const std::string& source, bool fmad) {
   nv.cubin(prog, &cubin[0]);
   nv.destroy(&prog);
   return cubin;
+}
+
+// Compile every unit, up to one thread per unit and hardware thread; the first
+// failure (in unit order) is rethrown after all threads have finished.
+std::vector<std::string> compile_units(const std::vector<std::string>& text, bool fmad) {
+  const size_t n = text.size();
+  std::vector<std::string> cubins(n);
+  if (n == 1) {
+    cubins[0] = compile_nvrtc(text[0], fmad);
+    return cubins;
+  }
+  std::vector<std::exception_ptr> errs(n);
+  std::atomic<size_t> next{0};
+  auto work = [&] {
+    for (size_t u; (u = next.fetch_add(1)) < n;) {
+      try {
+        cubins[u] = compile_nvrtc(text[u], fmad);
+      } catch (...) {
+        errs[u] = std::current_exception();
+      }
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>(n, std::min(hw, 16u));
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  for (auto& e : errs)
+    if (e) std::rethrow_exception(e);
+  return cubins;
 }
 
 }  // namespace
@@ -261,31 +327,32 @@ std::shared_ptr<Module> load_or_compile(const std::string& key, const std::strin
                                         const std::string& source, bool fmad) {
   std::string dir = cache_dir();
   std::string path = dir.empty() ? "" : dir + "/" + key + ".pyck";
-  std::string cubin;
+  std::vector<std::string> text, own, cubins;
+  split_units(source, &text, &own);
   bool have = false;
   if (!path.empty()) {
     bool ok = false;
     std::string rec = read_file(path, &ok);
-    if (ok && unpack_record(rec, key_text, &cubin)) {
+    if (ok && unpack_record(rec, key_text, &cubins) && cubins.size() == text.size()) {
       have = true;
       ++g_disk;
     }
   }
   if (!have) {
-    cubin = compile_nvrtc(source, fmad);
+    cubins = compile_units(text, fmad);
     ++g_compiled;
     if (!path.empty()) {
       mkdirs(dir);
       std::string tmp = path + ".tmp" + std::to_string(getpid());
       {
         std::ofstream f(tmp, std::ios::binary);
-        std::string rec = pack_record(key_text, cubin);
+        std::string rec = pack_record(key_text, cubins);
         f.write(rec.data(), (std::streamsize)rec.size());
       }
       std::rename(tmp.c_str(), path.c_str());  // atomic publish
     }
   }
-  return std::make_shared<Module>(cubin);
+  return std::make_shared<Module>(std::move(cubins), std::move(own));
 }
 
 }  // namespace
@@ -298,33 +365,43 @@ CacheStats cache_stats() {
   return s;
 }
 
+Module::Module(std::vector<std::string> cubins, std::vector<std::string> own_text)
+    : cubins_(std::move(cubins)), own_(std::move(own_text)) {}
+
 Module::~Module() {
   // Modules are unloaded only if the driver is present and the context lives;
   // errors at teardown are ignored on purpose.
-  for (auto& kv : loaded_) {
-    try {
-      drv().cuModuleUnload(kv.second);
-    } catch (...) {
+  for (auto& kv : loaded_)
+    for (CUmodule m : kv.second) {
+      if (!m) continue;
+      try {
+        drv().cuModuleUnload(m);
+      } catch (...) {
+      }
     }
-  }
 }
 
-CUdeviceptr Module::global(const std::string& name, size_t* bytes) {
+CUmodule Module::unit(CUcontext ctx, size_t u) {
+  auto& mods = loaded_[ctx];
+  if (mods.empty()) mods.assign(cubins_.size(), nullptr);
+  if (!mods[u]) PYC_CU(drv().cuModuleLoadData(&mods[u], cubins_[u].data()));
+  return mods[u];
+}
+
+std::vector<CUdeviceptr> Module::globals(const std::string& name, size_t* bytes) {
   CUcontext ctx = ensure_context();
   std::lock_guard<std::mutex> lk(mu_);
-  auto it = loaded_.find(ctx);
-  CUmodule mod;
-  if (it == loaded_.end()) {
-    PYC_CU(drv().cuModuleLoadData(&mod, cubin_.data()));
-    loaded_[ctx] = mod;
-  } else {
-    mod = it->second;
+  std::vector<CUdeviceptr> out;
+  for (size_t u = 0; u < cubins_.size(); ++u) {
+    CUdeviceptr p = 0;
+    size_t b = 0;
+    const CUresult r = drv().cuModuleGetGlobal(&p, &b, unit(ctx, u), name.c_str());
+    if (r == CUDA_ERROR_NOT_FOUND) continue;
+    PYC_CU(r);
+    if (bytes) *bytes = b;
+    out.push_back(p);
   }
-  CUdeviceptr p = 0;
-  size_t b = 0;
-  PYC_CU(drv().cuModuleGetGlobal(&p, &b, mod, name.c_str()));
-  if (bytes) *bytes = b;
-  return p;
+  return out;
 }
 
 CUfunction Module::function(const std::string& name) {
@@ -333,18 +410,24 @@ CUfunction Module::function(const std::string& name) {
   auto fk = std::make_pair(ctx, name);
   auto fit = funcs_.find(fk);
   if (fit != funcs_.end()) return fit->second;
-  auto it = loaded_.find(ctx);
-  CUmodule mod;
-  if (it == loaded_.end()) {
-    PYC_CU(drv().cuModuleLoadData(&mod, cubin_.data()));
-    loaded_[ctx] = mod;
-  } else {
-    mod = it->second;
+  // the unit whose own text defines the kernel, else every unit in turn
+  const std::string call = name + "(";
+  std::vector<size_t> order;
+  for (size_t u = 0; u < own_.size(); ++u)
+    if (own_[u].find(call) != std::string::npos) order.push_back(u);
+  for (size_t u = 0; u < cubins_.size(); ++u) order.push_back(u);
+  CUresult last = CUDA_ERROR_NOT_FOUND;
+  for (size_t u : order) {
+    CUfunction f;
+    last = drv().cuModuleGetFunction(&f, unit(ctx, u), name.c_str());
+    if (last == CUDA_SUCCESS) {
+      funcs_[fk] = f;
+      return f;
+    }
+    if (last != CUDA_ERROR_NOT_FOUND) break;
   }
-  CUfunction f;
-  PYC_CU(drv().cuModuleGetFunction(&f, mod, name.c_str()));
-  funcs_[fk] = f;
-  return f;
+  PYC_CU(last);
+  return nullptr;
 }
 
 }  // namespace pyc

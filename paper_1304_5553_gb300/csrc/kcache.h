@@ -14,22 +14,31 @@
 
 namespace pyc {
 
-// A compiled module (sm_103a CUBIN) and its per-context loaded copies.
+// Separates the units of a generated source: the text before the first mark
+// is common to every unit, and each unit (common text + its own text) is an
+// NVRTC program of its own, so the units of one source compile in parallel.
+// A source without the mark is one unit.
+constexpr const char* kUnitMark = "\n//@@pyc-unit\n";
+
+// A compiled module: one sm_103a CUBIN per unit and the per-context loaded
+// copies (a unit is loaded when a kernel it holds is first asked for).
 class Module {
  public:
-  explicit Module(std::string cubin) : cubin_(std::move(cubin)) {}
+  // own_text[u]: unit u's own text, where its kernels' names appear as "name("
+  Module(std::vector<std::string> cubins, std::vector<std::string> own_text);
   ~Module();
-  // Function `name` in the current context (loads the module on first use).
+  // Function `name` in the current context.
   CUfunction function(const std::string& name);
-  // Device address and size of the module-scope variable `name` in the current
-  // context (loads the module on first use).
-  CUdeviceptr global(const std::string& name, size_t* bytes);
-  const std::string& cubin() const { return cubin_; }
+  // Device address of the module-scope variable `name` in every unit that
+  // defines it, in the current context (loads every unit); *bytes its size.
+  std::vector<CUdeviceptr> globals(const std::string& name, size_t* bytes);
+  size_t units() const { return cubins_.size(); }
 
  private:
-  std::string cubin_;
+  CUmodule unit(CUcontext ctx, size_t u);  // mu_ held
+  std::vector<std::string> cubins_, own_;
   std::mutex mu_;
-  std::map<CUcontext, CUmodule> loaded_;
+  std::map<CUcontext, std::vector<CUmodule>> loaded_;
   std::map<std::pair<CUcontext, std::string>, CUfunction> funcs_;
 };
 

@@ -247,6 +247,43 @@ def test_kernel_cache_checks_the_full_key(tmp_path):
     assert run("z[i] = 5 * x[i]")["disk_hits"] == 1
 
 
+def test_kernel_cache_units(tmp_path):
+    """A generated source is split into one NVRTC unit per kernel (compiled in
+    parallel); its cache record holds one binary per unit, and a record cut
+    short inside a unit is ignored and rewritten."""
+    env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
+    code = _CACHE_CHILD % ROOT
+
+    def run(stmt):
+        out = subprocess.run([sys.executable, "-c", code, stmt], env=env, capture_output=True,
+                             text=True, check=True).stdout
+        return json.loads(out.strip().splitlines()[-1])
+
+    assert run("z[i] = 7 * x[i]")["compiled"] == 1
+    (f,) = [g for g in os.listdir(tmp_path) if g.endswith(".pyck")]
+    path = os.path.join(tmp_path, f)
+    data = open(path, "rb").read()
+    assert data.startswith(b"PYCK2\n")
+    p = 6
+    nl = data.index(b"\n", p)
+    klen = int(data[p:nl])
+    key = data[nl + 1:nl + 1 + klen]
+    p = nl + 1 + klen
+    nl = data.index(b"\n", p)
+    units = int(data[p:nl])
+    # six variants, each a single map and a batched map kernel
+    assert units == 12 and key.count(b"\n//@@pyc-unit\n") == 12
+    p = nl + 1
+    for _ in range(units):
+        nl = data.index(b"\n", p)
+        p = nl + 1 + int(data[p:nl])
+    assert p == len(data)
+    open(path, "wb").write(data[:-100])
+    r = run("z[i] = 7 * x[i]")
+    assert r["compiled"] == 1 and r["disk_hits"] == 0
+    assert run("z[i] = 7 * x[i]")["disk_hits"] == 1
+
+
 def test_front_end_params():
     k = pyc.ElementwiseKernel("float a, float *x, float b, float *y, float *z",
                               "z[i] = a*x[i] + b*y[i]", "linear_combination")

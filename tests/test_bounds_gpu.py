@@ -197,5 +197,13 @@ def test_narrowed_ranges_make_the_checks_fire(monkeypatch):
     with pytest.raises(pyc.PycError) as e:
         pyc.pyc_reduce_check_bounds(r)
     assert e.value.status == pyc.PYC_E_INTERNAL and "load" in e.value.message
+    pyc.pyc_reduce_check_bounds(r)  # cleared
+    # a sharded launch runs in the handle's second module, whose records are read too
+    rec = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    pyc.pyc_reduce_shard(r, n, 100, n - 100, [x.data_ptr() + 400], None, rec.data_ptr(), _s())
+    with pytest.raises(pyc.PycError) as e:
+        pyc.pyc_reduce_check_bounds(r)
+    assert e.value.status == pyc.PYC_E_INTERNAL and "load" in e.value.message
+    pyc.pyc_reduce_check_bounds(r)
     pyc.pyc_map_destroy(h)
     pyc.pyc_reduce_destroy(r)
