@@ -55,6 +55,39 @@ def test_int_segments_exact_and_sum_of_segments():
     assert int(s_out.sum().item()) == oracle.sum_i32_i64(xi)
 
 
+def test_segments_beyond_2e31_elements():
+    """2^31 + 100003 int32 elements in segments whose offsets, lengths and
+    chunks pass 2^31 (one segment of ~2^31 elements, an empty one at 2^31 - 3,
+    one of a single element after 2^31), summed into int64 exactly.  The input
+    is 1 everywhere except two windows of seeded values in [-2^30, 2^30), so a
+    segment's sum is P(b) - P(a), P(i) the ones before i plus the windows'
+    elements before i (each window summed by the oracle)."""
+    n = (1 << 31) + 100003
+    wins = [((1 << 31) - 70000, (1 << 31) + 70001), (n - 3000, n)]
+    x = torch.ones(n, dtype=torch.int32, device="cuda")
+    vals = []
+    for k, (a, b) in enumerate(wins):
+        v = inputs.int_uniform_i32(38, k, b - a, -(1 << 30), 1 << 30)
+        x[a:b] = torch.from_numpy(v).cuda()
+        vals.append(v)
+
+    def prefix(i):
+        s = i
+        for (a, b), v in zip(wins, vals):
+            m = min(max(i - a, 0), b - a)
+            s += oracle.sum_i32_i64(v[:m]) - m
+        return s
+
+    off = np.array([0, 100, (1 << 31) - 3, (1 << 31) - 3, (1 << 31) + 40000, (1 << 31) + 40001,
+                    n - 1500, n], np.int64)
+    out, _, _ = _batched("sum_i32_i64", off, [x], out_dtype=torch.int64)
+    got = out[:, 0].cpu().numpy()
+    want = [prefix(int(b)) - prefix(int(a)) for a, b in zip(off[:-1], off[1:])]
+    assert [int(g) for g in got] == want
+    del x
+    torch.cuda.empty_cache()
+
+
 def test_argmin_segments_exact():
     lens = inputs.segment_lengths(nseg=500, seed=13, max_log2=18)
     off = _offsets(lens)

@@ -116,6 +116,49 @@ def test_full_size_scan_sampled():
     torch.cuda.empty_cache()
 
 
+def test_scan_beyond_2e31_elements():
+    """n = 2^31 + 100003: int32 -> int64 exclusive prefix sums whose element
+    indices, tile offsets and look-back windows pass 2^31 (8.6 GB in, 17.2 GB
+    out).  The input is 1 everywhere except two windows of seeded values in
+    [-2^30, 2^30) (one across 2^31, one at the end), so every prefix has a
+    closed form: the ones before i plus the windows' elements before i."""
+    n = (1 << 31) + 100003
+    wins = [((1 << 31) - 70000, (1 << 31) + 70001), (n - 3000, n)]
+    x = torch.ones(n, dtype=torch.int32, device="cuda")
+    vals, cums = [], []
+    for k, (a, b) in enumerate(wins):
+        v = inputs.int_uniform_i32(36, k, b - a, -(1 << 30), 1 << 30)
+        x[a:b] = torch.from_numpy(v).cuda()
+        vals.append(v)
+        cums.append(np.concatenate([[0], np.cumsum(v.astype(np.int64))]))
+    h = stock.create("cumsum_excl_i32_i64")
+    y = torch.full((n,), -7, dtype=torch.int64, device="cuda")
+    pyc.pyc_scan_launch(h, n, [x.data_ptr(), y.data_ptr()], None, _s())
+    pyc.pyc_scan_sync(h, _s())
+
+    def want(i):
+        s = i
+        for (a, b), c in zip(wins, cums):
+            m = min(max(i - a, 0), b - a)
+            s += int(c[m]) - m
+        return s
+
+    # each window element by element: the closed form at its start plus the
+    # oracle's exclusive prefix of the window
+    for (a, b), v in zip(wins, vals):
+        ref = want(a) + oracle.scan_sum_i32_i64(v, exclusive=True)
+        assert np.array_equal(y[a:b].cpu().numpy(), ref), (a, b)
+    idx = np.unique(np.concatenate([
+        np.random.default_rng(37).integers(0, n, 4096),
+        [0, 1, 2, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, n - 1],
+        np.arange((1 << 31) - 70000 - 2048, (1 << 31) - 70000 + 2048)]))
+    got = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+    bad = [(int(i), int(g), want(int(i))) for g, i in zip(got, idx) if int(g) != want(int(i))]
+    assert not bad, bad[:5]
+    del x, y
+    torch.cuda.empty_cache()
+
+
 def _affine_inputs(seed, n):
     rng = np.random.default_rng(seed)
     a = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
