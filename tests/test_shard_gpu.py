@@ -204,3 +204,34 @@ def test_a_thousand_shards(data):
     _, out = _sharded("sum_f32_comp", [d["x"]], cuts)
     ex = oracle.exact_sum_f32(data["x"])
     assert abs(_f32(out) - ex) <= compensated_sum_bound(ex, oracle.sum_f32(data["x"])[1])
+
+
+def test_shards_beyond_2e31_elements():
+    """n = 2^31 + 100003: shards that start and end on either side of 2^31.
+    An argmin's record carries the global index (above 2^31, first of two
+    equal minima), an int32 sum's record its shard's int64 sum; the combine
+    gives the whole range's.  Inputs are constant except at a few planted
+    elements, so every record is known exactly."""
+    n = (1 << 31) + 100003
+    cuts = [0, (1 << 31) - 1, (1 << 31) + 500, n]
+    x = torch.ones(n, dtype=torch.float32, device="cuda")
+    for i, v in ((5, -2.0), ((1 << 31) + 777, -3.0), ((1 << 31) + 90000, -3.0)):
+        x[i] = v
+    recs, out = _sharded("argmin_f32", [x], cuts)
+    assert [(_f32(r), _i64(r, 8)) for r in recs] == \
+        [(-2.0, 5), (1.0, (1 << 31) - 1), (-3.0, (1 << 31) + 777)]
+    assert (_f32(out), _i64(out, 8)) == (-3.0, (1 << 31) + 777)
+    del x
+    xi = torch.ones(n, dtype=torch.int32, device="cuda")
+    planted = {7: -5, (1 << 31) - 2: 1 << 30, (1 << 31): -(1 << 30), n - 1: 12345}
+    for i, v in planted.items():
+        xi[i] = v
+
+    def shard_sum(a, b):
+        return (b - a) + sum(v - 1 for i, v in planted.items() if a <= i < b)
+
+    recs, out = _sharded("sum_i32_i64", [xi], cuts)
+    assert [_i64(r) for r in recs] == [shard_sum(a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+    assert _i64(out) == shard_sum(0, n)
+    del xi
+    torch.cuda.empty_cache()
