@@ -34,6 +34,10 @@ void reduce_shard(pyc_reduce* h, int64_t n_total, int64_t i0, int64_t n, void* c
   if (i0 > n_total || n > n_total - i0) fail(PYC_E_ARG, "shard [i0, i0 + n) exceeds [0, n_total)");
   check_record_ptr(d_rec, "d_rec");
   const ArgSpec& spec = h->spec;
+  // before the pointers are read for the vector head and the offsets below
+  if (spec.num_ptrs > 0 && !ptrs) fail(PYC_E_ARG, "ptrs is NULL but the spec declares arrays");
+  if (spec.scalar_bytes > 0 && !scalars)
+    fail(PYC_E_ARG, "scalars is NULL but the spec declares scalar parameters");
   // A shard holds elements [i0, i0 + n) of every array and nothing else, so
   // the map expression may touch each array only at index i.
   for (const auto& p : spec.params)

@@ -529,6 +529,7 @@ def test_shard_and_combine_argument_errors_need_no_gpu():
     E = pyc.PYC_E_ARG
     h = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i]*y[i]", "float *x, float *y")
     hs = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i+1]-x[i]", "float *x")
+    hk = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "k*x[i]*y[i]", "float k, float *x, float *y")
     p = pyc._ptr_array([1 << 20, 1 << 21])
     rec = 1 << 22
     try:
@@ -543,6 +544,12 @@ def test_shard_and_combine_argument_errors_need_no_gpu():
         assert lib.pyc_reduce_shard(h, 10, 0, 10, pyc._ptr_array([0, 1 << 21]), None, rec,
                                     None) == E
         assert lib.pyc_reduce_shard(None, 10, 0, 10, p, None, rec, None) == E
+        # NULL arrays or scalars for a spec that declares them: argument errors
+        # before the pointers are read
+        assert lib.pyc_reduce_shard(h, 10, 0, 10, None, None, rec, None) == E
+        assert "ptrs is NULL" in pyc.pyc_last_error()
+        assert lib.pyc_reduce_shard(hk, 10, 0, 10, p, None, rec, None) == E
+        assert "scalars is NULL" in pyc.pyc_last_error()
         assert lib.pyc_reduce_combine(h, -1, rec, rec, None) == E
         assert lib.pyc_reduce_combine(h, 2, None, rec, None) == E
         assert lib.pyc_reduce_combine(h, 2, rec + 4, rec, None) == E
@@ -552,6 +559,7 @@ def test_shard_and_combine_argument_errors_need_no_gpu():
     finally:
         pyc.pyc_reduce_destroy(h)
         pyc.pyc_reduce_destroy(hs)
+        pyc.pyc_reduce_destroy(hk)
 
 
 def test_shard_and_combine_kernels_are_generated():
