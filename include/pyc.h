@@ -556,8 +556,9 @@ void pyc_pool_destroy(pyc_pool_t p);
  * pyc_csr_create wraps a CSR matrix already in device memory (the caller owns it
  * and keeps it alive): rowptr int64[nrows + 1] (rowptr[0] = 0, nondecreasing,
  * rowptr[nrows] = nnz), colidx int32[nnz] (each < ncols < 2^31), vals[nnz] of vt
- * (F32 or F64).  Indices are not checked: out-of-range ones are undefined
- * behaviour.  The handle compiles its kernels (cached) and picks T, the lanes per
+ * (F32 or F64).  Every array, here and in the calls below, must be aligned to
+ * its element size, and x, y, b must not be NULL (else PYC_E_ARG).  Indices are
+ * not checked: out-of-range ones are undefined behaviour.  The handle compiles its kernels (cached) and picks T, the lanes per
  * row, from the mean row length. */
 typedef struct pyc_csr* pyc_csr_t;
 pyc_status pyc_csr_create(int64_t nrows, int64_t ncols, int64_t nnz, const void* rowptr,

@@ -652,6 +652,15 @@ void dot_launch(pyc_reduce_t h, int64_t n, CUdeviceptr x, CUdeviceptr y, CUdevic
 
 using namespace pyc;
 
+namespace {
+// Device arrays must be aligned to their element size: a kernel given a
+// misaligned one would fault, so it is an argument error here.
+void check_aligned(const void* p, int64_t bytes, const char* what) {
+  if (reinterpret_cast<uintptr_t>(p) % (uintptr_t)bytes)
+    fail(PYC_E_ARG, std::string(what) + " is not aligned to its element size");
+}
+}  // namespace
+
 PYC_API pyc_status pyc_csr_create(int64_t nrows, int64_t ncols, int64_t nnz, const void* rowptr,
                                   const void* colidx, const void* vals, pyc_dtype vt,
                                   pyc_csr_t* out) {
@@ -663,6 +672,9 @@ PYC_API pyc_status pyc_csr_create(int64_t nrows, int64_t ncols, int64_t nnz, con
     if (vt != PYC_F32 && vt != PYC_F64) fail(PYC_E_ARG, "values are F32 or F64");
     if (nrows > 0 && !rowptr) fail(PYC_E_ARG, "rowptr is NULL");
     if (nnz > 0 && (!colidx || !vals)) fail(PYC_E_ARG, "colidx / vals are NULL");
+    check_aligned(rowptr, 8, "rowptr");
+    check_aligned(colidx, 4, "colidx");
+    check_aligned(vals, vt == PYC_F64 ? 8 : 4, "vals");
     auto a = std::make_unique<pyc_csr>();
     a->nrows = nrows;
     a->ncols = ncols;
@@ -704,6 +716,8 @@ PYC_API pyc_status pyc_spmv(pyc_csr_t a, const void* x, void* y, pyc_stream_t st
   return guarded([&] {
     if (!a) fail(PYC_E_ARG, "matrix is NULL");
     if (a->nrows > 0 && (!x || !y)) fail(PYC_E_ARG, "x / y is NULL");
+    check_aligned(x, vbytes(a->vt), "x");
+    check_aligned(y, vbytes(a->vt), "y");
     launch_spmv(a, a->width, reinterpret_cast<CUdeviceptr>(x), reinterpret_cast<CUdeviceptr>(y),
                 reinterpret_cast<CUstream>(stream));
   });
@@ -713,6 +727,9 @@ PYC_API pyc_status pyc_spmv_autotune(pyc_csr_t a, const void* x, void* y, pyc_st
   return guarded([&] {
     if (!a) fail(PYC_E_ARG, "matrix is NULL");
     if (a->nrows == 0) return;
+    if (!x || !y) fail(PYC_E_ARG, "x / y is NULL");
+    check_aligned(x, vbytes(a->vt), "x");
+    check_aligned(y, vbytes(a->vt), "y");
     CUstream s = reinterpret_cast<CUstream>(stream);
     CUevent e0, e1;
     PYC_CU(drv().cuEventCreate(&e0, CU_EVENT_DEFAULT));
@@ -745,6 +762,8 @@ PYC_API pyc_status pyc_cg_solve(pyc_csr_t a, const void* b, void* x, double rtol
   return guarded([&] {
     if (!a || !b || !x) fail(PYC_E_ARG, "NULL argument");
     if (a->nrows != a->ncols) fail(PYC_E_ARG, "CG needs a square matrix");
+    check_aligned(b, vbytes(a->vt), "b");
+    check_aligned(x, vbytes(a->vt), "x");
     if (!(rtol >= 0) || maxit < 0) fail(PYC_E_ARG, "rtol >= 0 and maxit >= 0");
     const int64_t n = a->nrows;
     CUstream s = reinterpret_cast<CUstream>(stream);

@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library loads and exports every symbol
 include/pyc.h declares; arg-spec parsing, statement analysis, run-time
 compilation (NVRTC needs no GPU), the kernel cache and argument validation."""
+import ctypes
 import json
 import os
 import re
@@ -608,3 +609,29 @@ def test_extra_module_is_compiled_on_first_use(tmp_path):
     assert r["c0"] == 1            # creation compiled the main module only
     assert r["c1"] == 2            # the first shard call compiled the extra module, once
     assert r["st"] == [pyc.PYC_E_CUDA, pyc.PYC_E_CUDA]  # then needed a GPU
+
+
+def test_sparse_null_and_misaligned_arrays_are_argument_errors():
+    """The sparse calls reject NULL vectors and arrays not aligned to their
+    element size (a kernel given one would fault) before any GPU work."""
+    lib = pyc.load()
+    E = pyc.PYC_E_ARG
+    V = ctypes.c_void_p
+    h = ctypes.c_void_p()
+    for vt, vb in ((pyc.PYC_F32, 4), (pyc.PYC_F64, 8)):
+        for rp, ci, va in ((1 << 20, 1 << 21, (1 << 22) + vb // 2), ((1 << 20) + 4, 1 << 21, 1 << 22),
+                           (1 << 20, (1 << 21) + 2, 1 << 22)):
+            assert lib.pyc_csr_create(4, 4, 8, V(rp), V(ci), V(va), vt, ctypes.byref(h)) == E
+            assert "aligned" in pyc.pyc_last_error()
+        a = pyc.pyc_csr_create(4, 4, 8, 1 << 20, 1 << 21, 1 << 22, vt)
+        try:
+            good, odd = 1 << 23, (1 << 23) + vb // 2
+            for x, y in ((None, good), (good, None), (odd, good), (good, odd)):
+                assert lib.pyc_spmv(a, V(x), V(y), None) == E
+                assert lib.pyc_spmv_autotune(a, V(x), V(y), None) == E
+            info = pyc.pyc_cg_info()
+            for b, x in ((None, good), (good, None), (odd, good), (good, odd)):
+                assert lib.pyc_cg_solve(a, V(b), V(x), ctypes.c_double(1e-6), 10, None,
+                                        ctypes.byref(info)) == E
+        finally:
+            pyc.pyc_csr_destroy(a)
