@@ -670,7 +670,9 @@ typedef struct {
 pyc_status pyc_server_create(const pyc_server_cfg* cfg, pyc_server_t* out);
 
 /* Queue a request; *id identifies it until pyc_server_release.  Errors:
- * PYC_E_ARG (bad request), PYC_E_NOMEM (larger than the whole budget),
+ * PYC_E_ARG (bad request: among others a NULL array other than a written-only
+ * map output, or an array not aligned to its element size; checked here, so a
+ * bad request never joins a batch), PYC_E_NOMEM (larger than the whole budget),
  * PYC_E_BUSY (queue full or shutting down). */
 pyc_status pyc_server_submit(pyc_server_t s, const pyc_request* req, uint64_t* id);
 

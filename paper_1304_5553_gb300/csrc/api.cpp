@@ -62,14 +62,16 @@ std::vector<unsigned char> pack_args(const ArgSpec& spec, void* const* ptrs, con
 int64_t vector_head(const ArgSpec& spec, void* const* ptrs, int vec_bytes, int min_bytes,
                     int64_t n) {
   bool any = false;
+  // every array (also one the statement indexes other than as name[i]): a
+  // NULL or misaligned one would fault in the kernel
   for (auto& p : spec.params) {
-    if (!(p.is_ptr && p.lifted)) continue;
+    if (!p.is_ptr) continue;
     uintptr_t a = reinterpret_cast<uintptr_t>(ptrs[p.ptr_slot]);
     int sz = type_info(p.dtype).bytes;
     if (n > 0 && a == 0) fail(PYC_E_ARG, "array '" + p.name + "' is NULL");
     if (a % (uintptr_t)sz)
       fail(PYC_E_ARG, "array '" + p.name + "' is not aligned to its element size");
-    any = true;
+    any = any || p.lifted;
   }
   if (!any) return 0;
   const int span = vec_bytes / min_bytes;

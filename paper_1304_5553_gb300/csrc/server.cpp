@@ -571,12 +571,19 @@ PYC_API pyc_status pyc_server_submit(pyc_server_t s, const pyc_request* req, uin
     r->scalars.assign(spec.scalar_bytes + 8, 0);
     if (spec.scalar_bytes)
       std::memcpy(r->scalars.data(), req->scalars, (size_t)spec.scalar_bytes);
+    // every array is checked here, so that a bad one fails its own request
+    // rather than the batch it would join
     for (auto& p : spec.params) {
-      if (!p.is_ptr || r->ptrs[p.ptr_slot]) continue;
+      if (!p.is_ptr) continue;
+      if (const void* a = r->ptrs[p.ptr_slot]) {
+        if (reinterpret_cast<uintptr_t>(a) % (uintptr_t)type_info(p.dtype).bytes)
+          fail(PYC_E_ARG, "array '" + p.name + "' is not aligned to its element size");
+        continue;
+      }
       bool server_out = req->kind == PYC_REQ_MAP && p.lifted && p.written && !p.read;
       if (server_out)
         r->alloc_slots.push_back(p.ptr_slot);
-      else if (r->n > 0 && p.lifted)
+      else if (r->n > 0)
         fail(PYC_E_ARG, "array '" + p.name + "' is NULL (only written-only map outputs may be)");
     }
     r->bytes = request_bytes(*h, r->n, out_bytes);

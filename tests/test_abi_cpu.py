@@ -635,3 +635,24 @@ def test_sparse_null_and_misaligned_arrays_are_argument_errors():
                                         ctypes.byref(info)) == E
         finally:
             pyc.pyc_csr_destroy(a)
+
+
+def test_every_array_is_checked_before_a_launch():
+    """NULL or misaligned arrays are PYC_E_ARG before any GPU work, also those
+    a statement indexes other than as name[i] (not on the vector path)."""
+    lib = pyc.load()
+    m = pyc.pyc_map_create("float *x, float *y", "y[i] = x[i + 1] - x[i]")
+    r = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "x[i + 1] * y[i]", "float *x, float *y")
+    try:
+        for xp, what in ((0, "is NULL"), ((1 << 20) + 2, "not aligned")):
+            assert lib.pyc_map_launch(m, 10, pyc._ptr_array([xp, 1 << 21]), None,
+                                      None) == pyc.PYC_E_ARG
+            assert what in pyc.pyc_last_error()
+            assert lib.pyc_reduce_launch(r, 10, pyc._ptr_array([xp, 1 << 21]), None, 1 << 22,
+                                         None) == pyc.PYC_E_ARG
+            assert what in pyc.pyc_last_error()
+        # n = 0 launches nothing: a NULL array is allowed there
+        assert lib.pyc_map_launch(m, 0, pyc._ptr_array([0, 0]), None, None) == pyc.PYC_OK
+    finally:
+        pyc.pyc_map_destroy(m)
+        pyc.pyc_reduce_destroy(r)

@@ -190,6 +190,34 @@ def test_deadline_queue_limit_and_errors(pools):
         pyc.pyc_server_destroy(srv)
 
 
+def test_bad_arrays_fail_at_submit_and_spare_the_batch(pools):
+    """A NULL array (other than a written-only map output) or one not aligned to
+    its element size is refused by pyc_server_submit itself, also for an array
+    the statement indexes other than as name[i]; a good request after it runs."""
+    _, dev = pools
+    srv = pyc.pyc_server_create(1 << 30, num_streams=1)
+    diff = pyc.pyc_map_create("float *x, float *y", "y[i] = x[i + 1] - x[i]")
+    try:
+        x, y = dev["x"], dev["y"]
+        out = torch.empty(1000, dtype=torch.float32, device="cuda")
+        bad = [(pyc.PYC_REQ_MAP, diff, [0, out.data_ptr()]),
+               (pyc.PYC_REQ_MAP, diff, [x.data_ptr() + 2, out.data_ptr()]),
+               (pyc.PYC_REQ_REDUCE, stock.create("dot_f32"), [x.data_ptr() + 1, y.data_ptr()]),
+               (pyc.PYC_REQ_REDUCE, stock.create("dot_f32"), [x.data_ptr(), 0])]
+        for kind, h, ptrs in bad:
+            with pytest.raises(pyc.PycError) as e:
+                pyc.pyc_server_submit(srv, pyc.make_request(kind, h, 1000, ptrs))
+            assert e.value.status == pyc.PYC_E_ARG
+        _run_one(srv, pyc.make_request(pyc.PYC_REQ_MAP, diff, 1000, [x.data_ptr(), out.data_ptr()]))
+        want = (x[1:1001] - x[:1000]).cpu()
+        assert torch.equal(out.cpu(), want)
+        st = pyc.pyc_server_get_stats(srv)
+        assert st["failed"] == 0 and st["completed"] == 1
+    finally:
+        pyc.pyc_server_destroy(srv)
+        pyc.pyc_map_destroy(diff)
+
+
 def test_replay_server_and_direct_agree(pools):
     host, dev = pools
     nreq = 3000
