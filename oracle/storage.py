@@ -108,3 +108,40 @@ def map_u8_add_index(x, idx, shift):
     x = np.asarray(x, np.int64)
     idx = np.asarray(idx, np.int64)
     return ((x + ((idx >> shift) & 255)) & 255).astype(np.uint8)
+
+
+# ------------------------------------------------------------------ scans
+# Parallel prefix scans (Sec. 3.2.6) over these storage types, by their plain
+# definitions: out[i] combines x[0], ..., x[i] (inclusive) or x[0], ..., x[i-1]
+# (exclusive, the neutral element at i = 0) in index order.
+
+def scan_sum_int(x, exclusive=False):
+    """Prefix sums of integer values, exact.  The inputs are kept small enough
+    (n * max|x| < 2^62) that no prefix leaves int64, so the running sum in
+    int64 is the exact one; larger inputs are refused."""
+    x = np.asarray(x).ravel().astype(np.int64)
+    if x.size and int(np.abs(x).max()) * x.size >= 2 ** 62:
+        raise ValueError("prefix sums could leave int64")
+    inc = np.cumsum(x, dtype=np.int64)
+    if not exclusive:
+        return inc
+    out = np.zeros_like(inc)
+    out[1:] = inc[:-1]
+    return out
+
+
+def scan_count_nonzero(x, exclusive=True):
+    """Prefix counts of the nonzero elements (the output offsets of a stream
+    compaction when exclusive)."""
+    return scan_sum_int(np.asarray(x).ravel() != 0, exclusive)
+
+
+def scan_max(x, neutral):
+    """Prefix maxima by the C rule acc = acc > v ? acc : v, starting from
+    ``neutral``, in index order (values widened exactly to binary64)."""
+    out = np.empty(np.asarray(x).size, np.float64)
+    acc = float(neutral)
+    for k, v in enumerate(np.asarray(x).ravel().astype(np.float64).tolist()):
+        acc = acc if acc > v else v
+        out[k] = acc
+    return out

@@ -215,6 +215,43 @@ def test_map_u8_add_index_hand_values():
     assert all(int(g) == (int(a) + ((int(i) >> 20) % 256)) % 256 for g, a, i in zip(got, x, idx))
 
 
+def test_scan_sum_int_brute_force_and_closed_form():
+    # prefix sums of 1..n: k(k+1)/2; exclusive: (k-1)k/2
+    n = 1000
+    inc = storage.scan_sum_int(np.arange(1, n + 1))
+    exc = storage.scan_sum_int(np.arange(1, n + 1), exclusive=True)
+    k = np.arange(1, n + 1)
+    assert inc.tolist() == (k * (k + 1) // 2).tolist()
+    assert exc.tolist() == ((k - 1) * k // 2).tolist()
+    # brute force against Python integers on signed values near 2^40
+    rng = np.random.default_rng(23)
+    x = rng.integers(-(2 ** 40), 2 ** 40, 3001)
+    for ex in (False, True):
+        got = storage.scan_sum_int(x, exclusive=ex).tolist()
+        want = [sum(int(v) for v in x[: i + (0 if ex else 1)]) for i in range(0, 3001, 97)]
+        assert got[::97] == want
+    assert storage.scan_sum_int([]).size == 0
+    with pytest.raises(ValueError):
+        storage.scan_sum_int(np.full(4, 2 ** 61))
+
+
+def test_scan_count_nonzero_hand_values():
+    assert storage.scan_count_nonzero([0, 3, 0, 0, 255, 1]).tolist() == [0, 0, 1, 1, 1, 2]
+    assert storage.scan_count_nonzero([0, 3, 0, 0, 255, 1], exclusive=False).tolist() == [
+        0, 1, 1, 1, 2, 3]
+
+
+def test_scan_max_brute_force():
+    # worked by hand, with a tie and the neutral element kept until a larger value
+    got = storage.scan_max([-5.0, -7.0, 2.0, 2.0, 1.5, 3.25], -np.inf).tolist()
+    assert got == [-5.0, -5.0, 2.0, 2.0, 2.0, 3.25]
+    assert storage.scan_max([-1.0], 0.0).tolist() == [0.0]
+    rng = np.random.default_rng(29)
+    x = rng.standard_normal(2000).astype(np.float16)
+    got = storage.scan_max(x, -np.inf)
+    assert all(got[i] == max(float(v) for v in x[: i + 1]) for i in range(0, 2000, 37))
+
+
 # planted mistakes in the storage oracle: each must make one of the pins above fail
 def _f16_in_binary64(a, x16, b, y16):
     x = np.asarray(x16, np.float16).astype(np.float64)
@@ -252,6 +289,15 @@ _MUTANTS = {
         np.asarray(x, np.int64) & 255).astype(np.uint8)),
     "min keeps the first element": ("min_value", lambda x, empty: (
         np.asarray(x).ravel().tolist() or [empty])[0]),
+    "scan: exclusive taken as inclusive": ("scan_sum_int", lambda x, exclusive=False: np.cumsum(
+        np.asarray(x).ravel().astype(np.int64))),
+    "scan: prefix one element late": ("scan_sum_int", lambda x, exclusive=False: (
+        lambda inc: np.concatenate([[0, 0], inc[:-2]]) if exclusive else np.concatenate(
+            [[0], inc[:-1]]))(np.cumsum(np.asarray(x).ravel().astype(np.int64)))),
+    "scan max ignores the neutral": ("scan_max", lambda x, neutral: np.maximum.accumulate(
+        np.asarray(x, np.float64).ravel())),
+    "count counts zeros": ("scan_count_nonzero", lambda x, exclusive=True: storage.scan_sum_int(
+        np.asarray(x).ravel() == 0, exclusive)),
 }
 
 _PINS = [test_round_f16_boundary_values, test_round_f16_random_against_rationals,
@@ -260,7 +306,8 @@ _PINS = [test_round_f16_boundary_values, test_round_f16_random_against_rationals
          lambda: test_lin_comb_int_wraps_like_twos_complement(32),
          test_mixed_promotion_against_rationals, test_sum_exact_closed_form_and_sign,
          test_sum_exact_against_rationals, test_map_u8_add_index_hand_values,
-         test_extrema_brute_force]
+         test_extrema_brute_force, test_scan_sum_int_brute_force_and_closed_form,
+         test_scan_count_nonzero_hand_values, test_scan_max_brute_force]
 
 
 @pytest.mark.parametrize("name", sorted(_MUTANTS))
