@@ -17,6 +17,10 @@ expressions: + - * / min max, neg abs sqrt exp exp2 log log2 sin cos tanh.
   log2f: 1 ulp; sqrtf: correctly rounded).  One ulp of y is at most
   2^-23 |y| = 2u|y| (u = 2^-24), so k ulp <= 2ku|y|.
 * `eval_int(e)`: int32 arithmetic with two's-complement wrap (numpy int32).
+* `eval_typed(e)`: the mixed-type evaluation of the library's expression
+  typing (int32 < int64 < float32 < float64, true division, float64 math of
+  integers, int32 comparisons, wrap-around), one rounding per operation in the
+  operation's own type; the rules are written out at its definition.
 
 Propagation, for operands with exact values a, b and error bounds ea, eb:
   a +- b : ea + eb + u(|v| + ea + eb)
@@ -160,3 +164,92 @@ def eval_int(e):
     with np.errstate(over="ignore"):
         r = _INT[op](*vals)
     return np.asarray(r).astype(np.int32)
+
+
+# ------------------------------------------------------------------ typed evaluation
+# The typing of fused array expressions (C-style, on four types ordered
+# int32 < int64 < float32 < float64): bfloat16 and binary16 arrays are read as
+# binary32, so they enter here as float32 arrays holding their values; scalar
+# arguments carry their own type (numpy scalars: np.float32, np.float64,
+# np.int32, np.int64).  A binary operation converts both operands to the higher
+# of their types and rounds once in it; true division and the math functions of
+# an integer type compute in float64; comparisons give int32 1 or 0; integer
+# + - * wrap around in two's complement; the casts f32 f64 i32 i64 convert
+# (a float to an integer truncates toward zero).
+
+TYPE_ORDER = (np.int32, np.int64, np.float32, np.float64)
+_CMP = {"<": np.less, "<=": np.less_equal, ">": np.greater, ">=": np.greater_equal,
+        "==": np.equal, "!=": np.not_equal}
+_CASTS = {"f32": np.float32, "f64": np.float64, "i32": np.int32, "i64": np.int64}
+
+
+def type_of(v):
+    t = np.asarray(v).dtype.type
+    if t not in TYPE_ORDER:
+        raise TypeError("typed operands are int32, int64, float32 or float64, not %r" % t)
+    return t
+
+
+def _is_float(t):
+    return t in (np.float32, np.float64)
+
+
+def result_type(op, types):
+    """The type an operation computes in (and returns, but for comparisons)."""
+    if op in _CASTS:
+        return _CASTS[op]
+    if op in ("neg", "abs"):
+        return types[0]
+    if op == "sqrt":
+        return types[0] if _is_float(types[0]) else np.float64
+    if op == "where":
+        types = types[1:]
+    t = max(types, key=TYPE_ORDER.index)
+    if op == "/" and not _is_float(t):
+        return np.float64  # true division
+    return t
+
+
+def _apply(op, t, vals):
+    a = [np.asarray(v).astype(t) for v in vals]
+    with np.errstate(all="ignore"):
+        if op in _CASTS:
+            return np.asarray(vals[0]).astype(t)
+        if op == "neg":
+            return -a[0]
+        if op == "abs":
+            return np.abs(a[0])
+        if op == "sqrt":
+            return np.sqrt(a[0])
+        if op == "+":
+            return a[0] + a[1]
+        if op == "-":
+            return a[0] - a[1]
+        if op == "*":
+            return a[0] * a[1]
+        if op == "/":
+            return a[0] / a[1]
+        if op in ("min", "max"):
+            if _is_float(t):
+                return (np.fmin if op == "min" else np.fmax)(a[0], a[1])
+            return (np.minimum if op == "min" else np.maximum)(a[0], a[1])
+        if op in _CMP:
+            return _CMP[op](a[0], a[1]).astype(np.int32)
+    raise ValueError("eval_typed: unknown operator %r" % op)
+
+
+def eval_typed(e):
+    """Evaluate a tree under the typing above: each operation converts its
+    operands to its type and rounds once there, in source order."""
+    if not isinstance(e, tuple):
+        type_of(e)
+        return e
+    op, *args = e
+    vals = [eval_typed(a) for a in args]
+    if op == "where":
+        t = result_type(op, [type_of(v) for v in vals])
+        c = np.asarray(vals[0])
+        return np.where(c != 0, np.asarray(vals[1]).astype(t), np.asarray(vals[2]).astype(t))
+    t = result_type(op, [type_of(v) for v in vals])
+    r = _apply(op, t, vals)
+    return np.asarray(r).astype(np.int32 if op in _CMP else t)

@@ -69,7 +69,12 @@ class Expr:
     def __ge__(self, o): return Expr(">=", self, o)
     def eq(self, o): return Expr("==", self, o)
     def ne(self, o): return Expr("!=", self, o)
-    def astype(self, dtype): return Expr(_CAST[dtype], self)
+    def astype(self, dtype):
+        if not _CAST:
+            _init_casts()
+        if dtype not in _CAST:
+            raise TypeError("astype takes torch.float32, float64, int32 or int64, not %s" % dtype)
+        return Expr(_CAST[dtype], self)
 
 
 class GArray(Expr):

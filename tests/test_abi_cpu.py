@@ -656,3 +656,18 @@ def test_every_array_is_checked_before_a_launch():
     finally:
         pyc.pyc_map_destroy(m)
         pyc.pyc_reduce_destroy(r)
+
+
+def test_expression_casts_need_no_prior_evaluation():
+    """Expr.astype builds a cast node on its own (no evaluation has to come
+    first) and refuses a dtype the expression language has no cast for."""
+    import torch
+
+    from paper_1304_5553_gb300 import gpuarray as ga
+    leaf = ga.Expr("leaf")
+    for dt, op in ((torch.float32, "f32"), (torch.float64, "f64"), (torch.int32, "i32"),
+                   (torch.int64, "i64")):
+        e = leaf.astype(dt)
+        assert e.op == op and e.args == (leaf,)
+    with pytest.raises(TypeError):
+        leaf.astype(torch.bfloat16)

@@ -207,3 +207,125 @@ def test_pins_catch_planted_rule_mistakes(name, monkeypatch):
         except AssertionError:
             failed = True
     assert failed, "the pins did not catch: " + name
+
+
+
+# ------------------------------------------------------------------ typed evaluation
+_T = {"i32": np.int32, "i64": np.int64, "f32": np.float32, "f64": np.float64}
+
+
+def _exact_value(v):
+    return Fraction(int(v)) if np.issubdtype(type(v), np.integer) else Fraction(float(v))
+
+
+def _round_to(q: Fraction, t):
+    """A rational rounded once to type t (integers: exact, then wrapped)."""
+    if t is np.float64:
+        return float(q)                     # Fraction -> float rounds correctly
+    if t is np.float32:
+        return rn32(q)
+    bits = 32 if t is np.int32 else 64
+    assert q.denominator == 1
+    w = int(q) % 2 ** bits
+    return w - 2 ** bits if w >= 2 ** (bits - 1) else w
+
+
+def test_typed_result_types_follow_the_c_conversions():
+    # int < long long < float < double (C's usual arithmetic conversions for these
+    # four types), except that / of integers is true division in double
+    names = ["i32", "i64", "f32", "f64"]
+    for i, p in enumerate(names):
+        for j, q in enumerate(names):
+            a, b = np.array([3], _T[p]), np.array([2], _T[q])
+            want = _T[names[max(i, j)]]
+            for op in ("+", "-", "*", "min", "max"):
+                assert ox.eval_typed((op, a, b)).dtype == want, (op, p, q)
+            div = want if want in (np.float32, np.float64) else np.float64
+            assert ox.eval_typed(("/", a, b)).dtype == div, (p, q)
+            assert ox.eval_typed(("<", a, b)).dtype == np.int32
+    assert ox.eval_typed(("sqrt", np.array([9], np.int32))).dtype == np.float64
+    assert ox.eval_typed(("sqrt", np.array([9], np.float32))).dtype == np.float32
+    assert ox.eval_typed(("neg", np.array([9], np.int64))).dtype == np.int64
+    assert ox.eval_typed(("where", np.array([1], np.int32), np.array([1], np.float32),
+                          np.array([2], np.int64))).dtype == np.float32
+
+
+def test_typed_hand_values():
+    i = np.array([7, -7, 2 ** 31 - 1, -(2 ** 31)], np.int32)
+    two = np.int32(2)
+    assert ox.eval_typed(("/", i, two)).tolist() == [3.5, -3.5, 1073741823.5, -1073741824.0]
+    assert ox.eval_typed(("+", i, np.int32(1))).tolist() == [8, -6, -(2 ** 31), -(2 ** 31) + 1]
+    assert ox.eval_typed(("abs", i)).tolist() == [7, 7, 2 ** 31 - 1, -(2 ** 31)]  # wraps
+    assert ox.eval_typed(("sqrt", np.array([16, 2], np.int64))).tolist() == [4.0, 2.0 ** 0.5]
+    assert ox.eval_typed((">", np.array([1.5, 0.5], np.float32), np.int32(1))).tolist() == [1, 0]
+    # 2^24 + 1 has no binary32 value: int32 + float32 rounds the integer first
+    assert ox.eval_typed(("+", np.array([2 ** 24 + 1], np.int32), np.float32(0.0))).tolist() == [
+        float(2 ** 24)]
+    assert ox.eval_typed(("i32", np.array([-2.7, 2.7], np.float64))).tolist() == [-2, 2]
+    c = np.array([0, 3], np.int32)
+    assert ox.eval_typed(("where", c, np.array([1.25, 1.25], np.float64),
+                          np.array([9, 9], np.int64))).tolist() == [9.0, 1.25]
+
+
+def test_typed_operations_against_rationals():
+    """Each + - * / min max on random operands of every type pair equals the exact
+    rational result rounded once to the operation's type (integers: wrapped)."""
+    rng = np.random.default_rng(57)
+    draw = {
+        "i32": lambda k: rng.integers(-(2 ** 31), 2 ** 31, k).astype(np.int32),
+        "i64": lambda k: rng.integers(-(2 ** 62), 2 ** 62, k).astype(np.int64),
+        "f32": lambda k: (rng.uniform(-4, 4, k) * 2.0 ** rng.integers(-20, 20, k)).astype(
+            np.float32),
+        "f64": lambda k: rng.uniform(-4, 4, k) * 2.0 ** rng.integers(-40, 40, k),
+    }
+    ops = {"+": lambda a, b: a + b, "-": lambda a, b: a - b, "*": lambda a, b: a * b,
+           "/": lambda a, b: a / b, "min": min, "max": max}
+    names = list(_T)
+    for p in names:
+        for q in names:
+            a, b = draw[p](40), draw[q](40)
+            for op, f in ops.items():
+                got = ox.eval_typed((op, a, b))
+                t = got.dtype.type
+                for k in range(40):
+                    if op == "/" and b[k] == 0:
+                        continue
+                    x, y = _exact_value(a[k]), _exact_value(b[k])
+                    if t in (np.float32, np.float64):
+                        # operands convert to t first (one rounding each), then one more
+                        x, y = Fraction(_round_to(x, t)), Fraction(_round_to(y, t))
+                        want = _round_to(f(x, y), t)
+                    else:
+                        want = _round_to(f(x, y), t)
+                    assert float(got[k]) == float(want) if t in (np.float32, np.float64) else \
+                        int(got[k]) == want, (op, p, q, k, a[k], b[k], got[k], want)
+
+
+_TYPED_MUTANTS = {
+    "integer division floors": ("result_type", lambda op, types: (
+        max(types, key=ox.TYPE_ORDER.index) if op not in ox._CASTS and op not in (
+            "neg", "abs", "sqrt", "where") else _ORIG_RESULT_TYPE(op, types))),
+    "int64 with float32 widens to float64": ("result_type", lambda op, types: (
+        np.float64 if np.int64 in types and np.float32 in types else _ORIG_RESULT_TYPE(op, types))),
+    "sqrt of an integer in float32": ("result_type", lambda op, types: (
+        np.float32 if op == "sqrt" and types[0] in (np.int32, np.int64) else
+        _ORIG_RESULT_TYPE(op, types))),
+    "float min propagates the first operand": ("_apply", lambda op, t, vals: (
+        np.asarray(vals[0]).astype(t) if op == "min" else _ORIG_APPLY(op, t, vals))),
+}
+_ORIG_RESULT_TYPE = ox.result_type
+_ORIG_APPLY = ox._apply
+
+
+@pytest.mark.parametrize("name", sorted(_TYPED_MUTANTS))
+def test_typed_pins_catch_planted_mistakes(name, monkeypatch):
+    fn, bad = _TYPED_MUTANTS[name]
+    monkeypatch.setattr(ox, fn, bad)
+    failed = False
+    for pin in (test_typed_result_types_follow_the_c_conversions, test_typed_hand_values,
+                test_typed_operations_against_rationals):
+        try:
+            pin()
+        except (AssertionError, ZeroDivisionError):
+            failed = True
+    assert failed, "the pins did not catch: " + name
