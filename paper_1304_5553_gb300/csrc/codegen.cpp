@@ -1430,8 +1430,15 @@ __device__ __noinline__ bool pyc_check_fail(const pyc_scan_params& S, const pyc_
   }
   return false;
 }
+// PYC_SCAN_SHRINK (a test hook) narrows the array ranges (codes below 30) by
+// that many elements at their top; descriptor ranges are never narrowed.
+#ifndef PYC_SCAN_SHRINK
+#define PYC_SCAN_SHRINK 0
+#endif
 #define PYC_OK(S, idx, cnt, bound, code, t)                                        \
-  (((pyc_i64)(idx) >= 0 && (pyc_i64)(idx) + (pyc_i64)(cnt) <= (pyc_i64)(bound)) || \
+  (((pyc_i64)(idx) >= 0 &&                                                         \
+    (pyc_i64)(idx) + (pyc_i64)(cnt) <=                                             \
+        (pyc_i64)(bound) - ((code) < 30 ? (pyc_i64)PYC_SCAN_SHRINK : 0)) ||        \
    pyc_check_fail(S, (pyc_i64)(idx), code, t))
 #else
 #define PYC_OK(S, idx, cnt, bound, code, t) true

@@ -179,7 +179,15 @@ PYC_API pyc_status pyc_scan_create(pyc_dtype dtype, const char* neutral, const c
     bool checked = bounds_requested(h->opts);
     if (const char* c = std::getenv("PYC_CHECK_BOUNDS"))
       if (c[0] == '1') checked = true;
-    if (checked) h->preamble = "#define PYC_CHECK 1\n" + h->preamble;
+    if (checked) {
+      std::string d = "#define PYC_CHECK 1\n";
+      // test hook: narrow the array ranges, so that the checks can be seen to fire
+      if (const char* k = std::getenv("PYC_DEBUG_BOUNDS_SHRINK")) {
+        long long v = std::atoll(k);
+        if (v > 0) d += "#define PYC_SCAN_SHRINK " + std::to_string(v) + "LL\n";
+      }
+      h->preamble = d + h->preamble;
+    }
     h->dtype = dtype;
     h->name = "scan";
     h->spec = parse_argspec(argspec);

@@ -10,6 +10,8 @@ violation and give the same bits.  A last test narrows the checked ranges on
 purpose (a host-side test hook; no access leaves its array) to show that the
 checks fire and that the host reads and clears the record.
 """
+import re
+
 import numpy as np
 import pytest
 import torch
@@ -207,3 +209,64 @@ def test_narrowed_ranges_make_the_checks_fire(monkeypatch):
     pyc.pyc_reduce_check_bounds(r)
     pyc.pyc_map_destroy(h)
     pyc.pyc_reduce_destroy(r)
+
+
+SCAN_CFGS = [dict(vec_bytes=16, items_per_thread=1, block=128),
+             dict(vec_bytes=32, items_per_thread=4, block=512)]
+
+
+@pytest.mark.parametrize("cfg", range(len(SCAN_CFGS)))
+def test_scans_small_sizes_all_offsets(cfg):
+    """The scan's checked build (its own PYC_CHECK build, selected by the same
+    option): exact scans (int32 -> int64 exclusive sum, binary32 maximum, the
+    non-commutative affine composition) at n <= 1100 from 16 element offsets and
+    at 2^20 + 77 from offset 3, plain against checked, no violation, same bits."""
+    c = SCAN_CFGS[cfg]
+    N = (1 << 20) + 77 + 16
+    xi = torch.from_numpy(inputs.int_uniform_i32(15, 0, N)).cuda()
+    xf = torch.from_numpy(inputs.uniform_f32(15, 1, N, -1.0, 1.0)).cuda()
+    ca = torch.from_numpy(inputs.int_uniform_i32(15, 2, N, 0, 2 ** 31 - 1)).cuda()
+    cb = torch.from_numpy(inputs.int_uniform_i32(15, 3, N, 0, 2 ** 31 - 1)).cuda()
+    cases = [("cumsum_excl_i32_i64", [xi], torch.int64), ("cummax_f32", [xf], torch.float32),
+             ("affine_u32", [ca, cb], torch.int64)]
+    sizes = [(n, off) for n in list(range(0, 70)) + [255, 256, 257, 1000, 1100]
+             for off in range(16)] + [((1 << 20) + 77, 3)]
+    for name, ins, odt in cases:
+        hp, hc = _pair(name, **c)
+        for n, off in sizes:
+            outs = []
+            for h in (hp, hc):
+                y = torch.zeros(N, dtype=odt, device="cuda")
+                es = [a.element_size() for a in ins]
+                pyc.pyc_scan_launch(h, n, [a.data_ptr() + off * e for a, e in zip(ins, es)] +
+                                    [y.data_ptr() + off * y.element_size()], None, _s())
+                outs.append(y)
+            pyc.pyc_scan_sync(hc, _s())  # raises if the checked build recorded a violation
+            pyc.pyc_scan_sync(hp, _s())
+            assert torch.equal(outs[0].view(torch.uint8), outs[1].view(torch.uint8)), (name, n, off)
+
+
+def test_narrowed_scan_ranges_make_the_checks_fire(monkeypatch):
+    """With the scan's array ranges narrowed by one element (the test hook), the
+    access of the last element is skipped and recorded, and pyc_scan_sync reports
+    it as PYC_E_INTERNAL naming that index; the record is then cleared."""
+    monkeypatch.setenv("PYC_DEBUG_BOUNDS_SHRINK", "1")
+    n = 1000
+    h = pyc.pyc_scan_create(pyc.PYC_I64, "0", "a+b", "(long long)x[i]", "y[i] = item",
+                            "int *x, long long *y", dict(SCAN_CFGS[0], debug_bounds=1))
+    monkeypatch.delenv("PYC_DEBUG_BOUNDS_SHRINK")
+    try:
+        x = torch.ones(n, dtype=torch.int32, device="cuda")
+        y = torch.zeros(n, dtype=torch.int64, device="cuda")
+        pyc.pyc_scan_launch(h, n, [x.data_ptr(), y.data_ptr()], None, _s())
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_scan_sync(h, _s())
+        assert e.value.status == pyc.PYC_E_INTERNAL
+        # the recorded access covers the last element (one element, or its vector group)
+        idx = int(re.search(r"index (-?\d+)", str(e.value)).group(1))
+        assert n - 32 <= idx <= n - 1, str(e.value)
+        pyc.pyc_scan_sync(h, _s())  # cleared
+        # accesses below the narrowed group are unaffected
+        assert torch.equal(y[: n - 32].cpu(), torch.arange(1, n - 31, dtype=torch.int64))
+    finally:
+        pyc.pyc_scan_destroy(h)
