@@ -166,8 +166,12 @@ pyc_status pyc_map_create(const char* argspec, const char* stmt, const char* nam
  *            natural alignment (a C struct of the scalars; see pyc_param_info
  *            scalar_offset); may be NULL if there are none.
  *   stream   stream to enqueue on.
- * n == 0 is a no-op.  Errors: PYC_E_ARG (n < 0, null or misaligned array),
- * PYC_E_CUDA. */
+ * n == 0 is a no-op.  The kernel is launched with programmatic stream
+ * serialization (Blackwell's dependent launch): it may be scheduled while the
+ * previous kernel on the stream drains, but waits for that kernel to complete
+ * before its first memory access, so ordering is the stream's and back-to-back
+ * launches overlap their launch gaps.  pyc_reduce_launch likewise.  Errors:
+ * PYC_E_ARG (n < 0, null or misaligned array), PYC_E_CUDA. */
 pyc_status pyc_map_launch(pyc_map_t h, int64_t n, void* const* ptrs, const void* scalars,
                           pyc_stream_t stream);
 

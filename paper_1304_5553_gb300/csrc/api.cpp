@@ -234,6 +234,29 @@ void fill_param(const HandleBase& h, int idx, pyc_param_info* info) {
 
 }  // namespace
 
+// Launch with programmatic stream serialization: the kernel (which waits for its
+// predecessor with griddepcontrol.wait before touching memory) may be scheduled
+// while the previous kernel on the stream drains, hiding the launch gap between
+// back-to-back launches; the order of memory effects is the stream's.
+void launch_dependent(CUfunction f, unsigned grid, unsigned block, CUstream stream,
+                      void** params) {
+  CUlaunchAttribute at[1];
+  at[0].id = CU_LAUNCH_ATTRIBUTE_PROGRAMMATIC_STREAM_SERIALIZATION;
+  at[0].value.programmaticStreamSerializationAllowed = 1;
+  CUlaunchConfig lc{};
+  lc.gridDimX = grid;
+  lc.gridDimY = 1;
+  lc.gridDimZ = 1;
+  lc.blockDimX = block;
+  lc.blockDimY = 1;
+  lc.blockDimZ = 1;
+  lc.sharedMemBytes = 0;
+  lc.hStream = stream;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  PYC_CU(drv().cuLaunchKernelEx(&lc, f, params, nullptr));
+}
+
 void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
                 const void* scalars, CUstream stream) {
   check_cfg(cfg);
@@ -248,8 +271,7 @@ void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
   int64_t want = nfull > 0 ? nfull : (n + cfg.block - 1) / cfg.block;
   unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, want));
   void* params[] = {args.data(), &n, &head};
-  PYC_CU(drv().cuLaunchKernel(f, grid, 1, 1, (unsigned)cfg.block, 1, 1, 0, stream, params,
-                              nullptr));
+  launch_dependent(f, grid, (unsigned)cfg.block, stream, params);
 }
 
 pyc_reduce::Workspace& reduce_workspace(pyc_reduce* h, CUstream stream) {
@@ -283,8 +305,7 @@ void launch_reduce(pyc_reduce* h, const LaunchCfg& cfg, int64_t n, void* const* 
   ChunkPlan cp = plan_chunks(n, head, tile, resident);
   pyc_reduce::Workspace& w = reduce_workspace(h, stream);
   void* params[] = {args.data(), &n, &cp.head, &cp.chunk, &cp.nchunks, &w.part, &w.ticket, &d_out};
-  PYC_CU(drv().cuLaunchKernel(f, (unsigned)cp.grid, 1, 1, (unsigned)cfg.block, 1, 1, 0, stream,
-                              params, nullptr));
+  launch_dependent(f, (unsigned)cp.grid, (unsigned)cfg.block, stream, params);
 }
 
 }  // namespace pyc

@@ -311,6 +311,20 @@ __device__ __noinline__ bool pyc_bounds_fail(const long long idx, const long lon
 #define PYC_ALIGNED(ptr, width, code) true
 #endif
 
+// Programmatic dependent launch.  The single map and map-reduce kernels are
+// launched with programmatic stream serialization, so they may be scheduled
+// before the previous kernel on their stream has finished: each waits here for
+// that kernel to complete (and its memory to be visible) before its first
+// memory access, which keeps stream order, and lets the next launch be
+// scheduled once every CTA has signalled.  Launched without the attribute,
+// both are no-ops.
+__device__ __forceinline__ void pyc_grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pyc_grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Arrival at a ticket shared by the CTAs of one launch (or one segment): an add
 // with release-acquire semantics at GPU scope.  The partials the arriving thread
 // stored before it are visible to whichever thread sees the last arrival, and
@@ -613,6 +627,8 @@ __device__ __forceinline__ void pyc_map_body(const pyc_args& pyc_p, const pyc_i6
   o << R"PYC(  const pyc_i64 pyc_lo = 0, pyc_hi = n;  // every array holds n elements
   (void)pyc_lo;
   (void)pyc_hi;
+  pyc_grid_dependency_wait();
+  pyc_grid_launch_dependents();  // the next launch may be scheduled at once
   const pyc_i64 pyc_step = (pyc_i64)blockDim.x * E;
   const pyc_i64 pyc_tile = pyc_step * U;
   // aligned body [h, h + nfull * tile) in whole tiles; head [0, h) and tail scalar
@@ -1103,6 +1119,7 @@ __device__ __forceinline__ void pyc_reduce_body(const pyc_args& pyc_p, const pyc
   // one CTA and at most one chunk: its partial is the only one, so it is
   // combined where it is, with no partial slot, ticket or second read
   const bool pyc_solo = gridDim.x == 1 && nchunks <= 1;
+  pyc_grid_dependency_wait();
   pyc_acc_t pyc_v1 = pyc_neutral();
   for (pyc_i64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     pyc_acc_t v = pyc_chunk<VB, U>(pyc_p, n, head, chunk, c, threadIdx.x, blockDim.x);
@@ -1110,6 +1127,8 @@ __device__ __forceinline__ void pyc_reduce_body(const pyc_args& pyc_p, const pyc
     if (pyc_solo) pyc_v1 = v;
     else if (threadIdx.x == 0) part[c] = v;
   }
+  // the next launch on the stream may be scheduled while the partials are combined
+  pyc_grid_launch_dependents();
   if (pyc_solo) {
     const pyc_out_t r = pyc_combine_partials_reg(pyc_v1, (int)nchunks);
     if (threadIdx.x == 0) *out = r;
