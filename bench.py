@@ -901,7 +901,10 @@ def run_gpu(args):
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(args.dist_backend)
+    # one GPU per rank; ranks beyond the visible GPUs share them (a smoke run of
+    # the multi-rank path with --dist-backend gloo: no kernel waits on another rank)
+    local %= torch.cuda.device_count()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -1041,6 +1044,9 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="pyc", choices=["pyc", "reference"])
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="process group of a torchrun launch (gloo: several ranks may "
+                         "share one GPU, for a smoke run of the multi-rank path)")
     ap.add_argument("--quick", action="store_true", help="maps only (no details, no e2e)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--only", default="", help="comma-separated subset of the maps (profiling)")
