@@ -671,3 +671,64 @@ def test_expression_casts_need_no_prior_evaluation():
         assert e.op == op and e.args == (leaf,)
     with pytest.raises(TypeError):
         leaf.astype(torch.bfloat16)
+
+
+def test_introspection_of_reduce_and_scan_handles():
+    """Parameter records, scalar block sizes and launch configurations of
+    map-reduce and scan handles (no GPU needed)."""
+    lib = pyc.load()
+    r = pyc.pyc_reduce_create(pyc.PYC_F32, "0", "a+b", "k*x[i]*y[i]",
+                              "float k, const float *x, float *y")
+    s = pyc.pyc_scan_create(pyc.PYC_I64, "0", "a+b", "(long long)x[i]", "y[i] = prev_item",
+                            "int *x, long long *y")
+    try:
+        assert lib.pyc_reduce_num_params(r) == 3 and lib.pyc_reduce_scalar_bytes(r) == 4
+        assert lib.pyc_scan_num_params(s) == 2 and lib.pyc_scan_scalar_bytes(s) == 0
+        info = pyc.pyc_param_info()
+        want = [(b"k", 0, pyc.PYC_F32, 4, 0, -1, 0), (b"x", 1, pyc.PYC_F32, 4, -1, 0, 1),
+                (b"y", 1, pyc.PYC_F32, 4, -1, 1, 1)]
+        for i, w in enumerate(want):
+            assert lib.pyc_reduce_param(r, i, ctypes.byref(info)) == pyc.PYC_OK
+            got = (info.name, info.is_pointer, info.dtype, info.elem_bytes, info.scalar_offset,
+                   info.pointer_slot, info.read)
+            assert got == w, (i, got)
+            assert info.written == 0  # a map expression only reads
+        assert lib.pyc_reduce_param(r, 3, ctypes.byref(info)) == pyc.PYC_E_ARG
+        assert lib.pyc_scan_param(s, 1, ctypes.byref(info)) == pyc.PYC_OK
+        assert (info.name, info.dtype, info.read, info.written) == (b"y", pyc.PYC_I64, 0, 1)
+        assert lib.pyc_scan_param(s, -1, ctypes.byref(info)) == pyc.PYC_E_ARG
+        v, u, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        for fn, h in ((lib.pyc_reduce_config, r), (lib.pyc_scan_config, s)):
+            assert fn(h, ctypes.c_int64(1 << 20), ctypes.byref(v), ctypes.byref(u),
+                      ctypes.byref(b)) == pyc.PYC_OK
+            assert v.value in (16, 32) and u.value in (1, 2, 4) and b.value % 32 == 0
+    finally:
+        pyc.pyc_reduce_destroy(r)
+        pyc.pyc_scan_destroy(s)
+
+
+def test_expression_typing_matches_the_typed_oracle():
+    """pyc_expr_type (the library's typing of fused expressions) gives, for every
+    operator and pair of operand types, the type the expression oracle's typed
+    evaluation computes in."""
+    import numpy as np
+
+    from oracle import expr as ox
+    dts = {pyc.PYC_I32: np.int32, pyc.PYC_I64: np.int64, pyc.PYC_F32: np.float32,
+           pyc.PYC_F64: np.float64}
+    back = {v: k for k, v in dts.items()}
+    for a in dts:
+        for op in ("neg", "abs", "sqrt", "f32", "f64", "i32", "i64"):
+            got = pyc.pyc_expr_type("(%s $0)" % op, [a], [1])
+            assert got == back[ox.result_type(op, [dts[a]])], (op, a, got)
+        for b in dts:
+            for op in ("+", "-", "*", "/", "min", "max"):
+                got = pyc.pyc_expr_type("(%s $0 $1)" % op, [a, b], [1, 1])
+                assert got == back[ox.result_type(op, [dts[a], dts[b]])], (op, a, b, got)
+            assert pyc.pyc_expr_type("(< $0 $1)", [a, b], [1, 1]) == pyc.PYC_I32
+            # a scalar argument carries its own type like an array
+            got = pyc.pyc_expr_type("(* $0 %1)", [a, b], [1, 0])
+            assert got == back[ox.result_type("*", [dts[a], dts[b]])], (a, b, got)
+    # bfloat16 and binary16 arrays are read as binary32
+    for h in (pyc.PYC_BF16, pyc.PYC_F16):
+        assert pyc.pyc_expr_type("(+ $0 $1)", [h, pyc.PYC_I64], [1, 1]) == pyc.PYC_F32
