@@ -59,6 +59,28 @@ std::vector<unsigned char> pack_args(const ArgSpec& spec, void* const* ptrs, con
   return a;
 }
 
+void check_overlap(const ArgSpec& spec, void* const* ptrs, int64_t n) {
+  if (n <= 0 || !ptrs) return;
+  for (size_t a = 0; a < spec.params.size(); ++a) {
+    const auto& p = spec.params[a];
+    if (!(p.is_ptr && p.lifted && ptrs[p.ptr_slot])) continue;
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(ptrs[p.ptr_slot]);
+    const int sa = type_info(p.dtype).bytes;
+    for (size_t b = a + 1; b < spec.params.size(); ++b) {
+      const auto& q = spec.params[b];
+      if (!(q.is_ptr && q.lifted && ptrs[q.ptr_slot]) || !(p.written || q.written)) continue;
+      const uintptr_t qa = reinterpret_cast<uintptr_t>(ptrs[q.ptr_slot]);
+      const int sb = type_info(q.dtype).bytes;
+      if (pa == qa && sa == sb) continue;  // exact aliasing: element i is element i
+      const bool disjoint = pa + (uintptr_t)n * sa <= qa || qa + (uintptr_t)n * sb <= pa;
+      if (!disjoint)
+        fail(PYC_E_ARG, "arrays '" + p.name + "' and '" + q.name +
+                            "' overlap in part (only the same pointer with the same element "
+                            "type may alias a written array)");
+    }
+  }
+}
+
 int64_t vector_head(const ArgSpec& spec, void* const* ptrs, int vec_bytes, int min_bytes,
                     int64_t n) {
   bool any = false;
@@ -263,6 +285,7 @@ void launch_map(pyc_map* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs,
   if (n < 0) fail(PYC_E_ARG, "n must be >= 0");
   std::vector<unsigned char> args = pack_args(h->spec, ptrs, scalars);
   int64_t head = vector_head(h->spec, ptrs, cfg.v.vec_bytes, h->min_bytes, n);
+  check_overlap(h->spec, ptrs, n);
   if (n == 0) return;
   CUfunction f = h->mod->function(h->kname("pyc_map", cfg.v));
   int resident = resident_ctas(f, cfg.block);

@@ -134,6 +134,11 @@ std::vector<unsigned char> pack_args(const ArgSpec& spec, void* const* ptrs, con
 int64_t vector_head(const ArgSpec& spec, void* const* ptrs, int vec_bytes, int min_bytes,
                     int64_t n);
 
+// A written array that overlaps another array in part is undefined behaviour
+// (only exact aliasing -- the same pointer and element size -- is allowed); for
+// arrays indexed as name[i] over [0, n) it is detectable: PYC_E_ARG.
+void check_overlap(const ArgSpec& spec, void* const* ptrs, int64_t n);
+
 // Resident CTAs of `f` at `block` threads on the current device.
 // CTAs of f that fit on the device at once (dyn_smem: dynamic shared bytes per CTA).
 int resident_ctas(CUfunction f, int block, int dyn_smem = 0);

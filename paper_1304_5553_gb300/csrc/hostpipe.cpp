@@ -148,6 +148,7 @@ PYC_API pyc_status pyc_map_launch_host(pyc_map_t h, int64_t n, void* const* host
     for (auto& q : spec.params)
       if (q.is_ptr && q.used && !host_ptrs[q.ptr_slot])
         fail(PYC_E_ARG, "array '" + q.name + "' is NULL");
+    check_overlap(spec, host_ptrs, n);
     std::lock_guard<std::mutex> lk(h->pipe_mu);
     HostPipe* p = get_pipe(h);
     const Driver& d = drv();

@@ -107,6 +107,7 @@ void launch_scan(pyc_scan* h, const LaunchCfg& cfg, int64_t n, void* const* ptrs
   if (spin_limit < 1) fail(PYC_E_ARG, "spin_limit must be >= 1");
   std::vector<unsigned char> args = pack_args(h->spec, ptrs, scalars);
   int64_t head = vector_head(h->spec, ptrs, cfg.v.vec_bytes, h->min_bytes, n);
+  check_overlap(h->spec, ptrs, n);
   if (n == 0) return;
   CUfunction f = h->mod->function(h->kname("pyc_scan", cfg.v));
   // cfg.block compute threads and one look-back warp

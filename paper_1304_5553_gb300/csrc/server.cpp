@@ -586,6 +586,7 @@ PYC_API pyc_status pyc_server_submit(pyc_server_t s, const pyc_request* req, uin
       else if (r->n > 0)
         fail(PYC_E_ARG, "array '" + p.name + "' is NULL (only written-only map outputs may be)");
     }
+    check_overlap(spec, r->ptrs.data(), r->n);  // NULL (server-allocated) outputs skipped
     r->bytes = request_bytes(*h, r->n, out_bytes);
     if (r->bytes > s->cfg.mem_budget_bytes)
       fail(PYC_E_NOMEM, "request needs " + std::to_string(r->bytes) +

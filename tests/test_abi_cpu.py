@@ -732,3 +732,40 @@ def test_expression_typing_matches_the_typed_oracle():
     # bfloat16 and binary16 arrays are read as binary32
     for h in (pyc.PYC_BF16, pyc.PYC_F16):
         assert pyc.pyc_expr_type("(+ $0 $1)", [h, pyc.PYC_I64], [1, 1]) == pyc.PYC_F32
+
+
+def test_partial_overlap_with_a_written_array_is_an_argument_error():
+    """A written array that overlaps another array in part is undefined behaviour
+    (only exact aliasing is allowed, as in Listing 1's in-place a[i] *= 2); for
+    arrays indexed as name[i] the host rejects it before any GPU work: maps, scans
+    and host-array maps."""
+    lib = pyc.load()
+    m = pyc.pyc_map_create("float *x, float *y", "y[i] = 2*x[i]")
+    s = pyc.pyc_scan_create(pyc.PYC_I64, "0", "a+b", "(long long)x[i]", "y[i] = item",
+                            "int *x, long long *y")
+    base = 1 << 20
+    try:
+        for xp, yp in ((base, base + 400), (base + 400, base), (base, base + 3996)):
+            assert lib.pyc_map_launch(m, 1000, pyc._ptr_array([xp, yp]), None,
+                                      None) == pyc.PYC_E_ARG
+            assert "overlap in part" in pyc.pyc_last_error()
+            assert lib.pyc_map_launch_host(m, 1000, pyc._ptr_array([xp, yp]),
+                                           None) == pyc.PYC_E_ARG
+            assert "overlap in part" in pyc.pyc_last_error()
+        # int32 input and int64 output at the same address differ in element size:
+        # y[i] would overwrite x[2i] and x[2i + 1] before they are read
+        assert lib.pyc_scan_launch(s, 1000, pyc._ptr_array([base, base]), None,
+                                   None) == pyc.PYC_E_ARG
+        assert "overlap in part" in pyc.pyc_last_error()
+        # disjoint ranges and exact aliasing pass the check and go on to launch, which
+        # needs the driver: only where there is none (the pointers here are not real)
+        if not _has_gpu():
+            for xp, yp in ((base, base + 4000), (base + 4000, base), (base, base)):
+                lib.pyc_map_launch(m, 1000, pyc._ptr_array([xp, yp]), None, None)
+                assert "overlap" not in pyc.pyc_last_error()
+        # n = 0 touches nothing
+        assert lib.pyc_map_launch(m, 0, pyc._ptr_array([base, base + 4]), None,
+                                  None) == pyc.PYC_OK
+    finally:
+        pyc.pyc_map_destroy(m)
+        pyc.pyc_scan_destroy(s)

@@ -191,9 +191,10 @@ def test_deadline_queue_limit_and_errors(pools):
 
 
 def test_bad_arrays_fail_at_submit_and_spare_the_batch(pools):
-    """A NULL array (other than a written-only map output) or one not aligned to
-    its element size is refused by pyc_server_submit itself, also for an array
-    the statement indexes other than as name[i]; a good request after it runs."""
+    """A NULL array (other than a written-only map output), one not aligned to its
+    element size, or an output overlapping an input in part is refused by
+    pyc_server_submit itself, also for an array the statement indexes other than
+    as name[i]; a good request after it runs."""
     _, dev = pools
     srv = pyc.pyc_server_create(1 << 30, num_streams=1)
     diff = pyc.pyc_map_create("float *x, float *y", "y[i] = x[i + 1] - x[i]")
@@ -203,10 +204,14 @@ def test_bad_arrays_fail_at_submit_and_spare_the_batch(pools):
         bad = [(pyc.PYC_REQ_MAP, diff, [0, out.data_ptr()]),
                (pyc.PYC_REQ_MAP, diff, [x.data_ptr() + 2, out.data_ptr()]),
                (pyc.PYC_REQ_REDUCE, stock.create("dot_f32"), [x.data_ptr() + 1, y.data_ptr()]),
-               (pyc.PYC_REQ_REDUCE, stock.create("dot_f32"), [x.data_ptr(), 0])]
+               (pyc.PYC_REQ_REDUCE, stock.create("dot_f32"), [x.data_ptr(), 0]),
+               # an output overlapping an input in part (exact aliasing would be allowed)
+               (pyc.PYC_REQ_MAP, stock.create("lin_comb_f32"),
+                [x.data_ptr(), y.data_ptr(), x.data_ptr() + 4])]
         for kind, h, ptrs in bad:
+            scal = pyc.pack_scalars(h, [A, B]) if len(ptrs) == 3 else None
             with pytest.raises(pyc.PycError) as e:
-                pyc.pyc_server_submit(srv, pyc.make_request(kind, h, 1000, ptrs))
+                pyc.pyc_server_submit(srv, pyc.make_request(kind, h, 1000, ptrs, scal))
             assert e.value.status == pyc.PYC_E_ARG
         _run_one(srv, pyc.make_request(pyc.PYC_REQ_MAP, diff, 1000, [x.data_ptr(), out.data_ptr()]))
         want = (x[1:1001] - x[:1000]).cpu()
