@@ -694,6 +694,24 @@ pyc_status pyc_server_get_stats(pyc_server_t s, pyc_server_stats* st);
 /* Fail queued requests, wait for launched batches, free everything. */
 void pyc_server_destroy(pyc_server_t s);
 
+/* Test hook (the paper has no counterpart): a serving loop whose batches run
+ * on the host, so that everything in it but the device work -- admission
+ * against the budget in arrival order, grouping by handle, batch slots and the
+ * in-flight limit, deadlines, queue limits, outputs allocated by the server
+ * (from a host arena here), release, replay -- runs and can be tested without
+ * a GPU.  Each launched batch is handed to one executor thread, which calls
+ * `exec` once per request in batch order with the request as submitted except
+ * `ptrs`, which holds the arrays with the server's outputs filled in; for a
+ * map-reduce, exec writes the result (pyc_reduce_out_bytes bytes) to `value`.
+ * Its return value becomes the request's status (PYC_OK = 0).  The batch is
+ * retired when every call has returned.  cfg as for pyc_server_create (a
+ * default arena of at most 256 MiB of host memory); PYC_REPLAY_DIRECT is not
+ * available.  Handles may be created without a GPU (run-time compilation needs
+ * none).  Errors: PYC_E_ARG. */
+typedef int (*pyc_host_exec_fn)(void* user, const pyc_request* req, void* value);
+pyc_status pyc_server_create_host(const pyc_server_cfg* cfg, pyc_host_exec_fn exec, void* user,
+                                  pyc_server_t* out);
+
 /* Trace replay for load measurement.  Submits reqs[k] at t0 + arrival_ns[k]
  * (an open loop; all at t0 when arrival_ns is NULL), collects and releases every
  * request as it finishes and stores its pyc_result in results[k], with

@@ -15,6 +15,7 @@
 // result depends only on the request itself (its work list and the handle's
 // fixed batch configuration), never on the rest of its batch.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -127,6 +128,13 @@ struct Slot {
   unsigned char* host = nullptr;
   CUevent ev = nullptr;
   bool busy = false;
+  // host execution (pyc_server_create_host): the batch's requests, and per
+  // request its status and result, filled by the executor thread; done is set
+  // under the server lock once every request has been computed
+  std::vector<SReq*> host_reqs;
+  std::vector<int> host_status;
+  std::vector<std::array<unsigned char, 16>> host_vals;
+  bool host_done = false;
 };
 
 struct Batch {
@@ -185,6 +193,15 @@ struct pyc_server {
   bool stop = false;
   std::string fatal;
   std::thread th;
+  // host execution (test hook): batches run on exec_th through host_exec
+  pyc_host_exec_fn host_exec = nullptr;
+  void* host_user = nullptr;
+  std::vector<unsigned char> host_arena;
+  std::mutex exec_mu;
+  std::condition_variable exec_cv;
+  std::deque<int> exec_queue;  // slots whose batches wait for the executor
+  bool exec_stop = false;
+  std::thread exec_th;
 };
 
 namespace pyc {
@@ -232,6 +249,21 @@ SlotLayout layout(int max_batch, int64_t task_bytes, int64_t item_bytes, int64_t
 // Builds and enqueues one batch (without the server lock: it reads only the
 // batch's immutable request fields and its own slot).
 void launch_batch(pyc_server* s, Batch& b) {
+  if (s->host_exec) {
+    // hand the batch to the executor thread (its slot is this batch's alone)
+    Slot& hs = s->slots[b.slot];
+    hs.host_reqs = b.reqs;
+    hs.host_status.assign(b.reqs.size(), PYC_E_INTERNAL);
+    hs.host_vals.assign(b.reqs.size(), {});
+    hs.host_done = false;
+    b.out_bytes = b.kind == PYC_REQ_REDUCE ? static_cast<pyc_reduce*>(b.h)->gen.out_bytes : 0;
+    {
+      std::lock_guard<std::mutex> lk(s->exec_mu);
+      s->exec_queue.push_back(b.slot);
+    }
+    s->exec_cv.notify_one();
+    return;
+  }
   const Driver& d = drv();
   Slot& sl = s->slots[b.slot];
   CUstream st = s->streams[s->next_stream];
@@ -305,19 +337,58 @@ void retire(pyc_server* s, Batch& b, int status) {
   const int64_t t = now_ns();
   for (size_t k = 0; k < b.reqs.size(); ++k) {
     SReq* r = b.reqs[k];
-    if (status == PYC_OK && b.kind == PYC_REQ_REDUCE)
+    int st = status;
+    if (s->host_exec && st == PYC_OK) {
+      st = sl.host_status[k];
+      if (st == PYC_OK && b.kind == PYC_REQ_REDUCE)
+        std::memcpy(r->res.value, sl.host_vals[k].data(), (size_t)b.out_bytes);
+    } else if (st == PYC_OK && b.kind == PYC_REQ_REDUCE) {
       std::memcpy(r->res.value, sl.host + b.res_host_off + (int64_t)k * b.out_bytes, b.out_bytes);
-    if (status == PYC_OK && b.kind == PYC_REQ_MAP && !r->alloc_slots.empty())
+    }
+    if (st == PYC_OK && b.kind == PYC_REQ_MAP && !r->alloc_slots.empty())
       r->res.d_out = r->ptrs[r->alloc_slots[0]];
-    finish_req(s, r, status, t);
+    finish_req(s, r, st, t);
   }
+  sl.host_reqs.clear();
   sl.busy = false;
   ++s->stats.batches;
 }
 
+// The executor thread of a host-executed server: computes each handed-over
+// batch through host_exec, request by request, then marks its slot done.
+void host_executor(pyc_server* s) {
+  for (;;) {
+    int slot;
+    {
+      std::unique_lock<std::mutex> lk(s->exec_mu);
+      s->exec_cv.wait(lk, [&] { return s->exec_stop || !s->exec_queue.empty(); });
+      if (s->exec_queue.empty()) return;  // stopping, nothing left
+      slot = s->exec_queue.front();
+      s->exec_queue.pop_front();
+    }
+    Slot& sl = s->slots[slot];
+    for (size_t k = 0; k < sl.host_reqs.size(); ++k) {
+      SReq* r = sl.host_reqs[k];
+      pyc_request q{};
+      q.kind = r->kind;
+      q.handle = r->kind == PYC_REQ_MAP ? static_cast<void*>(r->mh) : static_cast<void*>(r->rh);
+      q.n = r->n;
+      q.ptrs = r->ptrs.data();
+      q.scalars = r->scalars.data();
+      q.deadline_us = 0;
+      sl.host_status[k] = s->host_exec(s->host_user, &q, sl.host_vals[k].data());
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      sl.host_done = true;
+    }
+    ++s->nevents;
+    s->cv_sched.notify_one();
+  }
+}
+
 void scheduler(pyc_server* s) {
-  const Driver& d = drv();
-  d.cuCtxSetCurrent(s->ctx);
+  if (!s->host_exec) drv().cuCtxSetCurrent(s->ctx);
   std::unique_lock<std::mutex> lk(s->mu);
   uint64_t seen = 0;
   auto notify = [&] {
@@ -330,7 +401,8 @@ void scheduler(pyc_server* s) {
   for (;;) {
     // 1. retire finished batches
     for (auto it = s->inflight.begin(); it != s->inflight.end();) {
-      CUresult q = d.cuEventQuery(s->slots[it->slot].ev);
+      CUresult q = s->host_exec ? (s->slots[it->slot].host_done ? CUDA_SUCCESS : CUDA_ERROR_NOT_READY)
+                                : drv().cuEventQuery(s->slots[it->slot].ev);
       if (q == CUDA_ERROR_NOT_READY) {
         ++it;
         continue;
@@ -491,20 +563,31 @@ int64_t request_bytes(const HandleBase& h, int64_t n, int out_bytes) {
 
 using namespace pyc;
 
+namespace pyc {
+namespace {
+// The configuration with defaults filled in (arena: at most `arena_cap` bytes
+// by default); PYC_E_ARG on a bad one.
+pyc_server_cfg server_cfg(const pyc_server_cfg* cfg, int64_t arena_cap) {
+  if (!cfg) fail(PYC_E_ARG, "cfg is NULL");
+  pyc_server_cfg c = *cfg;
+  if (c.mem_budget_bytes <= 0) fail(PYC_E_ARG, "mem_budget_bytes must be > 0");
+  if (c.num_streams <= 0) c.num_streams = 4;
+  if (c.max_batch <= 0) c.max_batch = 256;
+  if (c.max_inflight <= 0) c.max_inflight = 8;
+  if (c.max_queue <= 0) c.max_queue = 1 << 20;
+  if (c.arena_bytes <= 0) c.arena_bytes = std::min<int64_t>(c.mem_budget_bytes, arena_cap);
+  if (c.num_streams > 64 || c.max_inflight > 256 || c.max_batch > 4096)
+    fail(PYC_E_ARG, "num_streams <= 64, max_inflight <= 256, max_batch <= 4096");
+  return c;
+}
+}  // namespace
+}  // namespace pyc
+
 PYC_API pyc_status pyc_server_create(const pyc_server_cfg* cfg, pyc_server_t* out) {
   return guarded([&] {
     if (!out) fail(PYC_E_ARG, "out is NULL");
     *out = nullptr;
-    if (!cfg) fail(PYC_E_ARG, "cfg is NULL");
-    pyc_server_cfg c = *cfg;
-    if (c.mem_budget_bytes <= 0) fail(PYC_E_ARG, "mem_budget_bytes must be > 0");
-    if (c.num_streams <= 0) c.num_streams = 4;
-    if (c.max_batch <= 0) c.max_batch = 256;
-    if (c.max_inflight <= 0) c.max_inflight = 8;
-    if (c.max_queue <= 0) c.max_queue = 1 << 20;
-    if (c.arena_bytes <= 0) c.arena_bytes = std::min<int64_t>(c.mem_budget_bytes, (int64_t)8 << 30);
-    if (c.num_streams > 64 || c.max_inflight > 256 || c.max_batch > 4096)
-      fail(PYC_E_ARG, "num_streams <= 64, max_inflight <= 256, max_batch <= 4096");
+    const pyc_server_cfg c = server_cfg(cfg, (int64_t)8 << 30);
     auto s = std::make_unique<pyc_server>();
     s->cfg = c;
     s->ctx = ensure_context();
@@ -537,6 +620,29 @@ PYC_API pyc_status pyc_server_create(const pyc_server_cfg* cfg, pyc_server_t* ou
       throw;
     }
     pyc_server* raw = s.get();
+    s->th = std::thread([raw] { scheduler(raw); });
+    *out = s.release();
+  });
+}
+
+PYC_API pyc_status pyc_server_create_host(const pyc_server_cfg* cfg, pyc_host_exec_fn exec,
+                                          void* user, pyc_server_t* out) {
+  return guarded([&] {
+    if (!out) fail(PYC_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!exec) fail(PYC_E_ARG, "exec is NULL");
+    const pyc_server_cfg c = server_cfg(cfg, (int64_t)256 << 20);
+    auto s = std::make_unique<pyc_server>();
+    s->cfg = c;
+    s->host_exec = exec;
+    s->host_user = user;
+    // 256-byte aligned, as a device allocation is: outputs keep their inputs' alignment
+    s->host_arena.assign((size_t)c.arena_bytes + 256, 0);
+    s->arena_mem = (reinterpret_cast<CUdeviceptr>(s->host_arena.data()) + 255) & ~(CUdeviceptr)255;
+    s->arena.init(c.arena_bytes);
+    s->slots.resize(c.max_inflight);
+    pyc_server* raw = s.get();
+    s->exec_th = std::thread([raw] { host_executor(raw); });
     s->th = std::thread([raw] { scheduler(raw); });
     *out = s.release();
   });
@@ -673,6 +779,16 @@ PYC_API void pyc_server_destroy(pyc_server_t s) {
   s->cv_sched.notify_all();
   s->cv_done.notify_all();
   if (s->th.joinable()) s->th.join();
+  if (s->host_exec) {  // every batch has been retired: the executor is idle
+    {
+      std::lock_guard<std::mutex> lk(s->exec_mu);
+      s->exec_stop = true;
+    }
+    s->exec_cv.notify_all();
+    if (s->exec_th.joinable()) s->exec_th.join();
+    delete s;
+    return;
+  }
   try {
     const Driver& d = drv();
     d.cuCtxSetCurrent(s->ctx);
@@ -881,7 +997,9 @@ PYC_API pyc_status pyc_server_replay(pyc_server_t s, int64_t nreq, const pyc_req
     if (arrival_ns)
       for (int64_t k = 1; k < nreq; ++k)
         if (arrival_ns[k] < arrival_ns[k - 1]) fail(PYC_E_ARG, "arrival times must not decrease");
-    ensure_context();
+    if (s->host_exec && mode != PYC_REPLAY_SERVER)
+      fail(PYC_E_ARG, "a host-executed server replays through the serving loop only");
+    if (!s->host_exec) ensure_context();
     if (mode == PYC_REPLAY_SERVER)
       replay_server(s, nreq, reqs, arrival_ns, results);
     else if (mode == PYC_REPLAY_DIRECT)

@@ -74,6 +74,10 @@ class pyc_request(ctypes.Structure):
                 ("scalars", ctypes.c_void_p), ("deadline_us", ctypes.c_int64)]
 
 
+HOST_EXEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(pyc_request),
+                                ctypes.c_void_p)
+
+
 class pyc_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_int), ("d_out", ctypes.c_void_p),
                 ("value", ctypes.c_ubyte * 16), ("t_submit_ns", ctypes.c_int64),
@@ -114,7 +118,8 @@ EXPORTED = [
     "pyc_reduce_autotune", "pyc_reduce_destroy", "pyc_cache_stats", "pyc_reduce_launch_static",
     "pyc_reduce_static_scratch", "pyc_reduce_shard", "pyc_reduce_combine",
     "pyc_map_check_bounds", "pyc_reduce_check_bounds", "pyc_test_inject",
-    "pyc_server_create", "pyc_server_submit", "pyc_server_poll", "pyc_server_release",
+    "pyc_server_create", "pyc_server_create_host", "pyc_server_submit", "pyc_server_poll",
+    "pyc_server_release",
     "pyc_server_get_stats", "pyc_server_destroy", "pyc_server_replay", "pyc_map_launch_host",
     "pyc_map_config", "pyc_reduce_config", "pyc_reduce_batched_autotune",
     "pyc_reduce_batched_config", "pyc_reduce_batched_plan",
@@ -220,6 +225,8 @@ def load(build_if_missing=True):
         "pyc_reduce_destroy": (None, [vp]),
         "pyc_cache_stats": (None, [ctypes.POINTER(i64)] * 3),
         "pyc_server_create": (st, [ctypes.POINTER(pyc_server_cfg), ctypes.POINTER(vp)]),
+        "pyc_server_create_host": (st, [ctypes.POINTER(pyc_server_cfg), HOST_EXEC_FN, vp,
+                                        ctypes.POINTER(vp)]),
         "pyc_server_submit": (st, [vp, ctypes.POINTER(pyc_request), ctypes.POINTER(ctypes.c_uint64)]),
         "pyc_server_poll": (st, [vp, ctypes.c_uint64, ctypes.POINTER(pyc_result), i64]),
         "pyc_server_release": (st, [vp, ctypes.c_uint64]),
@@ -692,6 +699,24 @@ def pyc_server_create(mem_budget_bytes, arena_bytes=0, num_streams=0, max_batch=
     return h
 
 
+_host_servers = {}  # server handle -> its executor callback (kept alive while it runs)
+
+
+def pyc_server_create_host(exec_fn, mem_budget_bytes, arena_bytes=0, num_streams=0,
+                           max_batch=0, max_inflight=0, max_queue=0):
+    """A serving loop whose batches run on the host (test hook, no GPU needed):
+    exec_fn(req, value) is called once per request on the executor thread with
+    req a pyc_request (ptrs: the arrays, server outputs filled in) and value the
+    address of the result bytes of a map-reduce; it returns a status (0 = OK)."""
+    cb = HOST_EXEC_FN(lambda user, req, value: int(exec_fn(req.contents, value)))
+    cfg = pyc_server_cfg(int(mem_budget_bytes), int(arena_bytes), num_streams, max_batch,
+                         max_inflight, max_queue)
+    h = ctypes.c_void_p()
+    _check(load().pyc_server_create_host(ctypes.byref(cfg), cb, None, ctypes.byref(h)))
+    _host_servers[h.value] = cb
+    return h
+
+
 def make_request(kind, handle, n, ptrs, scalars=None, deadline_us=0):
     """A pyc_request plus the buffers it points to (keep the tuple alive)."""
     arr = _ptr_array(ptrs)
@@ -731,6 +756,7 @@ def pyc_server_get_stats(s):
 
 def pyc_server_destroy(s):
     load().pyc_server_destroy(s)
+    _host_servers.pop(s.value if isinstance(s, ctypes.c_void_p) else s, None)
 
 
 class RequestTable:
