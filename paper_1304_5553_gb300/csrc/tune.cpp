@@ -29,6 +29,7 @@ bool field(const std::string& line, const char* name, std::string* out) {
   size_t p = line.find(pat);
   if (p == std::string::npos) return false;
   p += pat.size();
+  while (p < line.size() && (line[p] == ' ' || line[p] == '\t')) ++p;  // "name": value
   if (p < line.size() && line[p] == '"') {
     size_t e = line.find('"', p + 1);
     if (e == std::string::npos) return false;

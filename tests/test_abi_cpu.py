@@ -769,3 +769,61 @@ def test_partial_overlap_with_a_written_array_is_an_argument_error():
     finally:
         pyc.pyc_map_destroy(m)
         pyc.pyc_scan_destroy(s)
+
+
+_TUNE_CHILD = r"""
+import json, os, sys
+sys.path.insert(0, %r)
+from paper_1304_5553_gb300 import pyc
+
+def digest(data):
+    # the library's source digest (two 64-bit FNV-style lanes), the tuning cache's key
+    h1, h2, m = 1469598103934665603, 0x9E3779B97F4A7C15, (1 << 64) - 1
+    for c in data:
+        h1 = ((h1 ^ c) * 1099511628211) & m
+        h2 = (((h2 ^ c) * 0x100000001B3) + 0x632BE59BD9B4E019) & m
+        h2 ^= h2 >> 29
+    return "%%016x%%016x" %% (h1, h2)
+
+spec, stmt = "float *x, float *y", "y[i] = 3.0f * x[i]"
+h0 = pyc.pyc_map_create(spec, stmt)
+key = digest(pyc.pyc_map_source(h0).encode())
+# records as the library writes them (compact), and with spaces as json.dumps writes them
+rec = lambda **k: json.dumps(dict({"key": key, "kind": "map", "us": 1.0}, **k),
+                             separators=(",", ":") if k.get("bucket", 0) %% 2 else None)
+lines = [rec(bucket=10, vec_bytes=32, unroll=2, block=128),
+         rec(bucket=10, vec_bytes=16, unroll=1, block=512),        # a later line wins
+         rec(bucket=11, vec_bytes=32, unroll=4, block=64, kind="reduce"),  # another kind
+         json.dumps({"key": "0" * 32, "kind": "map", "bucket": 11, "vec_bytes": 32,
+                     "unroll": 4, "block": 64}),                   # another spec
+         rec(bucket=12, vec_bytes=8, unroll=2, block=128),         # not a valid variant
+         rec(bucket=13, vec_bytes=32, unroll=4, block=96)]
+with open(os.path.join(os.environ["PYC_CACHE_DIR"], "tune.jsonl"), "a") as f:
+    f.write("\n".join(lines) + "\n")
+h = pyc.pyc_map_create(spec, stmt)                                 # loads the cache
+out = {}
+for n in (2 ** 19 - 1, 2 ** 19, 2 ** 21 - 1, 2 ** 21, 2 ** 23, 2 ** 25, 2 ** 27 - 1, 2 ** 27):
+    out[n] = list(pyc.launch_config(h, n))
+fixed = pyc.pyc_map_create(spec, stmt, None, {"block": 256})      # options win over tuning
+out["fixed"] = list(pyc.launch_config(fixed, 2 ** 19))
+print(json.dumps(out))
+"""
+
+
+def test_tuning_cache_buckets(tmp_path):
+    """Tuned configurations persist per (source digest, kind, size bucket), the
+    bucket of n being half the bit length of n (two powers of two per bucket);
+    records of another kind or spec, or with an invalid variant, are ignored, a
+    later record of a bucket wins, and configuration options override."""
+    env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path))
+    out = subprocess.run([sys.executable, "-c", _TUNE_CHILD % ROOT], env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    default = [16, 4, 256]
+    want = {2 ** 19 - 1: default, 2 ** 19: [16, 1, 512], 2 ** 21 - 1: [16, 1, 512],
+            2 ** 21: default, 2 ** 23: default, 2 ** 25: [32, 4, 96], 2 ** 27 - 1: [32, 4, 96],
+            2 ** 27: default}
+    for n, cfg in want.items():
+        assert r[str(n)] == cfg, (n, r[str(n)])
+    assert r["fixed"] == [16, 1, 256]
