@@ -740,12 +740,17 @@ pyc_status pyc_server_replay(pyc_server_t s, int64_t nreq, const pyc_request* re
  *   PYC_INJECT_STALL_MS  the next serving-loop scheduler to wake sleeps `value` ms
  *                        before admitting requests (a late scheduler: deadlines
  *                        run out, PYC_E_TIMEOUT).
+ *   PYC_INJECT_ADMIT     the next `value` requests a serving loop comes to admit
+ *                        are rejected there, as one the budget can never hold:
+ *                        the request fails with PYC_E_NOMEM, those behind it
+ *                        are admitted as usual.
  * value = 0 clears the kind.  Nothing is injected into the GPU.  Process-wide;
  * not for production use.  Errors: PYC_E_ARG (unknown kind, value < 0). */
 typedef enum {
   PYC_INJECT_ALLOC = 0,
   PYC_INJECT_COMPILE = 1,
-  PYC_INJECT_STALL_MS = 2
+  PYC_INJECT_STALL_MS = 2,
+  PYC_INJECT_ADMIT = 3
 } pyc_inject_kind;
 pyc_status pyc_test_inject(pyc_inject_kind what, int64_t value);
 

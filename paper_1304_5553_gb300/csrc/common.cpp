@@ -8,7 +8,7 @@ namespace pyc {
 
 namespace {
 thread_local std::string t_last_error;
-std::atomic<int64_t> g_inject[3];  // pending failures by pyc_inject_kind
+std::atomic<int64_t> g_inject[4];  // pending failures by pyc_inject_kind
 
 int64_t take_one(std::atomic<int64_t>& c, bool all) {
   int64_t v = c.load();
@@ -19,7 +19,8 @@ int64_t take_one(std::atomic<int64_t>& c, bool all) {
 }  // namespace
 
 bool take_injected(pyc_inject_kind k) {
-  return (int)k >= 0 && (int)k < 2 && take_one(g_inject[(int)k], false) > 0;
+  return k != PYC_INJECT_STALL_MS && (int)k >= 0 && (int)k < 4 &&
+         take_one(g_inject[(int)k], false) > 0;
 }
 
 int64_t take_injected_stall_ms() { return take_one(g_inject[PYC_INJECT_STALL_MS], true); }
@@ -62,7 +63,7 @@ PYC_API const char* pyc_version(void) { return "pyc 0.1 (sm_103a)"; }
 
 PYC_API pyc_status pyc_test_inject(pyc_inject_kind what, int64_t value) {
   return pyc::guarded([&] {
-    if ((int)what < 0 || (int)what > 2) pyc::fail(PYC_E_ARG, "unknown injection kind");
+    if ((int)what < 0 || (int)what > 3) pyc::fail(PYC_E_ARG, "unknown injection kind");
     if (value < 0) pyc::fail(PYC_E_ARG, "value must be >= 0");
     pyc::g_inject[(int)what].store(value);
   });

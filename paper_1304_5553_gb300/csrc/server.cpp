@@ -428,6 +428,11 @@ void scheduler(pyc_server* s) {
         finish_req(s, r, PYC_E_TIMEOUT, t);
         continue;
       }
+      if (take_injected(PYC_INJECT_ADMIT)) {  // an injected rejection (pyc_test_inject)
+        s->queue.pop_front();
+        finish_req(s, r, PYC_E_NOMEM, t);
+        continue;
+      }
       if (s->admitted_bytes + r->bytes > s->cfg.mem_budget_bytes) break;
       bool ok = true;
       for (int slot : r->alloc_slots) {

@@ -346,7 +346,7 @@ def pyc_reduce_combine(h, k, d_recs, d_out, stream=None):
     _check(load().pyc_reduce_combine(h, int(k), d_recs, d_out, _stream(stream)))
 
 
-PYC_INJECT_ALLOC, PYC_INJECT_COMPILE, PYC_INJECT_STALL_MS = 0, 1, 2
+PYC_INJECT_ALLOC, PYC_INJECT_COMPILE, PYC_INJECT_STALL_MS, PYC_INJECT_ADMIT = 0, 1, 2, 3
 
 
 def pyc_test_inject(what, value):

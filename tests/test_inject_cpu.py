@@ -4,7 +4,8 @@ A failed run-time compilation must surface as PYC_E_COMPILE and leave nothing
 behind (the next creation of the same spec compiles it); a failed system
 allocation in a memory pool must first give the retained blocks back and retry
 once, and when that fails too, report PYC_E_NOMEM with the pool's statistics
-unchanged.
+unchanged; a rejection injected at a serving loop's admission fails that
+request alone (the loop runs here with host-executed batches).
 """
 import os
 import threading
@@ -18,7 +19,8 @@ from paper_1304_5553_gb300 import pyc
 @pytest.fixture(autouse=True)
 def _clear():
     yield
-    for k in (pyc.PYC_INJECT_ALLOC, pyc.PYC_INJECT_COMPILE, pyc.PYC_INJECT_STALL_MS):
+    for k in (pyc.PYC_INJECT_ALLOC, pyc.PYC_INJECT_COMPILE, pyc.PYC_INJECT_STALL_MS,
+              pyc.PYC_INJECT_ADMIT):
         pyc.pyc_test_inject(k, 0)
 
 
@@ -28,7 +30,7 @@ def _unique_stmt():
 
 def test_argument_errors():
     lib = pyc.load()
-    assert lib.pyc_test_inject(3, 1) == pyc.PYC_E_ARG
+    assert lib.pyc_test_inject(4, 1) == pyc.PYC_E_ARG
     assert lib.pyc_test_inject(-1, 1) == pyc.PYC_E_ARG
     assert lib.pyc_test_inject(pyc.PYC_INJECT_ALLOC, -1) == pyc.PYC_E_ARG
 
@@ -108,3 +110,38 @@ def test_pool_retries_after_returning_retained_blocks():
         pyc.pyc_pool_free(p, q)
     finally:
         pyc.pyc_pool_destroy(p)
+
+
+def test_injected_admission_rejection_fails_only_those_requests():
+    """Two injected rejections at admission: the first two requests reaching
+    admission fail with PYC_E_NOMEM, the others are admitted and served, and no
+    budget is left counted for the rejected ones."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_1304_5553_gb300 import stock
+    x = np.arange(4096, dtype=np.float32)
+    h = stock.create("dot_f32")
+
+    def exec_fn(req, value):
+        a = np.ctypeslib.as_array(ctypes.cast(req.ptrs[0], ctypes.POINTER(ctypes.c_float)),
+                                  shape=(req.n,))
+        ctypes.cast(value, ctypes.POINTER(ctypes.c_float))[0] = float(np.dot(a, a))
+        return pyc.PYC_OK
+
+    srv = pyc.pyc_server_create_host(exec_fn, 1 << 24)
+    try:
+        pyc.pyc_test_inject(pyc.PYC_INJECT_ADMIT, 2)
+        reqs = [pyc.make_request(pyc.PYC_REQ_REDUCE, h, 100 + k, [x.ctypes.data] * 2)
+                for k in range(5)]
+        ids = [pyc.pyc_server_submit(srv, r) for r in reqs]
+        st = [pyc.pyc_server_poll(srv, i, 5_000_000).status for i in ids]
+        assert st == [pyc.PYC_E_NOMEM] * 2 + [pyc.PYC_OK] * 3
+        stats = pyc.pyc_server_get_stats(srv)
+        assert stats["failed"] == 2 and stats["completed"] == 3
+        for i in ids:
+            pyc.pyc_server_release(srv, i)
+        assert pyc.pyc_server_get_stats(srv)["admitted_bytes"] == 0
+    finally:
+        pyc.pyc_server_destroy(srv)
