@@ -309,7 +309,11 @@ pyc_reduce::Workspace& reduce_workspace(pyc_reduce* h, CUstream stream) {
   PYC_CU(drv().cuMemAlloc(&w.base, total));
   w.part = w.base;
   w.ticket = w.base + part_bytes;
-  PYC_CU(drv().cuMemsetD8Async(w.ticket, 0, 256, stream));
+  const CUresult r = drv().cuMemsetD8Async(w.ticket, 0, 256, stream);
+  if (r != CUDA_SUCCESS) {
+    drv().cuMemFree(w.base);
+    ::pyc::check(r, "cuMemsetD8Async");
+  }
   return h->ws.emplace(key, w).first->second;
 }
 

@@ -97,33 +97,39 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
   size_t b_part = up((size_t)std::max<int64_t>(slots, 1) * g.acc_bytes);
   const Driver& d = drv();
   PYC_CU(d.cuMemAlloc(&plan->mem, b_tasks + b_items + b_tickets + b_ctl + b_part));
-  plan->tasks = plan->mem;
-  plan->items = plan->tasks + b_tasks;
-  plan->tickets = plan->items + b_items;
-  plan->ctl = plan->tickets + b_tickets;
-  plan->part = plan->ctl + b_ctl;
-  if (!tasks.empty()) PYC_CU(d.cuMemcpyHtoD(plan->tasks, tasks.data(), tasks.size()));
-  if (!items.empty())
-    PYC_CU(d.cuMemcpyHtoD(plan->items, items.data(), items.size() * sizeof(ReduceItem)));
-  PYC_CU(d.cuMemsetD8(plan->tickets, 0, b_tickets + b_ctl));
-
-  plan->f = h->batched_module(cfg).function(h->rbatch_name(cfg));
-  int resident = resident_ctas(plan->f, cfg.block);
-  plan->grid = std::max(1, std::min(resident, plan->nitems));
-
-  CUstream cs = capture_stream();
-  PYC_CU(d.cuStreamBeginCapture(cs, CU_STREAM_CAPTURE_MODE_THREAD_LOCAL));
   try {
-    plan->launch_direct(cs);
+    plan->tasks = plan->mem;
+    plan->items = plan->tasks + b_tasks;
+    plan->tickets = plan->items + b_items;
+    plan->ctl = plan->tickets + b_tickets;
+    plan->part = plan->ctl + b_ctl;
+    if (!tasks.empty()) PYC_CU(d.cuMemcpyHtoD(plan->tasks, tasks.data(), tasks.size()));
+    if (!items.empty())
+      PYC_CU(d.cuMemcpyHtoD(plan->items, items.data(), items.size() * sizeof(ReduceItem)));
+    PYC_CU(d.cuMemsetD8(plan->tickets, 0, b_tickets + b_ctl));
+
+    plan->f = h->batched_module(cfg).function(h->rbatch_name(cfg));
+    int resident = resident_ctas(plan->f, cfg.block);
+    plan->grid = std::max(1, std::min(resident, plan->nitems));
+
+    CUstream cs = capture_stream();
+    PYC_CU(d.cuStreamBeginCapture(cs, CU_STREAM_CAPTURE_MODE_THREAD_LOCAL));
+    try {
+      plan->launch_direct(cs);
+    } catch (...) {
+      CUgraph tmp = nullptr;
+      d.cuStreamEndCapture(cs, &tmp);
+      if (tmp) d.cuGraphDestroy(tmp);
+      throw;
+    }
+    PYC_CU(d.cuStreamEndCapture(cs, &plan->graph));
+    PYC_CU(d.cuGraphInstantiateWithFlags(&plan->exec, plan->graph, 0));
   } catch (...) {
-    CUgraph tmp = nullptr;
-    d.cuStreamEndCapture(cs, &tmp);
-    if (tmp) d.cuGraphDestroy(tmp);
+    // a copy, a compilation (the register-lean module is built on first use) or
+    // the graph failed: the plan's memory goes back before the error surfaces
     plan->release();
     throw;
   }
-  PYC_CU(d.cuStreamEndCapture(cs, &plan->graph));
-  PYC_CU(d.cuGraphInstantiateWithFlags(&plan->exec, plan->graph, 0));
   return plan;
 }
 

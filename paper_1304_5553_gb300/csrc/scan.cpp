@@ -79,7 +79,12 @@ ScanParams scan_workspace(pyc_scan* h, CUstream stream, int64_t ntiles) {
     int64_t cap = std::max<int64_t>(4096, (ntiles + 63) / 64 * 64);
     int64_t bytes = kCtlBytes + flag_bytes(cap) + 2 * align256(cap * acc);
     PYC_CU(drv().cuMemAlloc(&w.base, (size_t)bytes));
-    PYC_CU(drv().cuMemsetD8Async(w.base, 0, (size_t)(kCtlBytes + flag_bytes(cap)), stream));
+    const CUresult r = drv().cuMemsetD8Async(w.base, 0, (size_t)(kCtlBytes + flag_bytes(cap)), stream);
+    if (r != CUDA_SUCCESS) {
+      drv().cuMemFree(w.base);
+      w.base = 0;
+      ::pyc::check(r, "cuMemsetD8Async");
+    }
     w.cap = cap;
     w.epoch = 0;
   }

@@ -889,16 +889,37 @@ void replay_direct(pyc_server* s, int64_t nreq, const pyc_request* reqs, const i
   const Driver& d = drv();
   CUstream st = s->streams[0];
   const int kEvents = 4096;
-  std::vector<CUevent> evs(kEvents);
-  for (auto& e : evs) PYC_CU(d.cuEventCreate(&e, CU_EVENT_DISABLE_TIMING));
   struct Out {
     int64_t k;
     std::vector<int64_t> offs;
     void* out = nullptr;  // first server-allocated output
     CUdeviceptr val = 0;
   };
-  std::deque<Out> pending;  // launched, in stream order
-  CUdeviceptr vals = 0;
+  // the replay's events, result buffer and the arena blocks of launched
+  // requests go back however the replay ends (an error included)
+  struct Held {
+    pyc_server* s;
+    CUstream st;
+    std::vector<CUevent> evs;
+    CUdeviceptr vals = 0;
+    std::deque<Out> pending;  // launched, in stream order
+    ~Held() {
+      const Driver& dd = drv();
+      dd.cuStreamSynchronize(st);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (const Out& o : pending)
+          for (int64_t off : o.offs) s->arena.release(off);
+      }
+      for (CUevent e : evs)
+        if (e) dd.cuEventDestroy(e);
+      if (vals) dd.cuMemFree(vals);
+    }
+  } held{s, st, std::vector<CUevent>(kEvents, nullptr)};
+  std::vector<CUevent>& evs = held.evs;
+  std::deque<Out>& pending = held.pending;
+  for (auto& e : evs) PYC_CU(d.cuEventCreate(&e, CU_EVENT_DISABLE_TIMING));
+  CUdeviceptr& vals = held.vals;
   PYC_CU(d.cuMemAlloc(&vals, (size_t)kEvents * 16));
   std::vector<unsigned char> host_val(16);
   const int64_t t0 = now_ns();
@@ -988,8 +1009,6 @@ void replay_direct(pyc_server* s, int64_t nreq, const pyc_request* reqs, const i
     }
     std::this_thread::sleep_for(std::chrono::microseconds(2));
   }
-  for (auto& e : evs) d.cuEventDestroy(e);
-  d.cuMemFree(vals);
 }
 
 }  // namespace
