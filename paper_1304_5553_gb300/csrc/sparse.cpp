@@ -622,6 +622,7 @@ pyc_csr::Work& cg_work(pyc_csr* a, CUstream s, int64_t n) {
       PYC_CU(drv().cuStreamSynchronize(s));
       drv().cuMemFree(w.base);
       w.base = 0;
+      w.n = 0;  // until the new block exists (an allocation below may fail)
     }
     const int64_t vb = (int64_t)vbytes(a->vt);
     const int64_t vec = (n * vb + 255) / 256 * 256;

@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(autouse=True)
 def _clear():
     yield
-    for k in (pyc.PYC_INJECT_ALLOC, pyc.PYC_INJECT_COMPILE, pyc.PYC_INJECT_STALL_MS):
+    for k in (pyc.PYC_INJECT_ALLOC, pyc.PYC_INJECT_COMPILE, pyc.PYC_INJECT_STALL_MS,
+              pyc.PYC_INJECT_ADMIT):
         pyc.pyc_test_inject(k, 0)
 
 
@@ -168,3 +169,35 @@ def test_arena_running_dry_waits_for_a_release():
         assert st["arena_in_use"] == 0 and st["admitted_bytes"] == 0 and st["failed"] == 0
     finally:
         pyc.pyc_server_destroy(srv)
+
+
+def test_cg_work_space_allocation_failure():
+    """A solver's first use on a stream allocates its work space (and its dot
+    products' workspaces): an injected failure there is PYC_E_NOMEM, x is left
+    as it was, and the next solve on the same stream converges."""
+    nx = 64
+    rp, c, v = inputs.poisson2d(nx, nx, np.float64)
+    n = nx * nx
+    d = [torch.from_numpy(t).cuda() for t in (rp, c, v)]
+    a = pyc.pyc_csr_create(n, n, c.size, *(t.data_ptr() for t in d), pyc.PYC_F64)
+    try:
+        b = torch.ones(n, dtype=torch.float64, device="cuda")
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        s2 = torch.cuda.Stream()
+        pyc.pyc_test_inject(pyc.PYC_INJECT_ALLOC, 1)
+        with pytest.raises(pyc.PycError) as e:
+            pyc.pyc_cg_solve(a, b.data_ptr(), x.data_ptr(), 1e-10, 2000, s2.cuda_stream)
+        assert e.value.status == pyc.PYC_E_NOMEM
+        s2.synchronize()
+        assert torch.count_nonzero(x).item() == 0
+        info = pyc.pyc_cg_solve(a, b.data_ptr(), x.data_ptr(), 1e-10, 2000, s2.cuda_stream)
+        s2.synchronize()
+        assert info["converged"]
+        # the true residual of the solution, in binary64 on the host
+        xs = x.cpu().numpy()
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        ax = np.zeros(n)
+        np.add.at(ax, rows, v * xs[c])
+        assert np.linalg.norm(1.0 - ax) <= 1e-9 * np.sqrt(n)
+    finally:
+        pyc.pyc_csr_destroy(a)
