@@ -219,7 +219,14 @@ const char* pyc_map_source(pyc_map_t h);
  * arrays together, halved while the device cannot hold them), remember the
  * fastest for the handle and persist it in the tuning cache.  Synchronises the
  * stream.  (Automated tuning, Sec. 3.3.1.)  pyc_reduce_autotune and
- * pyc_scan_autotune size their scratch the same way. */
+ * pyc_scan_autotune size their scratch the same way.
+ * With the environment variable PYC_AUTOTUNE=1, pyc_map_launch,
+ * pyc_reduce_launch and pyc_scan_launch do this themselves: a launch at a size
+ * bucket with no tuned configuration (none found in the tuning cache either)
+ * runs with the default configuration and then tunes the bucket on its stream,
+ * so that the launches after it use the tuned one -- unless the handle's options
+ * fix the whole configuration, the stream is being captured, or another thread
+ * is tuning the handle.  That launch allocates scratch and synchronises. */
 pyc_status pyc_map_autotune(pyc_map_t h, int64_t n, pyc_stream_t stream);
 
 /* The launch configuration (vector bytes, unroll, block) a launch of n

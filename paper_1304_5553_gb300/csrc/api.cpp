@@ -369,8 +369,14 @@ PYC_API pyc_status pyc_map_launch(pyc_map_t h, int64_t n, void* const* ptrs, con
                                   pyc_stream_t stream) {
   return guarded([&] {
     if (!h) fail(PYC_E_ARG, "handle is NULL");
+    const CUstream s = reinterpret_cast<CUstream>(stream);
     LaunchCfg cfg = choose_cfg(*h, n, false);
-    launch_map(h, cfg, n, ptrs, scalars, reinterpret_cast<CUstream>(stream));
+    launch_map(h, cfg, n, ptrs, scalars, s);
+    // PYC_AUTOTUNE=1: a first launch at an untuned size bucket tunes it for the next
+    autotune_if_due(*h, n, s, false,
+                    [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc,
+                        CUdeviceptr, CUstream ls) { launch_map(h, c, nt, p, sc, ls); },
+                    true);
   });
 }
 
@@ -496,8 +502,16 @@ PYC_API pyc_status pyc_reduce_launch(pyc_reduce_t h, int64_t n, void* const* ptr
                                      const void* scalars, void* d_out, pyc_stream_t stream) {
   return guarded([&] {
     if (!h) fail(PYC_E_ARG, "handle is NULL");
+    const CUstream s = reinterpret_cast<CUstream>(stream);
     LaunchCfg cfg = choose_cfg(*h, n, true);
-    launch_reduce(h, cfg, n, ptrs, scalars, d_out, reinterpret_cast<CUstream>(stream));
+    launch_reduce(h, cfg, n, ptrs, scalars, d_out, s);
+    // PYC_AUTOTUNE=1: a first launch at an untuned size bucket tunes it for the next
+    autotune_if_due(*h, n, s, true,
+                    [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc,
+                        CUdeviceptr out, CUstream ls) {
+                      launch_reduce(h, c, nt, p, sc, reinterpret_cast<void*>(out), ls);
+                    },
+                    true);
   });
 }
 

@@ -33,6 +33,7 @@ int size_bucket(int64_t n);
 struct TuneTable {
   std::mutex mu;
   std::map<int, LaunchCfg> by_bucket;
+  std::mutex tuning;  // held while a launch tunes the handle (PYC_AUTOTUNE)
 };
 
 struct BatchPlan;  // batched reducer plan (batched.cpp)
@@ -173,6 +174,13 @@ using TuneLaunch = std::function<void(const LaunchCfg&, int64_t, void* const*, c
                                       CUdeviceptr, CUstream)>;
 void autotune_generic(HandleBase& h, int64_t n, CUstream stream, bool reduce,
                       const TuneLaunch& launch_one, bool graph_timing = false);
+
+// With the environment variable PYC_AUTOTUNE=1, tunes the size bucket of n
+// after a launch when it has no tuned configuration yet, the handle's options
+// leave something to choose, the stream is not being captured and no other
+// thread is tuning the handle; otherwise does nothing.
+void autotune_if_due(HandleBase& h, int64_t n, CUstream stream, bool reduce,
+                     const TuneLaunch& launch_one, bool graph_timing = false);
 
 // One private non-blocking stream per context, used for graph capture.
 CUstream capture_stream();

@@ -225,9 +225,14 @@ PYC_API pyc_status pyc_scan_launch(pyc_scan_t h, int64_t n, void* const* ptrs,
                                    const void* scalars, pyc_stream_t stream) {
   return guarded([&] {
     if (!h) fail(PYC_E_ARG, "handle is NULL");
+    const CUstream s = reinterpret_cast<CUstream>(stream);
     LaunchCfg cfg = choose_cfg(*h, n, true);
     if (cfg.v.vec_bytes != 16 && cfg.v.vec_bytes != 32) fail(PYC_E_ARG, "bad vec_bytes");
-    launch_scan(h, cfg, n, ptrs, scalars, reinterpret_cast<CUstream>(stream));
+    launch_scan(h, cfg, n, ptrs, scalars, s);
+    // PYC_AUTOTUNE=1: a first launch at an untuned size bucket tunes it for the next
+    autotune_if_due(*h, n, s, true,
+                    [&](const LaunchCfg& c, int64_t nt, void* const* p, const void* sc,
+                        CUdeviceptr, CUstream) { launch_scan(h, c, nt, p, sc, s); });
   });
 }
 

@@ -212,6 +212,25 @@ void autotune_generic(HandleBase& h, int64_t n, CUstream stream, bool reduce,
   autotune(&h, n, stream, reduce, launch_one, graph_timing);
 }
 
+void autotune_if_due(HandleBase& h, int64_t n, CUstream stream, bool reduce,
+                     const TuneLaunch& launch_one, bool graph_timing) {
+  const char* e = std::getenv("PYC_AUTOTUNE");
+  if (!e || e[0] != '1' || n <= 0) return;
+  if (h.opts.block && h.opts.vec_bytes && h.opts.items_per_thread) return;  // nothing to choose
+  auto tuned = [&] {
+    std::lock_guard<std::mutex> lk(h.tune.mu);
+    return h.tune.by_bucket.count(size_bucket(n)) > 0;
+  };
+  if (tuned()) return;
+  // tuning allocates and synchronises: never inside a stream capture
+  CUstreamCaptureStatus cap = CU_STREAM_CAPTURE_STATUS_NONE;
+  if (stream) PYC_CU(drv().cuStreamIsCapturing(stream, &cap));
+  if (cap != CU_STREAM_CAPTURE_STATUS_NONE) return;
+  std::unique_lock<std::mutex> busy(h.tune.tuning, std::try_to_lock);
+  if (!busy.owns_lock() || tuned()) return;  // another thread tunes (or did): launch as is
+  autotune(&h, n, stream, reduce, launch_one, graph_timing);
+}
+
 void tune_cache_load(HandleBase& h, bool reduce) {
   std::string path = tune_path();
   if (path.empty()) return;
