@@ -765,7 +765,10 @@ pyc_status pyc_test_inject(pyc_inject_kind what, int64_t value);
 
 /* Kernel cache statistics since process start: compiled = NVRTC compilations,
  * disk_hits = modules read from the on-disk cache, mem_hits = in-memory hits.
- * The on-disk cache lives in $PYC_CACHE_DIR (default $HOME/.cache/pyc). */
+ * The on-disk cache lives in $PYC_CACHE_DIR (default $HOME/.cache/pyc).  With
+ * the environment variable PYC_LOG=1 the library writes one line to stderr for
+ * each compilation (with its time), disk-cache load, tuning result, segmented
+ * plan and server creation or destruction. */
 void pyc_cache_stats(int64_t* compiled, int64_t* disk_hits, int64_t* mem_hits);
 
 #ifdef __cplusplus

@@ -124,6 +124,9 @@ std::unique_ptr<BatchPlan> build_plan(pyc_reduce* h, int64_t nseg, const int64_t
     }
     PYC_CU(d.cuStreamEndCapture(cs, &plan->graph));
     PYC_CU(d.cuGraphInstantiateWithFlags(&plan->exec, plan->graph, 0));
+    log_event("segmented plan for %lld segments: %d work items, %zu bytes on the device, %s",
+              (long long)nseg, plan->nitems, b_tasks + b_items + b_tickets + b_ctl + b_part,
+              h->rbatch_name(cfg).c_str());
   } catch (...) {
     // a copy, a compilation (the register-lean module is built on first use) or
     // the graph failed: the plan's memory goes back before the error surfaces

@@ -3,6 +3,9 @@
 #include "common.h"
 
 #include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
 
 namespace pyc {
 
@@ -26,6 +29,20 @@ bool take_injected(pyc_inject_kind k) {
 int64_t take_injected_stall_ms() { return take_one(g_inject[PYC_INJECT_STALL_MS], true); }
 
 void set_last_error(const std::string& m) { t_last_error = m; }
+
+void log_event(const char* fmt, ...) {
+  static const bool on = [] {
+    const char* e = std::getenv("PYC_LOG");
+    return e && e[0] == '1';
+  }();
+  if (!on) return;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  std::fprintf(stderr, "pyc: %s\n", buf);
+}
 void clear_last_error() { t_last_error.clear(); }
 
 const TypeInfo& type_info(pyc_dtype t) {

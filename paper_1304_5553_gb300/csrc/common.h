@@ -21,6 +21,12 @@ struct Error : std::runtime_error {
 [[noreturn]] inline void fail(pyc_status s, const std::string& m) { throw Error(s, m); }
 
 void set_last_error(const std::string& m);
+
+// One line on stderr ("pyc: ...") for the library's slow or stateful events --
+// compilations, disk-cache loads, tuning results, segmented plans, server
+// lifetimes -- when the environment variable PYC_LOG=1 was set at the first
+// call; otherwise nothing.
+void log_event(const char* fmt, ...) __attribute__((format(printf, 1, 2)));
 void clear_last_error();
 
 // Runs f(); maps exceptions to a status and records the message.

@@ -1,4 +1,5 @@
 // NVRTC driver and kernel cache (see kcache.h).
+#include <chrono>
 #include "kcache.h"
 
 #include <dlfcn.h>
@@ -336,11 +337,17 @@ std::shared_ptr<Module> load_or_compile(const std::string& key, const std::strin
     if (ok && unpack_record(rec, key_text, &cubins) && cubins.size() == text.size()) {
       have = true;
       ++g_disk;
+      log_event("loaded %zu kernel units from the disk cache (%s)", cubins.size(), key.c_str());
     }
   }
   if (!have) {
+    const auto t0 = std::chrono::steady_clock::now();
     cubins = compile_units(text, fmad);
     ++g_compiled;
+    log_event("compiled %zu kernel units with NVRTC in %.0f ms (%s)", cubins.size(),
+              std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                  .count(),
+              key.c_str());
     if (!path.empty()) {
       mkdirs(dir);
       std::string tmp = path + ".tmp" + std::to_string(getpid());

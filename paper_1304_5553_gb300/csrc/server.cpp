@@ -626,6 +626,9 @@ PYC_API pyc_status pyc_server_create(const pyc_server_cfg* cfg, pyc_server_t* ou
     }
     pyc_server* raw = s.get();
     s->th = std::thread([raw] { scheduler(raw); });
+    log_event("server created: budget %lld bytes, arena %lld bytes, %d streams, batches of "
+              "up to %d, %d in flight", (long long)c.mem_budget_bytes, (long long)c.arena_bytes,
+              c.num_streams, c.max_batch, c.max_inflight);
     *out = s.release();
   });
 }
@@ -649,6 +652,8 @@ PYC_API pyc_status pyc_server_create_host(const pyc_server_cfg* cfg, pyc_host_ex
     pyc_server* raw = s.get();
     s->exec_th = std::thread([raw] { host_executor(raw); });
     s->th = std::thread([raw] { scheduler(raw); });
+    log_event("server created with host-executed batches: budget %lld bytes, batches of up to "
+              "%d, %d in flight", (long long)c.mem_budget_bytes, c.max_batch, c.max_inflight);
     *out = s.release();
   });
 }
@@ -771,6 +776,9 @@ PYC_API pyc_status pyc_server_get_stats(pyc_server_t s, pyc_server_stats* st) {
 
 PYC_API void pyc_server_destroy(pyc_server_t s) {
   if (!s) return;
+  log_event("server destroyed: %lld requests completed, %lld failed, %lld batches",
+            (long long)s->stats.completed, (long long)s->stats.failed,
+            (long long)s->stats.batches);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;

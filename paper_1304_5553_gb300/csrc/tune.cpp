@@ -202,6 +202,9 @@ void autotune(H* h, int64_t n, CUstream stream, bool reduce, Launch&& launch_one
     std::lock_guard<std::mutex> lk(h->tune.mu);
     h->tune.by_bucket[bucket] = best;
   }
+  log_event("tuned %s %s for size bucket %d (n = %lld): vec%d_u%d_b%d, %.2f us", reduce ? "reduce" : "map",
+            h->tag.c_str(), bucket, (long long)n, best.v.vec_bytes, best.v.unroll, best.block,
+            best_us);
   tune_cache_store(*h, reduce, bucket, best, best_us);
 }
 

@@ -827,3 +827,32 @@ def test_tuning_cache_buckets(tmp_path):
     for n, cfg in want.items():
         assert r[str(n)] == cfg, (n, r[str(n)])
     assert r["fixed"] == [16, 1, 256]
+
+
+_LOG_CHILD = r"""
+import sys
+sys.path.insert(0, %r)
+from paper_1304_5553_gb300 import pyc
+h = pyc.pyc_map_create("float *x, float *y", "y[i] = x[i] * 9.0f - 1.0f")
+s = pyc.pyc_server_create_host(lambda req, value: 0, 1 << 20)
+pyc.pyc_server_destroy(s)
+"""
+
+
+def test_event_log(tmp_path):
+    """PYC_LOG=1: one stderr line per compilation (and, in a later process, per
+    disk-cache load) and per server creation and destruction; nothing without."""
+    def run(log):
+        env = dict(os.environ, PYC_CACHE_DIR=str(tmp_path), PYC_LOG=log)
+        p = subprocess.run([sys.executable, "-c", _LOG_CHILD % ROOT], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert p.returncode == 0, p.stderr
+        return [l for l in p.stderr.splitlines() if l.startswith("pyc: ")]
+    first = run("1")
+    assert any(re.match(r"pyc: compiled \d+ kernel units with NVRTC in \d+ ms", l) for l in first)
+    assert any(l.startswith("pyc: server created with host-executed batches") for l in first)
+    assert any(l.startswith("pyc: server destroyed: 0 requests completed") for l in first)
+    second = run("1")
+    assert any(l.startswith("pyc: loaded") and "from the disk cache" in l for l in second)
+    assert not any("compiled" in l for l in second)
+    assert run("0") == []
