@@ -258,3 +258,38 @@ def test_replay_through_the_host_executed_loop(pool):
         assert e.value.status == pyc.PYC_E_ARG
     finally:
         pyc.pyc_server_destroy(srv)
+
+
+def test_size_limits_and_empty_requests(pool):
+    """n = 0 requests complete (a map-reduce gives its neutral element, a map
+    writes nothing and gets no output); n above 2^34 and negative n are argument
+    errors; a request larger than the whole budget is refused at submit with
+    PYC_E_NOMEM while smaller ones go on being served."""
+    ex = Executor()
+    n = 1000
+    per = n * 8 + 4
+    srv = pyc.pyc_server_create_host(ex, 3 * per)
+    try:
+        z_dot = pyc.pyc_server_submit(srv, _req(pool, pyc.PYC_REQ_REDUCE, 0, 0)[0])
+        z_map = pyc.pyc_server_submit(srv, _req(pool, pyc.PYC_REQ_MAP, 0, 0)[0])
+        res = pyc.pyc_server_poll(srv, z_dot, 5_000_000)
+        assert res.status == pyc.PYC_OK
+        assert ctypes.c_float.from_buffer_copy(bytes(res.value[:4])).value == 0.0
+        pyc.pyc_server_release(srv, z_dot)
+        res = pyc.pyc_server_poll(srv, z_map, 5_000_000)
+        assert res.status == pyc.PYC_OK
+        pyc.pyc_server_release(srv, z_map)
+        for bad_n, status in ((-1, pyc.PYC_E_ARG), ((1 << 34) + 1, pyc.PYC_E_ARG),
+                              (4 * n, pyc.PYC_E_NOMEM)):
+            x, y = pool
+            r = pyc.make_request(pyc.PYC_REQ_REDUCE, stock.create("dot_f32"), bad_n,
+                                 [x.ctypes.data, y.ctypes.data])
+            with pytest.raises(pyc.PycError) as e:
+                pyc.pyc_server_submit(srv, r)
+            assert e.value.status == status, bad_n
+        ok = pyc.pyc_server_submit(srv, _req(pool, pyc.PYC_REQ_REDUCE, n, 3)[0])
+        _check(pool, pyc.PYC_REQ_REDUCE, n, 3, pyc.pyc_server_poll(srv, ok, 5_000_000))
+        pyc.pyc_server_release(srv, ok)
+        assert pyc.pyc_server_get_stats(srv)["admitted_bytes"] == 0
+    finally:
+        pyc.pyc_server_destroy(srv)
