@@ -707,8 +707,15 @@ def pyc_server_create_host(exec_fn, mem_budget_bytes, arena_bytes=0, num_streams
     """A serving loop whose batches run on the host (test hook, no GPU needed):
     exec_fn(req, value) is called once per request on the executor thread with
     req a pyc_request (ptrs: the arrays, server outputs filled in) and value the
-    address of the result bytes of a map-reduce; it returns a status (0 = OK)."""
-    cb = HOST_EXEC_FN(lambda user, req, value: int(exec_fn(req.contents, value)))
+    address of the result bytes of a map-reduce; it returns a status (0 = OK).  An
+    exception raised by exec_fn fails that request with PYC_E_INTERNAL."""
+    def call(user, req, value):
+        try:
+            return int(exec_fn(req.contents, value))
+        except Exception:  # an executor that raised fails its request
+            return PYC_E_INTERNAL
+
+    cb = HOST_EXEC_FN(call)
     cfg = pyc_server_cfg(int(mem_budget_bytes), int(arena_bytes), num_streams, max_batch,
                          max_inflight, max_queue)
     h = ctypes.c_void_p()

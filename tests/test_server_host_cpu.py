@@ -293,3 +293,20 @@ def test_size_limits_and_empty_requests(pool):
         assert pyc.pyc_server_get_stats(srv)["admitted_bytes"] == 0
     finally:
         pyc.pyc_server_destroy(srv)
+
+
+def test_an_executor_that_raises_fails_its_request(pool):
+    def exec_fn(req, value):
+        if req.n == 13:
+            raise ValueError("executor fault")
+        ctypes.cast(value, ctypes.POINTER(ctypes.c_float))[0] = 1.0
+        return pyc.PYC_OK
+
+    srv = pyc.pyc_server_create_host(exec_fn, 1 << 24)
+    try:
+        bad = pyc.pyc_server_submit(srv, _req(pool, pyc.PYC_REQ_REDUCE, 13, 0)[0])
+        good = pyc.pyc_server_submit(srv, _req(pool, pyc.PYC_REQ_REDUCE, 14, 0)[0])
+        assert pyc.pyc_server_poll(srv, bad, 5_000_000).status == pyc.PYC_E_INTERNAL
+        assert pyc.pyc_server_poll(srv, good, 5_000_000).status == pyc.PYC_OK
+    finally:
+        pyc.pyc_server_destroy(srv)
