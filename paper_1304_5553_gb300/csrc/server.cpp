@@ -833,9 +833,15 @@ void replay_server(pyc_server* s, int64_t nreq, const pyc_request* reqs, const i
   std::unordered_map<uint64_t, int64_t> index;
   const int64_t t0 = now_ns();
   int64_t next = 0, done = 0;
+  // Submissions go in bursts, with finished requests collected and released in
+  // between: a client that submitted everything before releasing anything would
+  // hold the budget with finished requests and stall admission (with 50,000
+  // requests due at once, about 34 ms of submissions).
+  constexpr int kBurst = 64;
   while (done < nreq) {
-    // submit everything that is due
-    while (next < nreq && (!arr || now_ns() >= t0 + arr[next])) {
+    // submit what is due, up to a burst
+    for (int burst = 0; burst < kBurst && next < nreq && (!arr || now_ns() >= t0 + arr[next]);
+         ++burst) {
       uint64_t id;
       pyc_status st = pyc_server_submit(s, &reqs[next], &id);
       int64_t t_arr = arr ? t0 + arr[next] : t0;
@@ -854,10 +860,13 @@ void replay_server(pyc_server* s, int64_t nreq, const pyc_request* reqs, const i
     // collect finished requests, release them
     std::vector<uint64_t> fin;
     {
-      // spin (yielding) until something finishes or the next arrival is due
+      // spin (yielding) until something finishes or the next arrival is due; no
+      // waiting while requests are due already
       const uint64_t f0 = s->nfinished.load();
-      const int64_t t_end = std::min<int64_t>(now_ns() + 200000,
-                                              next < nreq && arr ? t0 + arr[next] : INT64_MAX);
+      const bool due = next < nreq && (!arr || now_ns() >= t0 + arr[next]);
+      const int64_t t_end = due ? 0 : std::min<int64_t>(now_ns() + 200000,
+                                                       next < nreq && arr ? t0 + arr[next]
+                                                                          : INT64_MAX);
       while (s->nfinished.load() == f0 && now_ns() < t_end) std::this_thread::yield();
       std::unique_lock<std::mutex> lk(s->mu);
       while (!s->finished.empty()) {
