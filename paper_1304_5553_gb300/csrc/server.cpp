@@ -122,6 +122,9 @@ struct SReq {
 constexpr int64_t kSlotDevBytes = 16 << 20;
 constexpr int64_t kSlotHostBytes = 16 << 20;
 constexpr int64_t kCtlBytes = 256;
+// Work lists up to this size are read by the batch kernel from page-locked host
+// memory instead of being copied to the device first.
+constexpr int64_t kDirectListBytes = 8192;
 
 struct Slot {
   CUdeviceptr dev = 0;
@@ -274,14 +277,16 @@ void launch_batch(pyc_server* s, Batch& b) {
   int nitems = 0;
   SlotLayout L;
   CUfunction f;
-  const int64_t res_off = layout(s->cfg.max_batch, 0, 0, 0, 0).res;
+  // results go straight to the slot's page-locked host area (the kernel writes
+  // them over the chip-to-chip link; no copy back after the kernel)
+  const int64_t host_res = layout(s->cfg.max_batch, 0, 0, 0, 0).host_res;
   if (reduce) {
     pyc_reduce* h = static_cast<pyc_reduce*>(b.h);
     std::vector<ReduceTaskIn> in;
     std::vector<ReduceItem> items;
     for (size_t k = 0; k < b.reqs.size(); ++k)
       in.push_back({b.reqs[k]->ptrs.data(), b.reqs[k]->scalars.data(), b.reqs[k]->n,
-                    reinterpret_cast<void*>(sl.dev + res_off + (int64_t)k * h->gen.out_bytes)});
+                    static_cast<void*>(sl.host + host_res + (int64_t)k * h->gen.out_bytes)});
     int64_t nslots = write_reduce_work(h, cfg, in, tasks, items);
     L = layout(s->cfg.max_batch, (int64_t)tasks.size(), (int64_t)(items.size() * sizeof(ReduceItem)),
                round_up(std::max<int64_t>(nslots, 1) * h->gen.acc_bytes, 256),
@@ -312,9 +317,15 @@ void launch_batch(pyc_server* s, Batch& b) {
     f = h->mod->function(h->kname("pyc_mbatch", cfg.v));
   }
   if (nitems > 0) {
-    PYC_CU(d.cuMemcpyHtoDAsync(sl.dev + L.tasks, sl.host, (size_t)(L.task_bytes + L.item_bytes), st));
+    // a small work list is read by the kernel from the page-locked slot itself;
+    // a larger one (read by many CTAs) is copied to the device first
+    const bool direct = L.task_bytes + L.item_bytes <= kDirectListBytes;
+    if (!direct)
+      PYC_CU(d.cuMemcpyHtoDAsync(sl.dev + L.tasks, sl.host, (size_t)(L.task_bytes + L.item_bytes),
+                                 st));
     int grid = std::max(1, std::min(resident_ctas(f, cfg.block), nitems));
-    CUdeviceptr tasks_d = sl.dev + L.tasks, items_d = sl.dev + L.items, ctl = sl.dev;
+    CUdeviceptr tasks_d = direct ? reinterpret_cast<CUdeviceptr>(sl.host) : sl.dev + L.tasks;
+    CUdeviceptr items_d = tasks_d + (CUdeviceptr)(L.items - L.tasks), ctl = sl.dev;
     CUdeviceptr tickets = sl.dev + kCtlBytes, part = sl.dev + L.part;
     if (reduce) {
       void* params[] = {&tasks_d, &items_d, &nitems, &part, &tickets, &ctl};
@@ -326,8 +337,6 @@ void launch_batch(pyc_server* s, Batch& b) {
                               nullptr));
     }
   }
-  if (reduce && L.res_bytes > 0)
-    PYC_CU(d.cuMemcpyDtoHAsync(sl.host + L.host_res, sl.dev + L.res, (size_t)L.res_bytes, st));
   PYC_CU(d.cuEventRecord(sl.ev, st));
 }
 
