@@ -112,3 +112,58 @@ def test_random_soak(data):
             v, idx = pyc.argf32_from_tensor(out.view(1, 2))
             assert (float(v.cpu()[0]), int(idx.cpu()[0])) == oracle.argmin_f32(
                 host["x"][off:off + n]), tag
+
+
+def test_random_segment_tables(data):
+    """80 random segment tables (1 to 600 segments, lengths log-uniform up to 2^17
+    with empty segments mixed in, misaligned bases, random configurations): dot
+    products within their bounds and int32 -> int64 sums and argmins exact per
+    segment, each table launched twice (the second a replay of the cached plan)."""
+    host, dev = data
+    rng = np.random.default_rng(97)
+    for case in range(80):
+        nseg = int(rng.integers(1, 600))
+        lens = np.where(rng.random(nseg) < 0.1, 0,
+                        (2 ** rng.uniform(0, 17, nseg)).astype(np.int64)).astype(np.int64)
+        total = int(lens.sum())
+        if total > POOL - 64:
+            lens = (lens * (POOL - 64) // max(total, 1)).astype(np.int64)
+            total = int(lens.sum())
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        base = int(rng.integers(0, 64))
+        name = ["dot_f32", "sum_i32_i64", "argmin_f32"][case % 3]
+        cfg = {} if rng.random() < 0.4 else dict(
+            vec_bytes=int(rng.choice([16, 32])), items_per_thread=int(rng.choice([1, 2, 4])),
+            block=int(rng.choice([64, 128, 256, 512])))
+        h = stock.create(name, **cfg)
+        tag = (case, name, nseg, total, base, cfg)
+        if name == "dot_f32":
+            ptrs = [dev["x"].data_ptr() + 4 * base, dev["y"].data_ptr() + 4 * base]
+            out = torch.zeros(nseg, dtype=torch.float32, device="cuda")
+        elif name == "sum_i32_i64":
+            ptrs = [dev["xi"].data_ptr() + 4 * base]
+            out = torch.zeros(nseg, dtype=torch.int64, device="cuda")
+        else:
+            ptrs = [dev["x"].data_ptr() + 4 * base]
+            out = torch.zeros((nseg, 2), dtype=torch.int64, device="cuda")
+        for rep in range(2):
+            out.zero_()
+            pyc.pyc_reduce_batched(h, nseg, off, ptrs, None, out.data_ptr(), _s())
+            torch.cuda.synchronize()
+            if name == "dot_f32":
+                ref, ab = oracle.dot_segments_f32(off, host["x"][base:base + total],
+                                                  host["y"][base:base + total])
+                got = out.cpu().numpy().astype(np.float64)
+                assert np.all(np.abs(got - ref) <= plain_sum_bound(ab)), tag
+            elif name == "sum_i32_i64":
+                got = out.cpu().numpy()
+                for k in range(nseg):
+                    a, b = base + off[k], base + off[k + 1]
+                    assert got[k] == oracle.sum_i32_i64(host["xi"][a:b]), tag + (k,)
+            else:
+                v, idx = pyc.argf32_from_tensor(out)
+                v, idx = v.cpu().numpy(), idx.cpu().numpy()
+                for k in range(nseg):
+                    a, b = base + off[k], base + off[k + 1]
+                    assert (float(v[k]), int(idx[k])) == oracle.argmin_f32(host["x"][a:b]), \
+                        tag + (k,)
