@@ -74,3 +74,113 @@ def test_mixed_type_trees_bit_exact(n):
         bad = np.flatnonzero((g.view(np.uint8).reshape(n, -1) !=
                               want.view(np.uint8).reshape(n, -1)).any(axis=1))
         assert bad.size == 0, (k, n, bad[:4], g[bad[:4]], want[bad[:4]])
+
+
+def _random_tree(rng, G, h, depth):
+    """A random expression over the arrays of _data (and Python scalars), built as
+    a GPU expression and as a record of its tree side by side.  No division by
+    zero (divisors are |e| + 1), square roots of |e|, small integer leaves; the
+    only cast is to binary64."""
+    names = ["x32", "x64", "i32", "i64", "h16", "b16"]
+    if depth == 0 or rng.random() < 0.25:
+        r = rng.random()
+        if r < 0.75:
+            k = names[int(rng.integers(0, len(names)))]
+            return G[k], ("leaf", k)
+        if r < 0.9:
+            v = float(np.round(rng.uniform(-3, 3), 3))
+            return v, ("float", v)
+        v = int(rng.integers(-9, 10))
+        return v, ("int", v)
+    op = ["+", "-", "*", "/", "min", "max", "neg", "abs", "sqrt", "cmp", "where", "cast"][
+        int(rng.integers(0, 12))]
+    if op in ("neg", "abs", "sqrt", "cast"):
+        ge, te = _random_tree(rng, G, h, depth - 1)
+        if not isinstance(ge, ga.Expr):  # unary operators need an array operand
+            ge, te = G["x32"], ("leaf", "x32")
+        if op == "neg":
+            return -ge, ("neg", te)
+        if op == "abs":
+            return abs(ge), ("abs", te)
+        if op == "sqrt":
+            return ga.sqrt(abs(ge)), ("sqrt", ("abs", te))
+        return ge.astype(torch.float64), ("f64", te)
+    ga_, ta = _random_tree(rng, G, h, depth - 1)
+    gb_, tb = _random_tree(rng, G, h, depth - 1)
+    if not isinstance(ga_, ga.Expr) and not isinstance(gb_, ga.Expr):
+        ga_, ta = G["x32"], ("leaf", "x32")
+    if op == "+":
+        return ga_ + gb_, ("+", ta, tb)
+    if op == "-":
+        return ga_ - gb_, ("-", ta, tb)
+    if op == "*":
+        return ga_ * gb_, ("*", ta, tb)
+    if op == "/":
+        if not isinstance(gb_, ga.Expr):
+            gb_, tb = G["i32"], ("leaf", "i32")
+        return ga_ / (abs(gb_) + 1), ("/", ta, ("+", ("abs", tb), ("int", 1)))
+    if op == "min":
+        return ga.minimum(ga_, gb_), ("min", ta, tb)
+    if op == "max":
+        return ga.maximum(ga_, gb_), ("max", ta, tb)
+    if op == "cmp":
+        return (ga_ < gb_), ("<", ta, tb)
+    return ga.where(ga_ > gb_, ga_, gb_), ("where", (">", ta, tb), ta, tb)
+
+
+def _oracle_tree(t, h, f64):
+    """The oracle tuple of a _random_tree record: Python floats are binary64
+    scalars when a binary64 array is in the whole tree, else binary32; Python
+    ints are int32."""
+    if t[0] == "leaf":
+        return h[t[1]]
+    if t[0] == "float":
+        return np.float64(t[1]) if f64 else np.float32(t[1])
+    if t[0] == "int":
+        return np.int32(t[1])
+    return (t[0],) + tuple(_oracle_tree(c, h, f64) for c in t[1:])
+
+
+def _all_finite(tree):
+    """True if every floating value the oracle computes on the way to tree's
+    result is finite (no overflow to infinity, no NaN from an integer that
+    wrapped to INT_MIN under sqrt(abs(.))): such trees are redrawn, since the
+    ordering of NaN under min / max / where is not what the test checks."""
+    if not isinstance(tree, tuple):
+        return True
+    if not all(_all_finite(c) for c in tree[1:]):
+        return False
+    v = np.asarray(ox.eval_typed(tree))
+    return v.dtype.kind != "f" or bool(np.all(np.isfinite(v)))
+
+
+def _has_f64(t):
+    return t == ("leaf", "x64") or (t[0] not in ("leaf", "float", "int") and
+                                    any(_has_f64(c) for c in t[1:]))
+
+
+def test_random_mixed_type_trees():
+    """60 random trees of depth up to 4 over every array type and Python scalars,
+    each compiled into one kernel and compared with the typed oracle: the result
+    type, and every element (integers exactly; floating values exactly, +0 and -0
+    counting as equal)."""
+    n = 4099
+    host, G = _data(n)
+    host = dict(host, i32=np.clip(host["i32"], -99, 99).astype(np.int32),
+                i64=np.clip(host["i64"], -99, 99).astype(np.int64))
+    G = dict(G, i32=ga.GArray(torch.from_numpy(host["i32"]).cuda()),
+             i64=ga.GArray(torch.from_numpy(host["i64"]).cuda()))
+    rng = np.random.default_rng(98)
+    done = 0
+    while done < 60:
+        expr, rec = _random_tree(rng, G, host, 4)
+        if not isinstance(expr, ga.Expr) or isinstance(expr, ga.GArray):
+            continue
+        tree = _oracle_tree(rec, host, _has_f64(rec))
+        if not _all_finite(tree):
+            continue
+        want = np.asarray(ox.eval_typed(tree))
+        got = ga.evaluate(expr).tensor.cpu().numpy()
+        assert got.dtype.type == want.dtype.type, (rec, got.dtype, want.dtype)
+        assert np.array_equal(got, want), (rec, np.flatnonzero(got != want)[:4])
+        done += 1
