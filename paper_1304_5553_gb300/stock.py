@@ -47,7 +47,9 @@ SCANS = {
     "cumsum_f32": (pyc.PYC_F32, "0", "a+b", "x[i]", "y[i] = item", "float *x, float *y"),
     "cumsum_excl_i32_i64": (pyc.PYC_I64, "0", "a+b", "(long long)x[i]", "y[i] = prev_item",
                             "int *x, long long *y"),
-    "cummax_f32": (pyc.PYC_F32, "-INFINITY", "a > b ? a : b", "x[i]", "y[i] = item",
+    # fmaxf: one instruction where a compare-and-select takes two, and a scan applies
+    # its operation about three times per element (NaN elements are skipped)
+    "cummax_f32": (pyc.PYC_F32, "-INFINITY", "fmaxf(a, b)", "x[i]", "y[i] = item",
                    "float *x, float *y"),
     # composition of v -> ca[i] v + cb[i] (mod 2^32), packed A << 32 | B: not commutative
     "affine_u32": (pyc.PYC_U64, "1ull << 32",
