@@ -657,6 +657,16 @@ def bench_serving(torch, pyc, stock, dev, nreq=50000, rate=20000.0, budget=40 <<
                     "reqs_per_s": round(nreq / span, 1),
                     "GB/s": round(total_bytes / span / 1e9, 1),
                     "mean_batch": round(float(bs.mean()), 2)}
+                if mode == pyc.PYC_REPLAY_SERVER and arr is not None:
+                    # where an open-loop request's time goes (medians): arrival ->
+                    # admitted, admitted -> its batch enqueued (work list, launch),
+                    # enqueued -> completion seen by the scheduler
+                    adm_t = np.array([r.t_admit_ns for r in res], np.int64)
+                    lau_t = np.array([r.t_launch_ns for r in res], np.int64)
+                    med = lambda v: round(float(np.percentile(v / 1e3, 50)), 1)
+                    out["%s_%s" % (label, mname)]["stages_p50_us"] = {
+                        "queued": med(adm_t - sub_t), "batched_and_launched": med(lau_t - adm_t),
+                        "on_device_until_seen": med(done_t - lau_t)}
         st = pyc.pyc_server_get_stats(srv)
         out["peak_admitted_bytes"] = st["peak_admitted_bytes"]
         c = out["closed_loop_server"]["reqs_per_s"] / out["closed_loop_direct"]["reqs_per_s"]

@@ -740,13 +740,15 @@ struct pyc_mitem {
 template <int VB, int U>
 __device__ __forceinline__ void pyc_map_batched_body(const pyc_mtask* __restrict__ tasks,
     const pyc_mitem* __restrict__ items, const int nitems, unsigned* __restrict__ ctl) {
-  __shared__ int pyc_it;
-  for (;;) {
-    if (threadIdx.x == 0) pyc_it = (int)atomicAdd(&ctl[0], 1u);
-    __syncthreads();
-    const int it = pyc_it;
-    __syncthreads();
-    if (it >= nitems) break;
+  // Item order: CTA b takes item b first (no counter round trip before its
+  // first load); later items come from the counter (offset by the grid), the
+  // next index fetched by thread 0 while the current item runs and handed to
+  // the CTA through one of two shared slots (the other may still be read).
+  __shared__ int pyc_it[2];
+  int it = (int)blockIdx.x;
+  for (int k = 0; it < nitems; ++k) {
+    int next = 0;
+    if (threadIdx.x == 0) next = (int)gridDim.x + (int)atomicAdd(&ctl[0], 1u);
     const pyc_mitem I = items[it];
     const pyc_mtask& T = tasks[I.task];
     const pyc_i64 n = T.n, head = T.head, chunk = T.chunk, c = I.chunk;
@@ -759,6 +761,9 @@ __device__ __forceinline__ void pyc_map_batched_body(const pyc_mtask* __restrict
       const pyc_i64 se = ss + chunk < n ? ss + chunk : n;
       pyc_map_span<VB, U>(T.args, n, 0, 0, ss, se, threadIdx.x, blockDim.x);
     }
+    if (threadIdx.x == 0) pyc_it[k & 1] = next;
+    __syncthreads();
+    it = pyc_it[k & 1];
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1215,14 +1220,14 @@ template <int VB, int U, int WU>
 __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ tasks,
     const pyc_item* __restrict__ items, const int nitems, pyc_acc_t* __restrict__ part,
     unsigned* __restrict__ tickets, unsigned* __restrict__ ctl) {
-  __shared__ int pyc_it;
+  // Item order as in the batched map: CTA b takes item b first, then the
+  // counter's (offset by the grid), the next index fetched while this item runs.
+  __shared__ int pyc_it[2];
   __shared__ unsigned pyc_last;
-  for (;;) {
-    if (threadIdx.x == 0) pyc_it = (int)atomicAdd(&ctl[0], 1u);
-    __syncthreads();
-    const int it = pyc_it;
-    __syncthreads();
-    if (it >= nitems) break;
+  int it = (int)blockIdx.x;
+  for (int k = 0; it < nitems; ++k) {
+    int next = 0;
+    if (threadIdx.x == 0) next = (int)gridDim.x + (int)atomicAdd(&ctl[0], 1u);
     const pyc_item I = items[it];
     if (I.chunk < 0) {
       const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1255,6 +1260,9 @@ __device__ __forceinline__ void pyc_batched_body(const pyc_task* __restrict__ ta
         }
       }
     }
+    if (threadIdx.x == 0) pyc_it[k & 1] = next;
+    __syncthreads();
+    it = pyc_it[k & 1];
   }
   // the last CTA to leave resets the work counter for the next launch
   if (threadIdx.x == 0) {

@@ -206,10 +206,15 @@ struct ReduceItem {
   int32_t task, chunk, count, pad;  // chunk < 0: warp bundle of `count` short tasks
 };
 // Writes task records (short tasks first, then long ones, longest first) and
-// work items; returns the number of partial slots the list needs.
+// work items; returns the number of partial slots the list needs.  Long tasks
+// are cut into chunks of kChunkElems elements (rounded to whole tiles); with
+// spread > 0 into about `spread` chunks of at least min_chunk elements each
+// instead, capped at that length.  A task's chunking depends on its own length
+// and the configuration only, so its result does not depend on the other tasks.
 int64_t write_reduce_work(const pyc_reduce* h, const LaunchCfg& cfg,
                           const std::vector<ReduceTaskIn>& in, std::vector<unsigned char>& tasks,
-                          std::vector<ReduceItem>& items);
+                          std::vector<ReduceItem>& items, int64_t spread = 0,
+                          int64_t min_chunk = 0);
 
 struct MapTaskIn {
   void* const* ptrs;
@@ -220,7 +225,8 @@ struct MapItem {
   int32_t task, chunk;
 };
 void write_map_work(const pyc_map* h, const LaunchCfg& cfg, const std::vector<MapTaskIn>& in,
-                    std::vector<unsigned char>& tasks, std::vector<MapItem>& items);
+                    std::vector<unsigned char>& tasks, std::vector<MapItem>& items,
+                    int64_t spread = 0, int64_t min_chunk = 0);
 
 // Batched reducer (batched.cpp).  The configuration of batched launches (the
 // segmented reducer and the server's batches) is tuned separately from single

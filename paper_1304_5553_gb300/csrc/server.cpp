@@ -125,6 +125,14 @@ constexpr int64_t kCtlBytes = 256;
 // Work lists up to this size are read by the batch kernel from page-locked host
 // memory instead of being copied to the device first.
 constexpr int64_t kDirectListBytes = 8192;
+// A request is cut into about kServeSpread chunks of at least kServeMinChunk
+// elements (at most the work list's usual chunk length), so that one request
+// arriving alone runs on many CTAs: a function of its own length only, so a
+// reduction's bits are the same alone and in any batch.
+constexpr int64_t kServeSpread = 256;
+constexpr int64_t kServeMinChunk = 4096;
+// Chunks of one batch at most (work items and partial slots of a slot).
+constexpr int64_t kBatchChunks = (int64_t)1 << 17;
 
 struct Slot {
   CUdeviceptr dev = 0;
@@ -287,7 +295,7 @@ void launch_batch(pyc_server* s, Batch& b) {
     for (size_t k = 0; k < b.reqs.size(); ++k)
       in.push_back({b.reqs[k]->ptrs.data(), b.reqs[k]->scalars.data(), b.reqs[k]->n,
                     static_cast<void*>(sl.host + host_res + (int64_t)k * h->gen.out_bytes)});
-    int64_t nslots = write_reduce_work(h, cfg, in, tasks, items);
+    int64_t nslots = write_reduce_work(h, cfg, in, tasks, items, kServeSpread, kServeMinChunk);
     L = layout(s->cfg.max_batch, (int64_t)tasks.size(), (int64_t)(items.size() * sizeof(ReduceItem)),
                round_up(std::max<int64_t>(nslots, 1) * h->gen.acc_bytes, 256),
                (int64_t)b.reqs.size() * h->gen.out_bytes);
@@ -305,7 +313,7 @@ void launch_batch(pyc_server* s, Batch& b) {
     std::vector<MapTaskIn> in;
     std::vector<MapItem> items;
     for (SReq* r : b.reqs) in.push_back({r->ptrs.data(), r->scalars.data(), r->n});
-    write_map_work(h, cfg, in, tasks, items);
+    write_map_work(h, cfg, in, tasks, items, kServeSpread, kServeMinChunk);
     L = layout(s->cfg.max_batch, (int64_t)tasks.size(), (int64_t)(items.size() * sizeof(MapItem)),
                0, 0);
     if (L.dev_end > kSlotDevBytes || L.task_bytes + L.item_bytes > L.host_res)
@@ -498,9 +506,11 @@ void scheduler(pyc_server* s) {
       std::vector<SReq*> rest;
       int64_t chunks = 0;
       for (SReq* r : s->admitted) {
-        int64_t rc = r->n / kChunkElems + 2;
+        // an upper bound on the request's chunks under kServeSpread / kServeMinChunk
+        const int64_t rc =
+            std::min(r->n / kServeMinChunk, std::max(kServeSpread, r->n / kChunkElems)) + 2;
         if (r->handle() == bt.h && (int)bt.reqs.size() < s->cfg.max_batch &&
-            (bt.reqs.empty() || chunks + rc <= (int64_t)1 << 15)) {
+            (bt.reqs.empty() || chunks + rc <= kBatchChunks)) {
           bt.reqs.push_back(r);
           chunks += rc;
         } else {

@@ -3,9 +3,12 @@
 // Reductions: a task of at most kSmallTask elements is reduced by one warp; such
 // tasks are placed first and packed blockDim/32 to a "bundle" item.  Longer tasks
 // are cut into chunks of kChunkElems elements rounded up to whole tiles (the
-// first chunk also takes the unaligned head); one CTA item per chunk, longest
-// tasks first.  A task with several chunks owns consecutive partial slots and a
-// ticket; its last chunk to finish combines the partials in chunk order.  Every
+// first chunk also takes the unaligned head), or, for a caller that asks for a
+// spread, into about that many chunks of at least a given length (a lone task of
+// moderate length then occupies many CTAs instead of a few); one CTA item per
+// chunk, longest tasks first.  A task with several chunks owns consecutive
+// partial slots and a ticket; its last chunk to finish combines the partials in
+// chunk order.  Every
 // choice depends only on the task itself and the launch configuration, so a
 // task's result does not depend on the other tasks of the list.
 //
@@ -18,19 +21,27 @@
 namespace pyc {
 
 namespace {
-int64_t chunk_elems(const HandleBase& h, const LaunchCfg& cfg) {
+// Chunk length of a task of len elements: kChunkElems rounded up to whole
+// tiles, or with spread > 0 short enough to cut the task into about `spread`
+// chunks, but never below min_chunk elements (both rounded up to whole tiles).
+// A function of the task's length and the launch configuration only.
+int64_t chunk_elems(const HandleBase& h, const LaunchCfg& cfg, int64_t len, int64_t spread,
+                    int64_t min_chunk) {
   const int64_t tile = (int64_t)cfg.block * (cfg.v.vec_bytes / h.min_bytes) * cfg.v.unroll;
-  return std::max<int64_t>(tile, (kChunkElems + tile - 1) / tile * tile);
+  auto whole = [&](int64_t e) { return std::max<int64_t>(tile, (e + tile - 1) / tile * tile); };
+  const int64_t cap = whole(kChunkElems);
+  if (spread <= 0) return cap;
+  const int64_t want = std::max<int64_t>((len + spread - 1) / spread, min_chunk);
+  return std::min(cap, whole(want));
 }
 }  // namespace
 
 int64_t write_reduce_work(const pyc_reduce* h, const LaunchCfg& cfg,
                           const std::vector<ReduceTaskIn>& in, std::vector<unsigned char>& tasks,
-                          std::vector<ReduceItem>& items) {
+                          std::vector<ReduceItem>& items, int64_t spread, int64_t min_chunk) {
   const ArgSpec& spec = h->spec;
   const ReduceGen& g = h->gen;
   const int64_t ntask = (int64_t)in.size();
-  const int64_t chunk = chunk_elems(*h, cfg);
   const int wpb = cfg.block / 32;
   std::vector<int64_t> small, large;
   for (int64_t t = 0; t < ntask; ++t) (in[t].n <= kSmallTask ? small : large).push_back(t);
@@ -56,8 +67,8 @@ int64_t write_reduce_work(const pyc_reduce* h, const LaunchCfg& cfg,
       nch = 0;
     } else {
       int64_t body = head >= 0 ? len - head : len;
-      tchunk = chunk;
-      nch = (body + chunk - 1) / chunk;
+      tchunk = chunk_elems(*h, cfg, len, spread, min_chunk);
+      nch = (body + tchunk - 1) / tchunk;
     }
     int32_t nchunks = (int32_t)nch, slot0 = 0;
     if (nch > 1) {
@@ -85,10 +96,10 @@ int64_t write_reduce_work(const pyc_reduce* h, const LaunchCfg& cfg,
 }
 
 void write_map_work(const pyc_map* h, const LaunchCfg& cfg, const std::vector<MapTaskIn>& in,
-                    std::vector<unsigned char>& tasks, std::vector<MapItem>& items) {
+                    std::vector<unsigned char>& tasks, std::vector<MapItem>& items, int64_t spread,
+                    int64_t min_chunk) {
   const ArgSpec& spec = h->spec;
   const MapGen& g = h->gen;
-  const int64_t chunk = chunk_elems(*h, cfg);
   tasks.assign(in.size() * (size_t)g.task_bytes, 0);
   items.clear();
   for (size_t t = 0; t < in.size(); ++t) {
@@ -97,6 +108,7 @@ void write_map_work(const pyc_map* h, const LaunchCfg& cfg, const std::vector<Ma
     std::vector<unsigned char> args = pack_args(spec, m.ptrs, m.scalars);
     int64_t head = vector_head(spec, m.ptrs, cfg.v.vec_bytes, h->min_bytes, m.n);
     unsigned char* rec = &tasks[t * g.task_bytes];
+    const int64_t chunk = chunk_elems(*h, cfg, m.n, spread, min_chunk);
     std::memcpy(rec, args.data(), args.size());
     std::memcpy(rec + g.task_off_n, &m.n, 8);
     std::memcpy(rec + g.task_off_head, &head, 8);
