@@ -625,8 +625,10 @@ void pyc_csr_destroy(pyc_csr_t a);
  * admits queued requests in arrival order while the logical bytes of admitted,
  * unreleased requests (every array of the request, n elements each, plus the
  * result) stay within mem_budget_bytes; groups admitted requests by handle into
- * one batched launch each (chunks of long requests across CTAs, short
- * reductions one warp each); spreads the batches over num_streams streams, at
+ * one batched launch each (a request longer than a warp's share is cut into
+ * about 256 chunks of at least 4096 elements, at most 2^16 rounded to whole
+ * tiles, one CTA each; short reductions one warp each); spreads the batches
+ * over num_streams streams, at
  * most max_inflight at a time; and retires them by completion events.  A
  * request's result depends only on the request itself, never on the other
  * requests of its batch.  The server owns a device arena (arena_bytes) for map
