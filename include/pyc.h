@@ -625,9 +625,9 @@ void pyc_csr_destroy(pyc_csr_t a);
  * admits queued requests in arrival order while the logical bytes of admitted,
  * unreleased requests (every array of the request, n elements each, plus the
  * result) stay within mem_budget_bytes; groups admitted requests by handle into
- * one batched launch each (a request longer than a warp's share is cut into
- * about 256 chunks of at least 4096 elements, at most 2^16 rounded to whole
- * tiles, one CTA each; short reductions one warp each); spreads the batches
+ * one batched launch each (a request is cut into about 256 chunks of at least
+ * 4096 elements and at most 2^16, both rounded up to whole tiles, one CTA each;
+ * a reduction of at most 2048 elements takes one warp); spreads the batches
  * over num_streams streams, at
  * most max_inflight at a time; and retires them by completion events.  A
  * request's result depends only on the request itself, never on the other
