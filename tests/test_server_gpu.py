@@ -358,3 +358,46 @@ def test_serving_config_mix_against_the_oracle():
     print("serving mix: checked", checked)
     assert checked["map"] > 200 and checked["reduce"] > 300 and checked["bf16_maps"] > 50
     assert checked["big"] >= 10
+
+
+def test_chunking_edges_alone():
+    """Requests whose lengths sit on the edges of the server's chunking -- one warp
+    (at most 2048 elements) or one CTA chunk, the least chunk (4096), where about
+    256 chunks stop being the least chunk (2^20), where the chunk reaches its cap
+    (2^24), ragged tails and misaligned starts -- each served alone: int32 dot
+    products into int64 and int32 maps bit-exact, binary32 dots within the plain
+    sum's bound."""
+    N = (1 << 25) + 64
+    xi, yi = inputs.int_uniform_i32(32, 0, N), inputs.int_uniform_i32(32, 1, N)
+    x, y = inputs.uniform_f32(32, 2, N, -1.0, 1.0), inputs.uniform_f32(32, 3, N, -1.0, 1.0)
+    dxi, dyi = torch.from_numpy(xi).cuda(), torch.from_numpy(yi).cuda()
+    dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    dz = torch.empty(N, dtype=torch.int32, device="cuda")
+    hdi, hdf, hm = stock.create("dot_i32_i64"), stock.create("dot_f32"), stock.create("lin_comb_i32")
+    sc = pyc.pack_scalars(hm, [3, -2])
+    sizes = [2048, 2049, 4095, 4096, 4097, 65537, (1 << 20) - 1, 1 << 20, (1 << 20) + 1,
+             (1 << 22) + 3, (1 << 24) - 1, (1 << 24) + 4097, (1 << 25) - 5]
+    srv = pyc.pyc_server_create(8 << 30)
+    try:
+        for n in sizes:
+            for off in (0, 3):
+                a, b = xi[off:off + n], yi[off:off + n]
+                rid, r = _run_one(srv, pyc.make_request(
+                    pyc.PYC_REQ_REDUCE, hdi, n, [dxi.data_ptr() + 4 * off, dyi.data_ptr() + 4 * off]))
+                pyc.pyc_server_release(srv, rid)
+                got = np.frombuffer(bytes(r.value)[:8], np.int64)[0]
+                assert got == oracle.dot_i32_i64(a, b), ("dot i32", n, off)
+                rid, r = _run_one(srv, pyc.make_request(
+                    pyc.PYC_REQ_REDUCE, hdf, n, [dx.data_ptr() + 4 * off, dy.data_ptr() + 4 * off]))
+                pyc.pyc_server_release(srv, rid)
+                ref, ab = oracle.dot_f32(x[off:off + n], y[off:off + n])
+                v = float(np.frombuffer(bytes(r.value)[:4], np.float32)[0])
+                assert abs(v - ref) <= plain_sum_bound(ab), ("dot f32", n, off, v, ref)
+                rid, r = _run_one(srv, pyc.make_request(
+                    pyc.PYC_REQ_MAP, hm, n, [dxi.data_ptr() + 4 * off, dyi.data_ptr() + 4 * off,
+                                             dz.data_ptr() + 4 * off], sc))
+                pyc.pyc_server_release(srv, rid)
+                want = (3 * a.astype(np.int64) - 2 * b.astype(np.int64)).astype(np.int32)
+                assert np.array_equal(dz[off:off + n].cpu().numpy(), want), ("map i32", n, off)
+    finally:
+        pyc.pyc_server_destroy(srv)
