@@ -795,7 +795,11 @@ def profile_scan(args):
     if args.config:  # vecV_uU_bB: a fixed launch configuration (no tuning launches)
         v, u, b = (int(q[1:] if q[0] in "ub" else q[3:]) for q in args.config.split("_"))
         opts = dict(vec_bytes=v, items_per_thread=u, block=b)
-    h = stock.create(name, **opts)
+    if args.scan_op:  # the stock spec with its operation written another way
+        dt, neu, _, inp, out, spec = stock.SCANS[name]
+        h = pyc.pyc_scan_create(dt, neu, args.scan_op, inp, out, spec, opts or None)
+    else:
+        h = stock.create(name, **opts)
     s = torch.cuda.current_stream().cuda_stream
     if args.autotune == "on" and not opts:
         pyc.pyc_scan_autotune(h, n, s)
@@ -1065,6 +1069,8 @@ def main():
                     help="profiling driver: time one stock reduction only (not a bench line)")
     ap.add_argument("--profile-scan", default="",
                     help="profiling driver: time one stock scan only (not a bench line)")
+    ap.add_argument("--scan-op", default="",
+                    help="with --profile-scan: the stock scan with this operation instead")
     ap.add_argument("--profile-batched", default="",
                     help="profiling driver: the segmented dot (dot_f32 / dot_bf16) only")
     ap.add_argument("--segments", type=int, default=20000,
